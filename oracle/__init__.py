@@ -1,0 +1,266 @@
+"""FP64 CPU oracle of the CG-SLAM Gaussian rasterizer (arXiv 2403.16095).
+
+TEST INFRASTRUCTURE ONLY: the product path never imports this package. Only the
+test-suite, the smoke check and the benchmark's CPU-baseline leg use it.
+
+The arithmetic lives in ``gs_oracle.c`` (plain C, FP64, OpenMP over image rows);
+this module compiles it with gcc and marshals numpy arrays through ctypes.
+Every function takes FP32 generator outputs and widens them to FP64 exactly.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gs_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+
+
+class _Scene(C.Structure):
+    _fields_ = [("n", C.c_int), ("means", _dp), ("log_scales", _dp), ("quats", _dp),
+                ("opacity_logit", _dp), ("colors", _dp), ("nu", _dp)]
+
+
+class _Cam(C.Structure):
+    _fields_ = [("width", C.c_int), ("height", C.c_int), ("fx", C.c_double), ("fy", C.c_double),
+                ("cx", C.c_double), ("cy", C.c_double), ("znear", C.c_double)]
+
+
+class _Opts(C.Structure):
+    _fields_ = [("jclamp", C.c_double), ("nu_cull", C.c_double)]
+
+
+class _Loss(C.Structure):
+    _fields_ = [("w_color", C.c_double), ("w_depth", C.c_double), ("w_unc", C.c_double),
+                ("w_nu", C.c_double), ("unc_tau", C.c_double), ("target_color", _dp),
+                ("target_depth", _dp)]
+
+
+class _Image(C.Structure):
+    _fields_ = [("color", _dp), ("depth", _dp), ("alpha", _dp), ("unc", _dp), ("nu_map", _dp),
+                ("median", _dp), ("T_final", _dp), ("n_contrib", _ip), ("margins", _dp)]
+
+
+class _Grads(C.Structure):
+    _fields_ = [("means", _dp), ("log_scales", _dp), ("quats", _dp), ("opacity_logit", _dp),
+                ("colors", _dp), ("nu", _dp), ("g_mean2d", _dp), ("g_conic", _dp),
+                ("g_opacity", _dp), ("g_depth", _dp), ("pose", _dp)]
+
+
+def build(force: bool = False) -> str:
+    """Compile gs_oracle.c into _build/liboracle.so (gcc, -O2, OpenMP, IEEE math)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
+                               "-fno-fast-math", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        _lib.orc_project.argtypes = [C.POINTER(_Scene), C.POINTER(_Cam), _dp, C.POINTER(_Opts),
+                                     _dp, _dp, _dp, _dp, _ip, _ip, _ip]
+        _lib.orc_render.argtypes = [C.POINTER(_Scene), C.POINTER(_Cam), _dp, C.POINTER(_Opts), _dp,
+                                    C.c_int, C.POINTER(_Image)]
+        _lib.orc_render_pixels.argtypes = [C.POINTER(_Scene), C.POINTER(_Cam), _dp, C.POINTER(_Opts),
+                                           _dp, C.c_int, _ip, C.POINTER(_Image)]
+        _lib.orc_loss_value.argtypes = [C.POINTER(_Scene), C.POINTER(_Cam), _dp, C.POINTER(_Opts),
+                                        C.POINTER(_Loss), _dp, C.POINTER(C.c_uint64)]
+        _lib.orc_grad.argtypes = [C.POINTER(_Scene), C.POINTER(_Cam), _dp, C.POINTER(_Opts),
+                                  C.POINTER(_Loss), C.POINTER(_Grads), _dp]
+        _lib.orc_bin_tiles.argtypes = [C.c_int, C.c_int, _ip, C.POINTER(C.c_float), C.c_int, C.c_int,
+                                       _ip, _ip, _ip, C.c_longlong, C.POINTER(C.c_uint64),
+                                       C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
+        _lib.orc_bin_tiles.restype = C.c_longlong
+        _lib.orc_adam_step.argtypes = [_dp, _dp, C.c_double, C.c_double, C.c_double, C.c_double,
+                                       C.c_double]
+        _lib.orc_set_threads.argtypes = [C.c_int]
+        _lib.orc_get_threads.restype = C.c_int
+    return _lib
+
+
+def set_threads(n: int) -> None:
+    lib().orc_set_threads(int(n))
+
+
+def threads() -> int:
+    return int(lib().orc_get_threads())
+
+
+# ----------------------------------------------------------------- helpers
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _p(a, t=_dp):
+    return None if a is None else a.ctypes.data_as(t)
+
+
+class _Keep:
+    """Holds FP64 copies alive while the C call runs."""
+
+    def __init__(self, scene):
+        self.arrs = [_f64(getattr(scene, k)) for k in
+                     ("means", "log_scales", "quats", "opacity_logit", "colors", "nu")]
+        self.s = _Scene(int(self.arrs[0].shape[0]), *(_p(a) for a in self.arrs))
+
+
+def _cam(cam):
+    return _Cam(int(cam.width), int(cam.height), float(cam.fx), float(cam.fy), float(cam.cx),
+                float(cam.cy), float(cam.znear))
+
+
+@dataclasses.dataclass
+class LossSpec:
+    """L = sum_p 1/(HW) [ m_p (w_color sum_ch |C-C*| + w_depth |D-D*|) + w_unc |U| + w_nu nu_map ],
+    m_p = 1/(1 + nu_map/unc_tau) if unc_tau > 0 else 1 (held constant in the gradient)."""
+    w_color: float = 1.0
+    w_depth: float = 1.0
+    w_unc: float = 0.0
+    w_nu: float = 0.0
+    unc_tau: float = 0.0
+    target_color: np.ndarray | None = None   # [3,H,W]
+    target_depth: np.ndarray | None = None   # [H,W] (also the sensor depth of U)
+
+
+class _KeepLoss:
+    def __init__(self, L: LossSpec):
+        self.tc = None if L.target_color is None else _f64(L.target_color)
+        self.td = None if L.target_depth is None else _f64(L.target_depth)
+        self.s = _Loss(L.w_color, L.w_depth, L.w_unc, L.w_nu, L.unc_tau, _p(self.tc), _p(self.td))
+
+
+# ----------------------------------------------------------------- API
+def project(scene, cam, T, jclamp=1.3, nu_cull=0.0):
+    k = _Keep(scene)
+    n = scene.n
+    Tc = _f64(T).reshape(3, 4)
+    out = dict(mean2d=np.zeros((n, 2)), conic=np.zeros((n, 3)), depth=np.zeros(n), opacity=np.zeros(n),
+               radius=np.zeros(n, np.int32), rect=np.zeros((n, 4), np.int32), valid=np.zeros(n, np.int32))
+    r = lib().orc_project(C.byref(k.s), C.byref(_cam(cam)), _p(Tc), C.byref(_Opts(jclamp, nu_cull)),
+                          _p(out["mean2d"]), _p(out["conic"]), _p(out["depth"]), _p(out["opacity"]),
+                          _p(out["radius"], _ip), _p(out["rect"], _ip), _p(out["valid"], _ip))
+    assert r == 0
+    out["valid"] = out["valid"].astype(bool)
+    return out
+
+
+def _image_bufs(n_pix, H=None, W=None):
+    shp = (n_pix,) if H is None else (H, W)
+    o = dict(color=np.zeros((3, *shp)), depth=np.zeros(shp), alpha=np.zeros(shp), unc=np.zeros(shp),
+             nu_map=np.zeros(shp), median=np.zeros(shp), T_final=np.zeros(shp),
+             n_contrib=np.zeros(shp, np.int32), margins=np.zeros((5, *shp)))
+    im = _Image(*(_p(o[k], _ip if k == "n_contrib" else _dp) for k in
+                  ("color", "depth", "alpha", "unc", "nu_map", "median", "T_final", "n_contrib", "margins")))
+    return o, im
+
+
+def render(scene, cam, T, obs_depth=None, mode="rect", jclamp=1.3, nu_cull=0.0):
+    """Full image, FP64. mode 'rect' (rect-scatter lists) or 'brute' (scan every
+    Gaussian per pixel). Returns planar arrays: color [3,H,W], others [H,W];
+    margins [5,H,W] are the per-pixel decision margins."""
+    k = _Keep(scene)
+    Tc = _f64(T).reshape(3, 4)
+    od = None if obs_depth is None else _f64(obs_depth)
+    o, im = _image_bufs(None, cam.height, cam.width)
+    r = lib().orc_render(C.byref(k.s), C.byref(_cam(cam)), _p(Tc), C.byref(_Opts(jclamp, nu_cull)),
+                         _p(od), 1 if mode == "rect" else 0, C.byref(im))
+    assert r == 0
+    return o
+
+
+def render_pixels(scene, cam, T, pix, obs_depth=None, jclamp=1.3, nu_cull=0.0):
+    """Sampled pixels (flat indices y*W+x), each computed on its own by brute force."""
+    k = _Keep(scene)
+    Tc = _f64(T).reshape(3, 4)
+    od = None if obs_depth is None else _f64(obs_depth)
+    pix = np.ascontiguousarray(pix, dtype=np.int32)
+    o, im = _image_bufs(len(pix))
+    r = lib().orc_render_pixels(C.byref(k.s), C.byref(_cam(cam)), _p(Tc), C.byref(_Opts(jclamp, nu_cull)),
+                                _p(od), len(pix), _p(pix, _ip), C.byref(im))
+    assert r == 0
+    return o
+
+
+def loss_value(scene, cam, T, L: LossSpec, jclamp=1.3, nu_cull=0.0):
+    """(loss, decision hash) for one frame."""
+    k = _Keep(scene)
+    kl = _KeepLoss(L)
+    Tc = _f64(T).reshape(3, 4)
+    v = C.c_double(0)
+    h = C.c_uint64(0)
+    r = lib().orc_loss_value(C.byref(k.s), C.byref(_cam(cam)), _p(Tc), C.byref(_Opts(jclamp, nu_cull)),
+                             C.byref(kl.s), C.byref(v), C.byref(h))
+    assert r == 0
+    return v.value, h.value
+
+
+def grad(scene, cam, T, L: LossSpec, jclamp=1.3, nu_cull=0.0):
+    """Loss, parameter gradients, per-Gaussian 2D gradients and the left se(3)
+    pose gradient (rho, phi) for one frame, all FP64."""
+    k = _Keep(scene)
+    kl = _KeepLoss(L)
+    n = scene.n
+    Tc = _f64(T).reshape(3, 4)
+    o = dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
+             opacity_logit=np.zeros(n), colors=np.zeros((n, 3)), nu=np.zeros(n),
+             g_mean2d=np.zeros((n, 2)), g_conic=np.zeros((n, 3)), g_opacity=np.zeros(n),
+             g_depth=np.zeros(n), pose=np.zeros(6))
+    g = _Grads(*(_p(o[f]) for f in ("means", "log_scales", "quats", "opacity_logit", "colors", "nu",
+                                     "g_mean2d", "g_conic", "g_opacity", "g_depth", "pose")))
+    v = C.c_double(0)
+    r = lib().orc_grad(C.byref(k.s), C.byref(_cam(cam)), _p(Tc), C.byref(_Opts(jclamp, nu_cull)),
+                       C.byref(kl.s), C.byref(g), C.byref(v))
+    assert r == 0
+    o["loss"] = v.value
+    return o
+
+
+def bin_tiles(rect, depth_f32, n_per_frame, tile, cams, capacity=None):
+    """Brute-force tile lists: (keys u64 [P], values u32 [P], ranges u32 [n_tiles,2])."""
+    rect = np.ascontiguousarray(rect, dtype=np.int32)
+    depth = np.ascontiguousarray(depth_f32, dtype=np.float32)
+    tx = np.array([(c.width + tile - 1) // tile for c in cams], np.int32)
+    ty = np.array([(c.height + tile - 1) // tile for c in cams], np.int32)
+    toff = np.concatenate([[0], np.cumsum(tx * ty)[:-1]]).astype(np.int32)
+    n_tiles = int((tx * ty).sum())
+    n = rect.shape[0]
+    cap = capacity if capacity is not None else int(n) * n_tiles if n * n_tiles < 50_000_000 else 50_000_000
+    while True:
+        keys = np.zeros(max(cap, 1), np.uint64)
+        vals = np.zeros(max(cap, 1), np.uint32)
+        ranges = np.zeros((n_tiles, 2), np.uint32)
+        P = lib().orc_bin_tiles(n, n_per_frame, _p(rect, _ip), depth.ctypes.data_as(C.POINTER(C.c_float)),
+                                tile, len(cams), _p(tx, _ip), _p(ty, _ip), _p(toff, _ip), cap,
+                                keys.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                vals.ctypes.data_as(C.POINTER(C.c_uint32)),
+                                ranges.ctypes.data_as(C.POINTER(C.c_uint32)))
+        if P == -1 and capacity is None:
+            cap *= 4
+            continue
+        assert P >= 0, P
+        return keys[:P], vals[:P], ranges
+
+
+def adam_step(state, grad6, lr_rot=0.0015, lr_trans=0.00215, beta1=0.9, beta2=0.999, eps=1e-8):
+    """In-place FP64 Adam step on the pose state [R(9), t(3), m(6), v(6), step]."""
+    assert state.dtype == np.float64 and state.shape == (25,)
+    g = _f64(grad6)
+    lib().orc_adam_step(_p(state), _p(g), lr_rot, lr_trans, beta1, beta2, eps)
+    return state

@@ -1,0 +1,260 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper's definitions and
+by mathematics (closed forms, invariants, brute force, finite differences).
+
+Each test names the equation it pins. None of these compares the oracle with
+itself through a retyped formula: every expected value comes from an
+independent route (a closed form for a special case, an invariant, a second
+algorithm, or numerical differentiation).
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+
+def _scene(means, log_scales, quats, logits, colors, nu=None):
+    n = len(means)
+    return synth.Scene(np.asarray(means, float), np.asarray(log_scales, float), np.asarray(quats, float),
+                       np.asarray(logits, float), np.asarray(colors, float),
+                       np.zeros(n) if nu is None else np.asarray(nu, float))
+
+
+def _ident():
+    T = np.zeros((3, 4))
+    T[:, :3] = np.eye(3)
+    return T
+
+
+CAM = synth.Camera(128, 96, 100.0, 100.0, 64.0, 48.0)
+
+
+# ----------------------------------------------------------- Eq. 1-5 closed form
+def test_single_isotropic_gaussian_closed_form():
+    """P1 (Eq. 1-5 with the 0.3 px^2 dilation): one isotropic Gaussian at (0,0,z)
+    renders alpha(p) = sigma exp(-|d|^2 / (2 v)), v = (f s / z)^2 + 0.3, inside
+    q <= 9, and its footprint radius is ceil(3 sqrt(v))."""
+    z, s, logit = 3.0, 0.05, 0.4
+    sc = _scene([[0, 0, z]], [[math.log(s)] * 3], [[0.3, -0.5, 0.7, 0.1]], [logit], [[1.0, 0.5, 0.25]])
+    im = oracle.render(sc, CAM, _ident())
+    pr = oracle.project(sc, CAM, _ident())
+    v = (CAM.fx * s / z) ** 2 + 0.3
+    sigma = 1.0 / (1.0 + math.exp(-logit))
+    assert pr["radius"][0] == math.ceil(3 * math.sqrt(v))
+    np.testing.assert_allclose(pr["mean2d"][0], [64.0, 48.0], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(pr["conic"][0], [1 / v, 0, 1 / v], rtol=1e-12, atol=1e-15)
+    xs = np.arange(128) + 0.5 - 64.0
+    ys = np.arange(96) + 0.5 - 48.0
+    d2 = ys[:, None] ** 2 + xs[None, :] ** 2
+    alpha = sigma * np.exp(-d2 / (2 * v))
+    alpha[d2 / v > 9] = 0
+    alpha[alpha < 1 / 255] = 0
+    np.testing.assert_allclose(im["alpha"], alpha, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(im["color"][1], 0.5 * alpha, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(im["depth"], z * alpha, rtol=0, atol=1e-12)
+
+
+def test_principal_point_symmetry():
+    """P2 (pixel-centre convention): with cx = W/2, cy = H/2 the image of an
+    isotropic Gaussian on the optical axis is mirror-symmetric, bit for bit."""
+    sc = _scene([[0, 0, 2.5]], [[math.log(0.04)] * 3], [[1, 0, 0, 0]], [1.0], [[0.2, 0.9, 0.4]])
+    im = oracle.render(sc, CAM, _ident())
+    a = im["alpha"]
+    assert np.array_equal(a, a[:, ::-1]) and np.array_equal(a, a[::-1, :])
+    assert a[47, 63] == a[48, 64] > 0.5
+
+
+# ----------------------------------------------------------- Eq. 6-10 wiring
+def test_fronto_parallel_opaque_depth_and_uncertainty():
+    """P3 (Eq. 6-10): a stack of flat, opaque Gaussians all at depth z gives
+    D_alpha / O = z, median depth z, and U = 0 when the sensor depth is z."""
+    z = 2.0
+    rng = np.random.default_rng(3)
+    n = 12
+    means = np.c_[rng.uniform(-0.1, 0.1, n), rng.uniform(-0.1, 0.1, n), np.full(n, z)]
+    ls = np.c_[np.full(n, math.log(0.08)), np.full(n, math.log(0.08)), np.full(n, math.log(1e-4))]
+    sc = _scene(means, ls, np.tile([1.0, 0, 0, 0], (n, 1)), np.full(n, 6.0), rng.uniform(0, 1, (n, 3)))
+    D = np.full((96, 128), z)
+    im = oracle.render(sc, CAM, _ident(), obs_depth=D)
+    cov = im["alpha"] > 0.5
+    assert cov.sum() > 200
+    np.testing.assert_allclose(im["depth"][cov] / im["alpha"][cov], z, rtol=1e-14)
+    assert np.all(im["median"][cov] == z)
+    assert np.all(im["unc"] == 0.0)
+    # an opaque single Gaussian saturates at the 0.99 clamp in its centre
+    one = oracle.render(sc.subset([0]), CAM, _ident())
+    assert abs(one["alpha"].max() - 0.99) < 1e-12
+
+
+def test_median_depth_is_first_crossing_of_half():
+    """Eq. 7-8: the median depth is the depth of the Gaussian at which T first
+    drops below 0.5; with alphas 0.3 then 0.4 (T: 1 -> 0.7 -> 0.42) it is the
+    second one."""
+    # two Gaussians straddling the centre pixel; alpha at the centre pixel set via opacity
+    v = (100 * 0.05 / 2.0) ** 2 + 0.3
+    g = math.exp(-0.5 * 0.5 / v)                     # centre pixel offset (0.5, 0.5)
+    lo1 = -math.log(1.0 / (0.3 / g) - 1)             # alpha_1 = 0.3 at that pixel
+    g2 = math.exp(-0.5 * 0.5 / ((100 * 0.05 / 3.0) ** 2 + 0.3))
+    lo2 = -math.log(1.0 / (0.4 / g2) - 1)
+    sc = _scene([[0, 0, 2.0], [0, 0, 3.0]], [[math.log(0.05)] * 3] * 2, [[1, 0, 0, 0]] * 2, [lo1, lo2],
+                [[1, 0, 0], [0, 1, 0]])
+    im = oracle.render(sc, CAM, _ident())
+    assert im["median"][48, 64] == 3.0
+    np.testing.assert_allclose(im["T_final"][48, 64], 0.7 * 0.6, rtol=1e-12)
+
+
+def test_two_gaussian_composite_by_hand():
+    """P5 (Eq. 3-4): front Gaussian 1, back Gaussian 2 on the same ray:
+    C = a1 c1 + (1 - a1) a2 c2 at every pixel both cover."""
+    s1, z1, o1, s2, z2, o2 = 0.06, 2.0, 0.2, 0.09, 3.5, 1.1
+    c1, c2 = np.array([0.9, 0.1, 0.3]), np.array([0.2, 0.8, 0.5])
+    sc = _scene([[0.0, 0, z1], [0.0, 0, z2]], [[math.log(s1)] * 3, [math.log(s2)] * 3],
+                [[1, 0, 0, 0], [0, 0, 1, 0]], [o1, o2], [c1, c2])
+    im = oracle.render(sc, CAM, _ident())
+    for (px, py) in [(64, 48), (66, 47), (60, 50)]:
+        d2 = (px + 0.5 - 64) ** 2 + (py + 0.5 - 48) ** 2
+        a1 = 1 / (1 + math.exp(-o1)) * math.exp(-d2 / (2 * ((100 * s1 / z1) ** 2 + 0.3)))
+        a2 = 1 / (1 + math.exp(-o2)) * math.exp(-d2 / (2 * ((100 * s2 / z2) ** 2 + 0.3)))
+        want = a1 * c1 + (1 - a1) * a2 * c2
+        np.testing.assert_allclose(im["color"][:, py, px], want, rtol=1e-12)
+        np.testing.assert_allclose(im["depth"][py, px], a1 * z1 + (1 - a1) * a2 * z2, rtol=1e-12)
+
+
+def test_projection_of_rotated_anisotropic_gaussian():
+    """Eq. 1-2 at the image centre: for a point on the optical axis J W = (f/z) [I2 | 0]
+    (identity pose), so Sigma_2d = (f/z)^2 [R S^2 R^T]_{2x2} + 0.3 I and the conic is
+    its inverse; checked with an explicit axis-angle rotation (not a quaternion)."""
+    ang, z, f = 0.6, 2.0, 100.0
+    s = np.array([0.02, 0.07, 0.01])
+    # quaternion of a rotation by ang about z
+    q = [math.cos(ang / 2), 0, 0, math.sin(ang / 2)]
+    sc = _scene([[0, 0, z]], [np.log(s)], [q], [0.0], [[1, 1, 1]])
+    pr = oracle.project(sc, CAM, _ident())
+    c, sn = math.cos(ang), math.sin(ang)
+    R2 = np.array([[c, -sn], [sn, c]])
+    cov = (f / z) ** 2 * R2 @ np.diag(s[:2] ** 2) @ R2.T + 0.3 * np.eye(2)
+    inv = np.linalg.inv(cov)
+    np.testing.assert_allclose(pr["conic"][0], [inv[0, 0], inv[0, 1], inv[1, 1]], rtol=1e-12)
+
+
+# ----------------------------------------------------------- invariants (P4)
+@pytest.fixture(scope="module")
+def tiny():
+    sc, cam, T = synth.tiny_scene()
+    _, td = synth.random_targets(cam, 1001 + 50)
+    im = oracle.render(sc, cam, T, obs_depth=td[0])
+    return sc, cam, T, im
+
+
+def test_blend_invariants(tiny):
+    """P4 (Eq. 3-10): O in [0, 1 - 1e-4]; O = 1 - T_final; C <= max(c) O;
+    D_alpha within [zmin O, zmax O]; U >= 0; nu map within [0, max nu * O]."""
+    sc, cam, T, im = tiny
+    O = im["alpha"]
+    assert O.min() >= 0 and O.max() <= 1 - 1e-4 + 1e-15
+    np.testing.assert_allclose(O, 1 - im["T_final"], rtol=0, atol=1e-12)
+    cmax = sc.colors.max(0)
+    for c in range(3):
+        assert np.all(im["color"][c] <= cmax[c] * O + 1e-12)
+    z = sc.means[:, 2].astype(float)
+    assert np.all(im["depth"] <= z.max() * O + 1e-12) and np.all(im["depth"] >= z.min() * O - 1e-12)
+    assert im["unc"].min() >= 0
+    assert np.all(im["nu_map"] <= sc.nu.max() * O + 1e-12)
+    assert im["n_contrib"].max() > 20
+
+
+def test_uniform_color_equals_color_times_opacity(tiny):
+    """Eq. 3 and 9: with every Gaussian coloured c the image is c * O."""
+    sc, cam, T, _ = tiny
+    sc2 = synth.Scene(sc.means, sc.log_scales, sc.quats, sc.opacity_logit,
+                      np.tile(np.array([0.25, 0.5, 0.75], np.float32), (sc.n, 1)), sc.nu)
+    im = oracle.render(sc2, cam, T)
+    for c, v in enumerate([0.25, 0.5, 0.75]):
+        np.testing.assert_allclose(im["color"][c], v * im["alpha"], rtol=1e-13, atol=1e-15)
+
+
+def test_brute_force_equals_rect_scatter(tiny):
+    """P6: per-pixel brute force over all Gaussians and the rect-scatter lists give
+    bit-identical FP64 images."""
+    sc, cam, T, im = tiny
+    _, td = synth.random_targets(cam, 1001 + 50)
+    im2 = oracle.render(sc, cam, T, obs_depth=td[0], mode="brute")
+    for k in im:
+        assert np.array_equal(im[k], im2[k]), k
+
+
+def test_sampled_pixels_equal_full_image(tiny):
+    sc, cam, T, im = tiny
+    _, td = synth.random_targets(cam, 1001 + 50)
+    pix = np.random.default_rng(0).choice(cam.width * cam.height, 300, replace=False)
+    s = oracle.render_pixels(sc, cam, T, pix, obs_depth=td[0])
+    for k in ("depth", "alpha", "unc", "nu_map", "median", "T_final"):
+        assert np.array_equal(s[k], im[k].reshape(-1)[pix]), k
+    assert np.array_equal(s["color"], im["color"].reshape(3, -1)[:, pix])
+
+
+def test_stop_rule_never_lets_T_below_1e4():
+    """The blend stops before an entry that would take T below 1e-4: a deep stack
+    of nearly opaque Gaussians on the optical axis keeps two entries at the
+    centre pixel, T_final = (1-a1)(1-a2) >= 1e-4 while (1-a3) T_final < 1e-4."""
+    n, s, sig = 30, 0.2, 0.97
+    z = np.linspace(2, 3, n)
+    sc = _scene(np.c_[np.zeros(n), np.zeros(n), z], np.full((n, 3), math.log(s)),
+                np.tile([1.0, 0, 0, 0], (n, 1)), np.full(n, math.log(sig / (1 - sig))), np.full((n, 3), 0.5))
+    im = oracle.render(sc, CAM, _ident())
+    assert im["T_final"].min() >= 1e-4
+    a = [sig * math.exp(-0.25 / ((100 * s / zk) ** 2 + 0.3)) for zk in z[:3]]
+    assert im["n_contrib"][48, 64] == 2
+    np.testing.assert_allclose(im["T_final"][48, 64], (1 - a[0]) * (1 - a[1]), rtol=1e-12)
+    assert (1 - a[2]) * im["T_final"][48, 64] < 1e-4
+
+
+# ----------------------------------------------------------- binning (Sec. 3.1 pre-sort)
+def test_oracle_tile_binning_counts_and_order():
+    """P7 (oracle side): every record is listed in exactly the tiles of its tile
+    rectangle (count = closed form (x1//t - x0//t + 1)(y1//t - y0//t + 1)), each
+    tile's list is sorted by (depth bits, record index), and the ranges cover it."""
+    rng = np.random.default_rng(5)
+    n, t = 500, 16
+    cam = synth.Camera(200, 120, 1, 1, 0, 0)
+    x0 = rng.integers(0, 200, n)
+    y0 = rng.integers(0, 120, n)
+    rect = np.c_[x0, y0, np.minimum(199, x0 + rng.integers(0, 40, n)), np.minimum(119, y0 + rng.integers(0, 40, n))]
+    rect[::17] = [1, 1, 0, 0]  # culled
+    depth = rng.choice(np.float32([0.5, 1.0, 2.0, 3.0]), n)  # many exact ties
+    keys, vals, ranges = oracle.bin_tiles(rect, depth, n, t, [cam])
+    cnt = np.bincount(vals, minlength=n)
+    want = np.where(rect[:, 0] > rect[:, 2], 0,
+                    (rect[:, 2] // t - rect[:, 0] // t + 1) * (rect[:, 3] // t - rect[:, 1] // t + 1))
+    assert np.array_equal(cnt, want)
+    tiles = (keys >> np.uint64(32)).astype(np.int64)
+    for tid in range(ranges.shape[0]):
+        a, b = ranges[tid]
+        assert np.all(tiles[a:b] == tid)
+        zb = (keys[a:b] & np.uint64(0xFFFFFFFF)).astype(np.int64)
+        order = np.lexsort((vals[a:b], zb))
+        assert np.array_equal(order, np.arange(b - a))
+    assert ranges[:, 1].max() == len(keys)
+
+
+# ----------------------------------------------------------- pose update
+def test_adam_first_step_is_signed_learning_rate():
+    """Adam's first step has mhat = g, vhat = g^2, so each coordinate moves by
+    -lr * sign(g) (Sec. 4 learning rates {0.0015 rot, 0.00215 trans}); the rotation
+    part stays orthonormal."""
+    st = np.zeros(25)
+    st[:9] = np.eye(3).reshape(-1)
+    st[9:12] = [0.3, -0.2, 1.0]
+    g = np.array([2.0, -3.0, 0.5, 0.0, 0.0, 0.0])
+    oracle.adam_step(st, g, lr_rot=0.0015, lr_trans=0.00215, eps=1e-12)
+    np.testing.assert_allclose(st[9:12], [0.3 - 0.00215, -0.2 + 0.00215, 1.0 - 0.00215], rtol=0, atol=1e-12)
+    # rotation-only gradient about z (t = 0 so the {so(3)|T} conversion is the identity)
+    st = np.zeros(25)
+    st[:9] = np.eye(3).reshape(-1)
+    oracle.adam_step(st, np.array([0, 0, 0, 0, 0, -1.0]), eps=1e-12)
+    th = 0.0015
+    want = np.array([[math.cos(th), -math.sin(th), 0], [math.sin(th), math.cos(th), 0], [0, 0, 1]])
+    np.testing.assert_allclose(st[:9].reshape(3, 3), want, atol=1e-15)
