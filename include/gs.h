@@ -1,0 +1,252 @@
+/*
+ * gs.h -- C ABI of libgs, a B300 (sm_103a) implementation of the
+ * differentiable tile-based 3D Gaussian rasterizer that CG-SLAM
+ * (arXiv 2403.16095) runs in every tracking and mapping iteration.
+ *
+ * Pipeline for one iteration (all calls asynchronous on one CUDA stream, no
+ * host synchronisation, no allocation -- the sequence can be captured in a
+ * CUDA graph):
+ *
+ *   gs_project          Eq. 1-2   activate parameters, EWA-project each Gaussian
+ *   gs_bin_tiles        Sec. 3.1  duplicate per overlapped tile, radix-sort the
+ *                                 64-bit (tile id, depth) keys, tile ranges
+ *   gs_render_fwd       Eq. 3-10  front-to-back alpha blending per pixel
+ *   gs_render_bwd       Eq. 3-10 adjoint (+ Eq. 14/16/19 loss when fused):
+ *                                 reverse walk of each tile list; gradients to the
+ *                                 pose (POSE mode) or to every Gaussian parameter
+ *                                 and the pose (FULL mode)
+ *   gs_pose_grad_reduce Sec. 3.4  deterministic FP64 sum of the pose partials
+ *   gs_pose_adam_step   Sec. 3.4/4 one Adam step of the pose in {so(3)|T} form
+ *
+ * Conventions shared by every call
+ *   - Memory: the caller owns every buffer. Pointers documented "device" must
+ *     be device memory of the current device; "host" means host memory read
+ *     during the call only. The library never allocates, frees, or keeps a
+ *     pointer past the call. Scratch space is passed as (ws, ws_bytes) after
+ *     querying the *_workspace_size function.
+ *   - Errors: argument errors return a status synchronously (nothing is
+ *     launched). Conditions only the device can see (pair-buffer overflow) are
+ *     written to the device status word `status` (int32[4]): status[0] is a
+ *     gs_status code (0 = OK), status[1] the number of (Gaussian, tile) pairs
+ *     the last gs_bin_tiles needed. Every kernel reads status[0] first and does
+ *     nothing if it is non-zero, so a failed iteration never reads past a
+ *     buffer. The caller zeroes the status word (e.g. per frame). A failed CUDA
+ *     launch returns GS_ERR_CUDA. gs_last_error() gives a message for the last
+ *     non-OK status returned on the calling host thread.
+ *   - Camera: pinhole intrinsics, world->camera pose T_cw = [R | t] (3x4
+ *     row-major float), camera axes x right, y down, z forward. Pixel (i, j)
+ *     (column i, row j) has its centre at (i + 0.5, j + 0.5).
+ *   - Frames: a call may process F frames at once (F <= GS_MAX_FRAMES) with
+ *     their own camera and pose. Records are indexed r = f * n_gaussians + i.
+ *     Images of frame f occupy pixels [pix_off_f, pix_off_f + H_f * W_f) with
+ *     pix_off the exclusive prefix sum of H_f * W_f; a one-channel image is
+ *     [pix][...] = buf[pix_off_f + y * W_f + x]; the colour image is planar per
+ *     frame: buf[3 * pix_off_f + c * H_f * W_f + y * W_f + x] (i.e. [F][3][H][W]
+ *     for equal frames). Tiles of frame f are numbered tile_off_f + ty * tx_f + tx.
+ *   - Threshold constants (prior-art readings where the paper is silent):
+ *     near-plane cull z <= znear, 0.3 px^2 dilation, q <= 9 footprint,
+ *     alpha = min(0.99, opacity * G), entries with alpha < 1/255 skipped,
+ *     blending stops before an entry that would take T below 1e-4.
+ */
+#ifndef GS_H_
+#define GS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GS_MAX_FRAMES 64
+#define GS_ABI_VERSION 1
+
+typedef struct CUstream_st *gs_stream; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = 1,   /* bad pointer, size, alignment or option            */
+    GS_ERR_CAPACITY = 2,      /* pair buffer too small; status[1] holds the need   */
+    GS_ERR_CUDA = 3,          /* a CUDA runtime call or launch failed              */
+    GS_ERR_TIMEOUT = 4,       /* a bounded device wait gave up                     */
+    GS_ERR_UNSUPPORTED = 5    /* option combination not built                      */
+} gs_status;
+
+enum { GS_MODE_FWD = 0, GS_MODE_POSE = 1, GS_MODE_FULL = 2 };
+
+/* Pinhole camera of one frame (host struct). */
+typedef struct {
+    int width, height;     /* pixels, 1..16384                                  */
+    float fx, fy, cx, cy;  /* focal lengths and principal point in pixels       */
+    float znear;           /* Gaussians with camera z <= znear are culled       */
+} gs_camera;
+
+/* Gaussian parameters (Eq. 1), FP32, device, row-major, [n][k]. */
+typedef struct {
+    int n;                      /* number of Gaussians                          */
+    const float *means;         /* [n][3] world-space centres X                 */
+    const float *log_scales;    /* [n][3] s = exp(log_scale)                    */
+    const float *quats;         /* [n][4] (w,x,y,z), normalised inside; |q|=0 culls */
+    const float *opacity_logit; /* [n]    opacity = sigmoid(logit)              */
+    const float *colors;        /* [n][3] RGB (degree-0 colour used as is)      */
+    const float *nu;            /* [n]    per-Gaussian uncertainty (Eq. 13)     */
+} gs_gaussians;
+
+typedef struct {
+    int tile;        /* tile edge in pixels: 8, 16 or 32                         */
+    int mode;        /* GS_MODE_FWD / GS_MODE_POSE / GS_MODE_FULL                 */
+    float jclamp;    /* clamp of x/z, y/z in the EWA Jacobian, in units of the half
+                        field of view (1.3 typical); <= 0 disables the clamp       */
+    float nu_cull;   /* > 0: Gaussians with nu > nu_cull are culled (Sec. 3.2);
+                        <= 0: off                                                  */
+} gs_opts;
+
+/* Projected records (output of gs_project), device, caller-allocated.
+ * rec: GS_REC_FLOATS floats per record, 16-byte aligned:
+ *   [0..1] mean2d (pixels)   [2..4] conic (A, B, C): q = A dx^2 + 2B dx dy + C dy^2
+ *   [5] opacity  [6] depth z  [7] nu  [8..10] RGB  [11] radius (pixels)
+ *   [12..15] int32 inclusive pixel rect x0, y0, x1, y1 (x0 > x1: culled).       */
+#define GS_REC_FLOATS 16
+#define GS_JAC_FLOATS 36
+typedef struct {
+    int n_gaussians;      /* N                                                 */
+    int n_frames;         /* F; records = F * N                                */
+    float *rec;           /* [F*N][16]                                         */
+    int *tiles_touched;   /* [F*N] tiles overlapped (0 if culled)              */
+    float *pose_jac;      /* [F*N][6][6] d(mean2d.x, mean2d.y, A, B, C, z)/d(rho, phi),
+                             written in POSE mode only; may be NULL otherwise    */
+} gs_projected;
+
+/* Tile lists (output of gs_bin_tiles), device, caller-allocated. */
+typedef struct {
+    int capacity;         /* pairs the value/key buffers hold                  */
+    int n_tiles;          /* sum over frames of tiles_x * tiles_y              */
+    uint32_t *values;     /* [capacity] record index of each pair, sorted by
+                             (tile id, float bits of depth, record index)      */
+    uint64_t *keys;       /* [capacity] sorted keys (tile << 32 | depth bits), or NULL */
+    uint32_t *ranges;     /* [n_tiles][2] [start, end) of each tile's pairs    */
+} gs_tiles;
+
+/* Rendered channels (Eq. 3-10), device, FP32 except n_last. A NULL member is not
+ * written; color, T_final and n_last are required. */
+typedef struct {
+    float *color;    /* [.][3][H][W] Eq. 3                                       */
+    float *depth;    /* alpha-blended depth, Eq. 6 (not normalised by opacity)   */
+    float *alpha;    /* accumulated opacity, Eq. 9                               */
+    float *unc;      /* depth uncertainty U, Eq. 10 (needs obs_depth)            */
+    float *nu_map;   /* blended per-Gaussian uncertainty sum w_i nu_i            */
+    float *median;   /* median depth, Eq. 7-8 (0 if T never drops below 0.5)     */
+    float *T_final;  /* transmittance after the last blended Gaussian            */
+    int32_t *n_last; /* one past the tile-list position of the last blended entry */
+} gs_image;
+
+/* Upstream gradients dL/d(channel) per pixel (same layouts); NULL = zero. */
+typedef struct {
+    const float *color, *depth, *alpha, *unc, *nu_map;
+} gs_image_grad;
+
+/* Fused per-pixel loss (Eq. 14, 16, 19; Eq. 11 optional), per frame f:
+ *   L_f = 1/(H W) sum_p [ m_p (w_color sum_c |C - C*| + w_depth |D - D*|)
+ *                          + w_unc |U| + w_nu nu_map ],
+ *   m_p = 1 / (1 + nu_map_p / unc_tau) if unc_tau > 0 else 1 (no gradient through m).
+ * The total loss is sum_f L_f. sign(0) = 0. */
+typedef struct {
+    float w_color, w_depth, w_unc, w_nu, unc_tau;
+    const float *target_color;  /* [.][3][H][W] device                        */
+    const float *target_depth;  /* [.][H][W] device (also the sensor depth of U) */
+} gs_loss;
+
+/* Parameter gradients (FULL mode), device, same layouts as gs_gaussians,
+ * summed over frames; overwritten (not accumulated). NULL member = skipped. */
+typedef struct {
+    float *means, *log_scales, *quats, *opacity_logit, *colors, *nu;
+} gs_grads;
+
+/* Adam hyper-parameters of the pose step (Sec. 4: lr_rot 0.0015, lr_trans 0.00215). */
+typedef struct {
+    float lr_rot, lr_trans, beta1, beta2, eps;
+} gs_adam;
+
+#define GS_POSE_STATE_DOUBLES 25  /* R[9], t[3], m[6], v[6], step */
+
+/* ------------------------------------------------------------------ calls */
+
+/* ABI version and a message for the last non-OK status on this host thread. */
+int gs_abi_version(void);
+const char *gs_last_error(void);
+
+/* Eq. 1-2. For each frame f and Gaussian i: s = exp(ls), q_hat = q/|q|,
+ * Sigma = R S S^T R^T, opacity = sigmoid(logit); p = R_cw X + t_cw, cull
+ * z <= znear; J = [[fx/z, 0, -fx u/z], [0, fy/z, -fy v/z]] with (u, v) = (x/z, y/z)
+ * clamped to +-jclamp * (W/2fx, H/2fy); Sigma_2d = J R_cw Sigma R_cw^T J^T + 0.3 I,
+ * conic = Sigma_2d^-1; mean2d = (fx x/z + cx, fy y/z + cy);
+ * radius = ceil(3 sqrt(lambda_max)); pixel rect = [ceil(mx - .5 - r), floor(mx - .5 + r)]
+ * clipped to the image (same in y); tiles_touched = area of the tile rect.
+ * In POSE mode also writes pose_jac (forward-mode derivative of mean2d, conic and
+ * z w.r.t. a left perturbation Exp(xi) T_cw, xi = (rho, phi)).
+ *   cams: host [n_frames]; T_cw: device [n_frames][3][4].                    */
+gs_status gs_project(const gs_gaussians *g, int n_frames, const gs_camera *cams, const float *T_cw,
+                     const gs_opts *opts, gs_projected *out, const int32_t *status, gs_stream stream);
+
+/* Sec. 3.1 pre-sort. Emits one (key, record) pair per tile overlapped by each
+ * record's tile rect, key = (global tile id << 32) | float bits of z, sorts the
+ * pairs by key with a stable LSD radix sort (ties keep record order) and writes
+ * each tile's [start, end). The result is bit-exact and independent of the
+ * launch configuration. If the pairs exceed tiles->capacity, status[0] is set to
+ * GS_ERR_CAPACITY and status[1] to the pairs needed; later kernels then no-op.
+ *   status: device int32[4]; ws: device scratch of
+ *   gs_bin_tiles_workspace_size(records, capacity) bytes, 256-byte aligned.   */
+size_t gs_bin_tiles_workspace_size(int n_records, int capacity);
+gs_status gs_bin_tiles(const gs_projected *proj, int n_frames, const gs_camera *cams,
+                       const gs_opts *opts, gs_tiles *tiles, int32_t *status, void *ws,
+                       size_t ws_bytes, gs_stream stream);
+
+/* Eq. 3-10. One CTA per tile: the tile's sorted list is staged in shared memory
+ * in batches and every pixel blends front to back (alpha test, stop rule,
+ * median crossing of T = 0.5) until all of the tile's pixels are done.
+ *   obs_depth: device [.][H][W] sensor depth D for U (Eq. 10), or NULL (U not written). */
+gs_status gs_render_fwd(const gs_projected *proj, const gs_tiles *tiles, int n_frames,
+                        const gs_camera *cams, const float *obs_depth, const gs_opts *opts,
+                        gs_image *out, const int32_t *status, gs_stream stream);
+
+/* Adjoint of gs_render_fwd. Each tile's list is walked back to front from the
+ * last blended entry, recovering T_i = T_{i+1} / (1 - alpha_i) instead of
+ * storing it. Per-pixel dL/d(channel) come from `dL` or, when `loss` is not
+ * NULL, from the fused loss above (dL is then ignored).
+ *   POSE mode: every pixel contracts its gradient w.r.t. (mean2d, conic, z) of
+ *     each blended Gaussian with that record's pose_jac and the tile's pixels
+ *     are reduced by warp shuffles and a block tree into one FP64 partial per
+ *     tile: pose_partials[f][local tile][6].
+ *   FULL mode: per-record gradients of (mean2d, conic, opacity, z, nu, RGB) are
+ *     accumulated (warp-reduced, then atomics), chained through the projection
+ *     to `grads` (needs `g` and T_cw) and the pose partials of each block of 256
+ *     records are written to pose_partials[f][block][6].
+ * Unused partial slots are zeroed. ws: gs_render_bwd_workspace_size bytes.  */
+int gs_pose_partials_per_frame(int mode, int n_gaussians, int n_frames, const gs_camera *cams, int tile);
+size_t gs_render_bwd_workspace_size(int n_records, int mode);
+gs_status gs_render_bwd(const gs_projected *proj, const gs_tiles *tiles, int n_frames,
+                        const gs_camera *cams, const float *T_cw, const gs_gaussians *g,
+                        const float *obs_depth, const gs_image *fwd, const gs_image_grad *dL,
+                        const gs_loss *loss, const gs_opts *opts, gs_grads *grads,
+                        double *pose_partials, const int32_t *status, void *ws, size_t ws_bytes,
+                        gs_stream stream);
+
+/* Deterministic pose-gradient reduction (Sec. 3.4): pose_grad[f][k] =
+ * sum_j partials[f][j][k] in FP64 with Neumaier compensation and a fixed
+ * reduction tree (bit-identical across runs). pose_grad: device [n_frames][6],
+ * (rho, phi) of the left perturbation Exp(xi) T_cw.                          */
+gs_status gs_pose_grad_reduce(const double *partials, int n_frames, int per_frame,
+                              double *pose_grad, const int32_t *status, gs_stream stream);
+
+/* One Adam step per frame on the pose in the {so(3) | T} form of Sec. 3.4:
+ * g_t = g_rho, g_R = g_phi - t x g_rho; d = -lr * mhat / (sqrt(vhat) + eps);
+ * R <- Exp(d_R) R, t <- t + d_t; the FP64 state (GS_POSE_STATE_DOUBLES per frame:
+ * R, t, Adam moments, step count) is updated in place and T_cw (float [F][3][4])
+ * rewritten for the next gs_project.                                         */
+gs_status gs_pose_adam_step(double *state, const double *pose_grad, float *T_cw, int n_frames,
+                            const gs_adam *adam, const int32_t *status, gs_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS_H_ */

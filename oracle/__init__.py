@@ -165,7 +165,7 @@ def _image_bufs(n_pix, H=None, W=None):
     shp = (n_pix,) if H is None else (H, W)
     o = dict(color=np.zeros((3, *shp)), depth=np.zeros(shp), alpha=np.zeros(shp), unc=np.zeros(shp),
              nu_map=np.zeros(shp), median=np.zeros(shp), T_final=np.zeros(shp),
-             n_contrib=np.zeros(shp, np.int32), margins=np.zeros((5, *shp)))
+             n_contrib=np.zeros(shp, np.int32), margins=np.zeros((6, *shp)))
     im = _Image(*(_p(o[k], _ip if k == "n_contrib" else _dp) for k in
                   ("color", "depth", "alpha", "unc", "nu_map", "median", "T_final", "n_contrib", "margins")))
     return o, im
@@ -174,7 +174,8 @@ def _image_bufs(n_pix, H=None, W=None):
 def render(scene, cam, T, obs_depth=None, mode="rect", jclamp=1.3, nu_cull=0.0):
     """Full image, FP64. mode 'rect' (rect-scatter lists) or 'brute' (scan every
     Gaussian per pixel). Returns planar arrays: color [3,H,W], others [H,W];
-    margins [5,H,W] are the per-pixel decision margins."""
+    margins [6,H,W] are the per-pixel decision margins (q vs 9, alpha vs 1/255,
+    T' vs 1e-4, opacity*G vs 0.99, relative depth gap of neighbours, T' vs 0.5)."""
     k = _Keep(scene)
     Tc = _f64(T).reshape(3, 4)
     od = None if obs_depth is None else _f64(obs_depth)

@@ -68,7 +68,7 @@ typedef struct {
 typedef struct { /* optional outputs; NULL members are skipped */
     double *color, *depth, *alpha, *unc, *nu_map, *median, *T_final; /* color [3][H][W] */
     int *n_contrib;
-    double *margins; /* [5][H][W]: q-9, alpha-1/255, T'-1e-4, opacity*G-0.99, depth gap */
+    double *margins; /* [6][H][W]: q-9, alpha-1/255, T'-1e-4, opacity*G-0.99, depth gap, T'-0.5 */
 } orc_image;
 
 typedef struct { /* gradient outputs; NULL members are skipped */
@@ -247,7 +247,7 @@ typedef struct { int k; double alpha, T, G, dx, dy; int clamped; } contrib;
 typedef struct {
     double color[3], depth, alpha, unc, nu, median, T;
     int n;
-    double margin[5];
+    double margin[6];
     uint64_t hash;
 } pixout;
 
@@ -260,7 +260,7 @@ static uint64_t fnv(uint64_t h, uint64_t v) {
 static void blend_pixel(const orc_scene *sc, const gproj *G, const zent *list, int nl, int px, int py,
                         double Dp, int has_D, pixout *o, contrib *cb) {
     memset(o, 0, sizeof(*o));
-    for (int k = 0; k < 5; ++k) o->margin[k] = INFINITY;
+    for (int k = 0; k < 6; ++k) o->margin[k] = INFINITY;
     o->hash = 1469598103934665603ULL;
     double T = 1.0;
     double prev_z = -1.0;
@@ -290,6 +290,8 @@ static void blend_pixel(const orc_scene *sc, const gproj *G, const zent *list, i
         double mt = fabs(Tn - 1e-4) / 1e-4;
         if (mt < o->margin[2]) o->margin[2] = mt;
         if (Tn < 1e-4) { o->hash = fnv(o->hash, 0xffffffffULL); break; }
+        double mh = fabs(Tn - 0.5) / 0.5;
+        if (mh < o->margin[5]) o->margin[5] = mh;
         double w = a * T;
         for (int c = 0; c < 3; ++c) o->color[c] += w * sc->colors[3 * k + c];
         o->depth += w * g->p[2];
@@ -336,7 +338,7 @@ static void store_pixel(orc_image *im, int HW, int p, const pixout *o) {
     if (im->median) im->median[p] = o->median;
     if (im->T_final) im->T_final[p] = o->T;
     if (im->n_contrib) im->n_contrib[p] = o->n;
-    if (im->margins) for (int k = 0; k < 5; ++k) im->margins[k * HW + p] = o->margin[k];
+    if (im->margins) for (int k = 0; k < 6; ++k) im->margins[k * HW + p] = o->margin[k];
 }
 
 /* ---------------------------------------------------------------- loss */

@@ -1,0 +1,291 @@
+"""ctypes binding of libgs (include/gs.h): argument marshalling only.
+
+Each public function has the name of the C entry point it calls and takes
+torch tensors (device memory) plus small Python/ctypes structs; it checks
+dtype, device, contiguity and size, passes raw pointers through, and raises
+``GsError`` with ``gs_last_error()`` if the call returns a non-OK status.
+There is no fallback: if libgs.so is missing the import fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libgs.so")
+
+GS_MAX_FRAMES = 64
+GS_REC_FLOATS = 16
+GS_JAC_FLOATS = 36
+GS_POSE_STATE_DOUBLES = 25
+GS_MODE_FWD, GS_MODE_POSE, GS_MODE_FULL = 0, 1, 2
+GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_UNSUPPORTED = range(6)
+STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CAPACITY", 3: "GS_ERR_CUDA",
+                4: "GS_ERR_TIMEOUT", 5: "GS_ERR_UNSUPPORTED"}
+
+
+class GsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_fp = C.POINTER(C.c_float)
+_dp = C.POINTER(C.c_double)
+_vp = C.c_void_p
+
+
+class gs_camera(C.Structure):
+    _fields_ = [("width", C.c_int), ("height", C.c_int), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("znear", C.c_float)]
+
+
+class gs_gaussians(C.Structure):
+    _fields_ = [("n", C.c_int), ("means", _vp), ("log_scales", _vp), ("quats", _vp),
+                ("opacity_logit", _vp), ("colors", _vp), ("nu", _vp)]
+
+
+class gs_opts(C.Structure):
+    _fields_ = [("tile", C.c_int), ("mode", C.c_int), ("jclamp", C.c_float), ("nu_cull", C.c_float)]
+
+
+class gs_projected(C.Structure):
+    _fields_ = [("n_gaussians", C.c_int), ("n_frames", C.c_int), ("rec", _vp), ("tiles_touched", _vp),
+                ("pose_jac", _vp)]
+
+
+class gs_tiles(C.Structure):
+    _fields_ = [("capacity", C.c_int), ("n_tiles", C.c_int), ("values", _vp), ("keys", _vp), ("ranges", _vp)]
+
+
+class gs_image(C.Structure):
+    _fields_ = [("color", _vp), ("depth", _vp), ("alpha", _vp), ("unc", _vp), ("nu_map", _vp),
+                ("median", _vp), ("T_final", _vp), ("n_last", _vp)]
+
+
+class gs_image_grad(C.Structure):
+    _fields_ = [("color", _vp), ("depth", _vp), ("alpha", _vp), ("unc", _vp), ("nu_map", _vp)]
+
+
+class gs_loss(C.Structure):
+    _fields_ = [("w_color", C.c_float), ("w_depth", C.c_float), ("w_unc", C.c_float), ("w_nu", C.c_float),
+                ("unc_tau", C.c_float), ("target_color", _vp), ("target_depth", _vp)]
+
+
+class gs_grads(C.Structure):
+    _fields_ = [("means", _vp), ("log_scales", _vp), ("quats", _vp), ("opacity_logit", _vp),
+                ("colors", _vp), ("nu", _vp)]
+
+
+class gs_adam(C.Structure):
+    _fields_ = [("lr_rot", C.c_float), ("lr_trans", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
+                ("eps", C.c_float)]
+
+
+EXPORTS = ("gs_abi_version", "gs_last_error", "gs_project", "gs_bin_tiles_workspace_size", "gs_bin_tiles",
+           "gs_render_fwd", "gs_pose_partials_per_frame", "gs_render_bwd_workspace_size", "gs_render_bwd",
+           "gs_pose_grad_reduce", "gs_pose_adam_step")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libgs.so not built at {LIB_PATH}; run `python -m paper_2403_16095_b300.build`")
+    lib = C.CDLL(LIB_PATH)
+    lib.gs_abi_version.restype = C.c_int
+    lib.gs_last_error.restype = C.c_char_p
+    lib.gs_project.argtypes = [C.POINTER(gs_gaussians), C.c_int, C.POINTER(gs_camera), _vp,
+                               C.POINTER(gs_opts), C.POINTER(gs_projected), _vp, _vp]
+    lib.gs_bin_tiles_workspace_size.argtypes = [C.c_int, C.c_int]
+    lib.gs_bin_tiles_workspace_size.restype = C.c_size_t
+    lib.gs_bin_tiles.argtypes = [C.POINTER(gs_projected), C.c_int, C.POINTER(gs_camera), C.POINTER(gs_opts),
+                                 C.POINTER(gs_tiles), _vp, _vp, C.c_size_t, _vp]
+    lib.gs_render_fwd.argtypes = [C.POINTER(gs_projected), C.POINTER(gs_tiles), C.c_int, C.POINTER(gs_camera),
+                                  _vp, C.POINTER(gs_opts), C.POINTER(gs_image), _vp, _vp]
+    lib.gs_pose_partials_per_frame.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(gs_camera), C.c_int]
+    lib.gs_pose_partials_per_frame.restype = C.c_int
+    lib.gs_render_bwd_workspace_size.argtypes = [C.c_int, C.c_int]
+    lib.gs_render_bwd_workspace_size.restype = C.c_size_t
+    lib.gs_render_bwd.argtypes = [C.POINTER(gs_projected), C.POINTER(gs_tiles), C.c_int, C.POINTER(gs_camera),
+                                  _vp, C.POINTER(gs_gaussians), _vp, C.POINTER(gs_image),
+                                  C.POINTER(gs_image_grad), C.POINTER(gs_loss), C.POINTER(gs_opts),
+                                  C.POINTER(gs_grads), _vp, _vp, _vp, C.c_size_t, _vp]
+    lib.gs_pose_grad_reduce.argtypes = [_vp, C.c_int, C.c_int, _vp, _vp, _vp]
+    lib.gs_pose_adam_step.argtypes = [_vp, _vp, _vp, C.c_int, C.POINTER(gs_adam), _vp, _vp]
+    for name in ("gs_project", "gs_bin_tiles", "gs_render_fwd", "gs_render_bwd", "gs_pose_grad_reduce",
+                 "gs_pose_adam_step"):
+        getattr(lib, name).restype = C.c_int
+    return lib
+
+
+lib = _load()
+
+
+def last_error() -> str:
+    return lib.gs_last_error().decode()
+
+
+def _check(st: int) -> None:
+    if st != GS_OK:
+        raise GsError(st, last_error())
+
+
+# ----------------------------------------------------------------- marshalling
+def _ptr(t: Optional[torch.Tensor], dtype=None, name="tensor", numel=None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name} holds {t.numel()} elements, needs {numel}")
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def cameras(cams: Sequence) -> C.Array:
+    arr = (gs_camera * len(cams))()
+    for i, c in enumerate(cams):
+        arr[i] = gs_camera(int(c.width), int(c.height), float(c.fx), float(c.fy), float(c.cx), float(c.cy),
+                           float(getattr(c, "znear", 0.2)))
+    return arr
+
+
+@dataclass
+class Gaussians:
+    """Gaussian parameters as FP32 CUDA tensors ([N,3], [N,3], [N,4], [N], [N,3], [N])."""
+    means: torch.Tensor
+    log_scales: torch.Tensor
+    quats: torch.Tensor
+    opacity_logit: torch.Tensor
+    colors: torch.Tensor
+    nu: torch.Tensor
+
+    @property
+    def n(self) -> int:
+        return int(self.means.shape[0])
+
+    def struct(self) -> gs_gaussians:
+        n = self.n
+        return gs_gaussians(n, _ptr(self.means, torch.float32, "means", 3 * n),
+                            _ptr(self.log_scales, torch.float32, "log_scales", 3 * n),
+                            _ptr(self.quats, torch.float32, "quats", 4 * n),
+                            _ptr(self.opacity_logit, torch.float32, "opacity_logit", n),
+                            _ptr(self.colors, torch.float32, "colors", 3 * n),
+                            _ptr(self.nu, torch.float32, "nu", n))
+
+
+def gs_project(g: Gaussians, cams, T_cw: torch.Tensor, opts: gs_opts, rec: torch.Tensor,
+               tiles_touched: torch.Tensor, pose_jac: Optional[torch.Tensor], status: torch.Tensor,
+               stream=None) -> None:
+    F = len(cams)
+    M = F * g.n
+    proj = gs_projected(g.n, F, _ptr(rec, torch.float32, "rec", M * GS_REC_FLOATS),
+                        _ptr(tiles_touched, torch.int32, "tiles_touched", M),
+                        _ptr(pose_jac, torch.float32, "pose_jac", M * GS_JAC_FLOATS))
+    _check(lib.gs_project(C.byref(g.struct()), F, cameras(cams), _ptr(T_cw, torch.float32, "T_cw", 12 * F),
+                          C.byref(opts), C.byref(proj), _ptr(status, torch.int32, "status", 4), _stream(stream)))
+
+
+def gs_bin_tiles_workspace_size(n_records: int, capacity: int) -> int:
+    return int(lib.gs_bin_tiles_workspace_size(n_records, capacity))
+
+
+def gs_bin_tiles(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tensor, tiles_touched: torch.Tensor,
+                 values: torch.Tensor, keys: Optional[torch.Tensor], ranges: torch.Tensor, status: torch.Tensor,
+                 ws: torch.Tensor, stream=None) -> None:
+    F = len(cams)
+    proj = gs_projected(n_gaussians, F, _ptr(rec, torch.float32, "rec"), _ptr(tiles_touched, torch.int32), None)
+    cap = values.numel()
+    if keys is not None and keys.numel() < cap:
+        raise ValueError("keys must hold as many entries as values")
+    tiles = gs_tiles(cap, ranges.numel() // 2, _ptr(values, torch.int32, "values"),
+                     _ptr(keys, torch.int64, "keys"), _ptr(ranges, torch.int32, "ranges"))
+    _check(lib.gs_bin_tiles(C.byref(proj), F, cameras(cams), C.byref(opts), C.byref(tiles),
+                            _ptr(status, torch.int32, "status", 4), _ptr(ws, torch.uint8, "ws"), ws.numel(),
+                            _stream(stream)))
+
+
+def _image(img: dict) -> gs_image:
+    return gs_image(*(_ptr(img.get(k), torch.int32 if k == "n_last" else torch.float32, k)
+                      for k in ("color", "depth", "alpha", "unc", "nu_map", "median", "T_final", "n_last")))
+
+
+def gs_render_fwd(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tensor, values: torch.Tensor,
+                  ranges: torch.Tensor, obs_depth: Optional[torch.Tensor], out: dict, status: torch.Tensor,
+                  stream=None) -> None:
+    F = len(cams)
+    proj = gs_projected(n_gaussians, F, _ptr(rec, torch.float32, "rec"), 1, None)  # touched unused
+    tiles = gs_tiles(values.numel(), ranges.numel() // 2, _ptr(values, torch.int32), None,
+                     _ptr(ranges, torch.int32))
+    _check(lib.gs_render_fwd(C.byref(proj), C.byref(tiles), F, cameras(cams),
+                             _ptr(obs_depth, torch.float32, "obs_depth"), C.byref(opts), C.byref(_image(out)),
+                             _ptr(status, torch.int32, "status", 4), _stream(stream)))
+
+
+def gs_pose_partials_per_frame(mode: int, n_gaussians: int, cams, tile: int) -> int:
+    return int(lib.gs_pose_partials_per_frame(mode, n_gaussians, len(cams), cameras(cams), tile))
+
+
+def gs_render_bwd_workspace_size(n_records: int, mode: int) -> int:
+    return int(lib.gs_render_bwd_workspace_size(n_records, mode))
+
+
+def gs_render_bwd(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tensor, pose_jac: Optional[torch.Tensor],
+                  values: torch.Tensor, ranges: torch.Tensor, T_cw: Optional[torch.Tensor], g: Optional[Gaussians],
+                  obs_depth: Optional[torch.Tensor], fwd: dict, dL: Optional[dict], loss: Optional[dict],
+                  grads: Optional[dict], pose_partials: torch.Tensor, status: torch.Tensor, ws: torch.Tensor,
+                  stream=None) -> None:
+    F = len(cams)
+    proj = gs_projected(n_gaussians, F, _ptr(rec, torch.float32, "rec"), 1,
+                        _ptr(pose_jac, torch.float32, "pose_jac"))
+    tiles = gs_tiles(values.numel(), ranges.numel() // 2, _ptr(values, torch.int32), None,
+                     _ptr(ranges, torch.int32))
+    gl = None
+    if loss is not None:
+        gl = gs_loss(float(loss.get("w_color", 0.0)), float(loss.get("w_depth", 0.0)), float(loss.get("w_unc", 0.0)),
+                     float(loss.get("w_nu", 0.0)), float(loss.get("unc_tau", 0.0)),
+                     _ptr(loss.get("target_color"), torch.float32, "target_color"),
+                     _ptr(loss.get("target_depth"), torch.float32, "target_depth"))
+    gd = None
+    if dL is not None:
+        gd = gs_image_grad(*(_ptr(dL.get(k), torch.float32, "dL." + k)
+                             for k in ("color", "depth", "alpha", "unc", "nu_map")))
+    gg = None
+    if grads is not None:
+        gg = gs_grads(*(_ptr(grads.get(k), torch.float32, "grads." + k)
+                        for k in ("means", "log_scales", "quats", "opacity_logit", "colors", "nu")))
+    _check(lib.gs_render_bwd(C.byref(proj), C.byref(tiles), F, cameras(cams), _ptr(T_cw, torch.float32, "T_cw"),
+                             C.byref(g.struct()) if g is not None else None,
+                             _ptr(obs_depth, torch.float32, "obs_depth"), C.byref(_image(fwd)),
+                             C.byref(gd) if gd is not None else None, C.byref(gl) if gl is not None else None,
+                             C.byref(opts), C.byref(gg) if gg is not None else None,
+                             _ptr(pose_partials, torch.float64, "pose_partials"),
+                             _ptr(status, torch.int32, "status", 4), _ptr(ws, torch.uint8, "ws"), ws.numel(),
+                             _stream(stream)))
+
+
+def gs_pose_grad_reduce(partials: torch.Tensor, n_frames: int, per_frame: int, pose_grad: torch.Tensor,
+                        status: torch.Tensor, stream=None) -> None:
+    _check(lib.gs_pose_grad_reduce(_ptr(partials, torch.float64, "partials", n_frames * per_frame * 6), n_frames,
+                                   per_frame, _ptr(pose_grad, torch.float64, "pose_grad", 6 * n_frames),
+                                   _ptr(status, torch.int32, "status", 4), _stream(stream)))
+
+
+def gs_pose_adam_step(state: torch.Tensor, pose_grad: torch.Tensor, T_cw: torch.Tensor, n_frames: int,
+                      adam: gs_adam, status: torch.Tensor, stream=None) -> None:
+    _check(lib.gs_pose_adam_step(_ptr(state, torch.float64, "state", GS_POSE_STATE_DOUBLES * n_frames),
+                                 _ptr(pose_grad, torch.float64, "pose_grad", 6 * n_frames),
+                                 _ptr(T_cw, torch.float32, "T_cw", 12 * n_frames), n_frames, C.byref(adam),
+                                 _ptr(status, torch.int32, "status", 4), _stream(stream)))

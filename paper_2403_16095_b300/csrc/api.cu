@@ -1,0 +1,266 @@
+// C ABI entry points of libgs (declared in include/gs.h): argument checks,
+// frame tables and kernel launches. Nothing here allocates memory or
+// synchronises with the host.
+#include <climits>
+#include <cstdarg>
+#include <cstdio>
+
+#include "gs_internal.cuh"
+
+namespace {
+
+thread_local char g_msg[512] = "";
+
+gs_status fail(gs_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+gs_status cuda_status(cudaError_t e, const char *where) {
+    if (e == cudaSuccess) return GS_OK;
+    return fail(GS_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Builds the per-frame table; returns GS_OK or an argument error.
+gs_status make_frames(int n_frames, const gs_camera *cams, int tile, gs::FrameTable &ft) {
+    if (n_frames < 1 || n_frames > GS_MAX_FRAMES) return fail(GS_ERR_INVALID_ARG, "n_frames=%d outside [1,%d]", n_frames, GS_MAX_FRAMES);
+    if (!cams) return fail(GS_ERR_INVALID_ARG, "cams is NULL");
+    if (tile != 8 && tile != 16 && tile != 32) return fail(GS_ERR_INVALID_ARG, "tile=%d not in {8,16,32}", tile);
+    ft.n = n_frames;
+    ft.tile = tile;
+    long long tiles = 0, pix = 0;
+    for (int f = 0; f < n_frames; ++f) {
+        const gs_camera &c = cams[f];
+        if (c.width < 1 || c.height < 1 || c.width > 16384 || c.height > 16384)
+            return fail(GS_ERR_INVALID_ARG, "frame %d: image %dx%d outside 1..16384", f, c.width, c.height);
+        if (!(c.fx > 0.f) || !(c.fy > 0.f) || !(c.znear > 0.f))
+            return fail(GS_ERR_INVALID_ARG, "frame %d: fx, fy and znear must be > 0", f);
+        gs::FrameDesc &d = ft.f[f];
+        d.W = c.width;
+        d.H = c.height;
+        d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy; d.znear = c.znear;
+        d.tiles_x = (c.width + tile - 1) / tile;
+        d.tiles_y = (c.height + tile - 1) / tile;
+        d.tile_off = (int)tiles;
+        d.pix_off = (int)pix;
+        tiles += (long long)d.tiles_x * d.tiles_y;
+        pix += (long long)c.width * c.height;
+        if (tiles > INT_MAX / 2 || pix > INT_MAX / 4) return fail(GS_ERR_INVALID_ARG, "frames too large");
+    }
+    ft.total_tiles = (int)tiles;
+    ft.total_pix = (int)pix;
+    return GS_OK;
+}
+
+gs_status check_opts(const gs_opts *o) {
+    if (!o) return fail(GS_ERR_INVALID_ARG, "opts is NULL");
+    if (o->mode != GS_MODE_FWD && o->mode != GS_MODE_POSE && o->mode != GS_MODE_FULL)
+        return fail(GS_ERR_INVALID_ARG, "mode=%d unknown", o->mode);
+    return GS_OK;
+}
+
+gs_status check_proj(const gs_projected *p, int n_frames) {
+    if (!p) return fail(GS_ERR_INVALID_ARG, "projected is NULL");
+    if (p->n_gaussians < 0) return fail(GS_ERR_INVALID_ARG, "n_gaussians < 0");
+    if (p->n_frames != n_frames) return fail(GS_ERR_INVALID_ARG, "projected.n_frames=%d != n_frames=%d", p->n_frames, n_frames);
+    if ((long long)p->n_gaussians * n_frames > (long long)INT_MAX) return fail(GS_ERR_INVALID_ARG, "records exceed 2^31-1");
+    if (p->n_gaussians > 0 && (!p->rec || !p->tiles_touched)) return fail(GS_ERR_INVALID_ARG, "rec/tiles_touched NULL");
+    if (!aligned(p->rec, 16)) return fail(GS_ERR_INVALID_ARG, "rec must be 16-byte aligned");
+    return GS_OK;
+}
+
+gs::GaussPtrs gauss_ptrs(const gs_gaussians *g) {
+    return gs::GaussPtrs{g->means, g->log_scales, g->quats, g->opacity_logit, g->colors, g->nu};
+}
+
+gs_status check_gauss(const gs_gaussians *g) {
+    if (!g) return fail(GS_ERR_INVALID_ARG, "gaussians is NULL");
+    if (g->n < 0) return fail(GS_ERR_INVALID_ARG, "n < 0");
+    if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logit || !g->colors || !g->nu))
+        return fail(GS_ERR_INVALID_ARG, "a Gaussian parameter pointer is NULL");
+    if (!aligned(g->quats, 16)) return fail(GS_ERR_INVALID_ARG, "quats must be 16-byte aligned");
+    return GS_OK;
+}
+
+gs_status check_tiles(const gs_tiles *t, const gs::FrameTable &ft) {
+    if (!t) return fail(GS_ERR_INVALID_ARG, "tiles is NULL");
+    if (t->capacity < 1) return fail(GS_ERR_INVALID_ARG, "tiles.capacity must be >= 1");
+    if (!t->values || !t->ranges) return fail(GS_ERR_INVALID_ARG, "tiles.values/ranges NULL");
+    if (t->n_tiles != ft.total_tiles) return fail(GS_ERR_INVALID_ARG, "tiles.n_tiles=%d but the frames have %d tiles", t->n_tiles, ft.total_tiles);
+    if (!aligned(t->ranges, 8)) return fail(GS_ERR_INVALID_ARG, "tiles.ranges must be 8-byte aligned");
+    return GS_OK;
+}
+
+#define GS_TRY(expr)                           \
+    do {                                       \
+        const gs_status st__ = (expr);         \
+        if (st__ != GS_OK) return st__;        \
+    } while (0)
+
+constexpr size_t kAlign = 256;
+size_t bwd_ws_bytes(int n_records, int mode) {
+    if (mode != GS_MODE_FULL) return kAlign;
+    return (((size_t)n_records * gs::kGrad2d * sizeof(float)) + kAlign - 1) / kAlign * kAlign;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gs_abi_version(void) { return GS_ABI_VERSION; }
+
+const char *gs_last_error(void) { return g_msg; }
+
+gs_status gs_project(const gs_gaussians *g, int n_frames, const gs_camera *cams, const float *T_cw,
+                     const gs_opts *opts, gs_projected *out, const int32_t *status, gs_stream stream) {
+    GS_TRY(check_gauss(g));
+    GS_TRY(check_opts(opts));
+    gs::FrameTable ft;
+    GS_TRY(make_frames(n_frames, cams, opts->tile, ft));
+    GS_TRY(check_proj(out, n_frames));
+    if (out->n_gaussians != g->n) return fail(GS_ERR_INVALID_ARG, "projected.n_gaussians != gaussians.n");
+    if (!T_cw || !status) return fail(GS_ERR_INVALID_ARG, "T_cw/status NULL");
+    if (opts->mode == GS_MODE_POSE && (!out->pose_jac || !aligned(out->pose_jac, 16)))
+        return fail(GS_ERR_INVALID_ARG, "POSE mode needs a 16-byte aligned pose_jac");
+    return cuda_status(gs::launch_project(gauss_ptrs(g), g->n, ft, T_cw, opts->jclamp, opts->nu_cull, opts->mode,
+                                          out->rec, out->tiles_touched, out->pose_jac, status, stream),
+                       "gs_project");
+}
+
+size_t gs_bin_tiles_workspace_size(int n_records, int capacity) {
+    if (n_records < 0 || capacity < 1) return 0;
+    return gs::bin_workspace_bytes(n_records, capacity);
+}
+
+gs_status gs_bin_tiles(const gs_projected *proj, int n_frames, const gs_camera *cams, const gs_opts *opts,
+                       gs_tiles *tiles, int32_t *status, void *ws, size_t ws_bytes, gs_stream stream) {
+    GS_TRY(check_opts(opts));
+    gs::FrameTable ft;
+    GS_TRY(make_frames(n_frames, cams, opts->tile, ft));
+    GS_TRY(check_proj(proj, n_frames));
+    GS_TRY(check_tiles(tiles, ft));
+    if (!status) return fail(GS_ERR_INVALID_ARG, "status NULL");
+    const int M = proj->n_gaussians * n_frames;
+    const size_t need = gs::bin_workspace_bytes(M, tiles->capacity);
+    if (!ws || ws_bytes < need) return fail(GS_ERR_INVALID_ARG, "workspace %zu bytes < %zu needed", ws_bytes, need);
+    if (!aligned(ws, 256)) return fail(GS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    const int npf = proj->n_gaussians > 0 ? proj->n_gaussians : 1;
+    return cuda_status(gs::launch_bin_tiles(proj->rec, proj->tiles_touched, M, npf, ft, tiles->capacity, tiles->values,
+                                            tiles->keys, tiles->ranges, status, ws, stream),
+                       "gs_bin_tiles");
+}
+
+gs_status gs_render_fwd(const gs_projected *proj, const gs_tiles *tiles, int n_frames, const gs_camera *cams,
+                        const float *obs_depth, const gs_opts *opts, gs_image *out, const int32_t *status,
+                        gs_stream stream) {
+    GS_TRY(check_opts(opts));
+    gs::FrameTable ft;
+    GS_TRY(make_frames(n_frames, cams, opts->tile, ft));
+    GS_TRY(check_proj(proj, n_frames));
+    GS_TRY(check_tiles(tiles, ft));
+    if (!out || !out->color || !out->T_final || !out->n_last) return fail(GS_ERR_INVALID_ARG, "image color/T_final/n_last required");
+    if (!status) return fail(GS_ERR_INVALID_ARG, "status NULL");
+    gs::ImagePtrs ip{out->color, out->depth, out->alpha, out->unc, out->nu_map, out->median, out->T_final, out->n_last};
+    return cuda_status(gs::launch_render_fwd(proj->rec, tiles->values, tiles->ranges, ft, obs_depth, ip, status, stream),
+                       "gs_render_fwd");
+}
+
+int gs_pose_partials_per_frame(int mode, int n_gaussians, int n_frames, const gs_camera *cams, int tile) {
+    if (mode == GS_MODE_FULL) return n_gaussians > 0 ? (n_gaussians + 255) / 256 : 1;
+    if (!cams || n_frames < 1 || (tile != 8 && tile != 16 && tile != 32)) return 0;
+    int mx = 1;
+    for (int f = 0; f < n_frames; ++f) {
+        const int t = ((cams[f].width + tile - 1) / tile) * ((cams[f].height + tile - 1) / tile);
+        if (t > mx) mx = t;
+    }
+    return mx;
+}
+
+size_t gs_render_bwd_workspace_size(int n_records, int mode) { return bwd_ws_bytes(n_records, mode); }
+
+gs_status gs_render_bwd(const gs_projected *proj, const gs_tiles *tiles, int n_frames, const gs_camera *cams,
+                        const float *T_cw, const gs_gaussians *g, const float *obs_depth, const gs_image *fwd,
+                        const gs_image_grad *dL, const gs_loss *loss, const gs_opts *opts, gs_grads *grads,
+                        double *pose_partials, const int32_t *status, void *ws, size_t ws_bytes, gs_stream stream) {
+    GS_TRY(check_opts(opts));
+    const int mode = opts->mode;
+    if (mode != GS_MODE_POSE && mode != GS_MODE_FULL) return fail(GS_ERR_INVALID_ARG, "backward needs POSE or FULL mode");
+    gs::FrameTable ft;
+    GS_TRY(make_frames(n_frames, cams, opts->tile, ft));
+    GS_TRY(check_proj(proj, n_frames));
+    GS_TRY(check_tiles(tiles, ft));
+    if (!status || !pose_partials) return fail(GS_ERR_INVALID_ARG, "status/pose_partials NULL");
+    if (!fwd || !fwd->T_final || !fwd->n_last) return fail(GS_ERR_INVALID_ARG, "forward T_final/n_last required");
+    gs::LossParams lp{};
+    if (loss) {
+        lp.fused = 1;
+        lp.w_color = loss->w_color; lp.w_depth = loss->w_depth; lp.w_unc = loss->w_unc;
+        lp.w_nu = loss->w_nu; lp.unc_tau = loss->unc_tau;
+        lp.target_color = loss->target_color; lp.target_depth = loss->target_depth;
+        if (lp.w_color != 0.f && (!fwd->color || !lp.target_color)) return fail(GS_ERR_INVALID_ARG, "colour loss needs fwd.color and target_color");
+        if (lp.w_depth != 0.f && (!fwd->depth || !lp.target_depth)) return fail(GS_ERR_INVALID_ARG, "depth loss needs fwd.depth and target_depth");
+        if (lp.w_unc != 0.f && (!fwd->unc || !obs_depth)) return fail(GS_ERR_INVALID_ARG, "|U| loss needs fwd.unc and obs_depth");
+        if (lp.unc_tau > 0.f && !fwd->nu_map) return fail(GS_ERR_INVALID_ARG, "unc_tau weighting needs fwd.nu_map");
+    } else if (dL) {
+        lp.g_color = dL->color; lp.g_depth = dL->depth; lp.g_alpha = dL->alpha; lp.g_unc = dL->unc; lp.g_nu = dL->nu_map;
+        if (lp.g_unc && !obs_depth) return fail(GS_ERR_INVALID_ARG, "a gradient on U needs obs_depth");
+    } else {
+        return fail(GS_ERR_INVALID_ARG, "either dL or loss is required");
+    }
+    gs::ImagePtrs ip{fwd->color, fwd->depth, fwd->alpha, fwd->unc, fwd->nu_map, fwd->median, fwd->T_final, fwd->n_last};
+    const int N = proj->n_gaussians;
+    const int M = N * n_frames;
+    const int per_frame = gs_pose_partials_per_frame(mode, N, n_frames, cams, opts->tile);
+    cudaError_t e;
+    if (mode == GS_MODE_POSE) {
+        if (!proj->pose_jac) return fail(GS_ERR_INVALID_ARG, "POSE mode needs projected.pose_jac");
+        for (int f = 0; f < n_frames; ++f) {
+            const int used = ft.f[f].tiles_x * ft.f[f].tiles_y;
+            if (used < per_frame) {
+                e = cudaMemsetAsync(pose_partials + ((size_t)f * per_frame + used) * 6, 0,
+                                    sizeof(double) * 6 * (size_t)(per_frame - used), stream);
+                if (e != cudaSuccess) return cuda_status(e, "gs_render_bwd memset");
+            }
+        }
+        return cuda_status(gs::launch_render_bwd(mode, proj->rec, proj->pose_jac, tiles->values, tiles->ranges, ft,
+                                                 obs_depth, ip, lp, nullptr, pose_partials, per_frame, status, stream),
+                           "gs_render_bwd");
+    }
+    GS_TRY(check_gauss(g));
+    if (g->n != N) return fail(GS_ERR_INVALID_ARG, "gaussians.n != projected.n_gaussians");
+    if (!T_cw || !grads) return fail(GS_ERR_INVALID_ARG, "FULL mode needs T_cw and grads");
+    const size_t need = bwd_ws_bytes(M, mode);
+    if (!ws || ws_bytes < need || !aligned(ws, 256)) return fail(GS_ERR_INVALID_ARG, "workspace %zu bytes < %zu needed (256-aligned)", ws_bytes, need);
+    float *grad2d = static_cast<float *>(ws);
+    if ((e = cudaMemsetAsync(grad2d, 0, sizeof(float) * gs::kGrad2d * (size_t)M, stream)) != cudaSuccess)
+        return cuda_status(e, "gs_render_bwd memset");
+    if ((e = gs::launch_render_bwd(mode, proj->rec, nullptr, tiles->values, tiles->ranges, ft, obs_depth, ip, lp,
+                                   grad2d, pose_partials, per_frame, status, stream)) != cudaSuccess)
+        return cuda_status(e, "gs_render_bwd");
+    return cuda_status(gs::launch_project_bwd(gauss_ptrs(g), N, ft, T_cw, opts->jclamp, proj->rec, grad2d, *grads,
+                                              pose_partials, per_frame, status, stream),
+                       "gs_render_bwd (projection adjoint)");
+}
+
+gs_status gs_pose_grad_reduce(const double *partials, int n_frames, int per_frame, double *pose_grad,
+                              const int32_t *status, gs_stream stream) {
+    if (!partials || !pose_grad || !status) return fail(GS_ERR_INVALID_ARG, "NULL pointer");
+    if (n_frames < 1 || n_frames > GS_MAX_FRAMES || per_frame < 1) return fail(GS_ERR_INVALID_ARG, "bad n_frames/per_frame");
+    return cuda_status(gs::launch_pose_reduce(partials, n_frames, per_frame, pose_grad, status, stream),
+                       "gs_pose_grad_reduce");
+}
+
+gs_status gs_pose_adam_step(double *state, const double *pose_grad, float *T_cw, int n_frames, const gs_adam *adam,
+                            const int32_t *status, gs_stream stream) {
+    if (!state || !pose_grad || !T_cw || !adam || !status) return fail(GS_ERR_INVALID_ARG, "NULL pointer");
+    if (n_frames < 1 || n_frames > GS_MAX_FRAMES) return fail(GS_ERR_INVALID_ARG, "bad n_frames");
+    return cuda_status(gs::launch_pose_adam(state, pose_grad, T_cw, n_frames, *adam, status, stream),
+                       "gs_pose_adam_step");
+}
+
+}  // extern "C"

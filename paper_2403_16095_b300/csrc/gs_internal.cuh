@@ -1,0 +1,91 @@
+// Internal declarations shared by the libgs CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gs.h"
+
+namespace gs {
+
+constexpr int kRecFloats = GS_REC_FLOATS;
+constexpr int kJacFloats = GS_JAC_FLOATS;
+constexpr int kGrad2d = 12;       // FULL-mode per-record accumulators
+constexpr int kScanBlocks = 592;  // 4 CTAs per SM on 148 SMs
+constexpr int kSortBlocks = 592;
+constexpr int kSortThreads = 256;
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+
+// Per-frame constants, passed to kernels by value (<= 64 frames, ~3 KB).
+struct FrameDesc {
+    int W, H;
+    float fx, fy, cx, cy, znear;
+    int tiles_x, tiles_y;
+    int tile_off;  // first global tile id of the frame
+    int pix_off;   // first pixel of the frame in the concatenated images
+};
+struct FrameTable {
+    int n;
+    int tile;
+    int total_tiles;
+    int total_pix;
+    FrameDesc f[GS_MAX_FRAMES];
+};
+
+// Records of the projection: field offsets in the 16-float record.
+enum RecField { R_MX = 0, R_MY, R_CA, R_CB, R_CC, R_OP, R_Z, R_NU, R_CR, R_CG, R_CBL, R_RAD, R_X0, R_Y0, R_X1, R_Y1 };
+// FULL-mode accumulator layout per record.
+enum GradField { G_MX = 0, G_MY, G_CA, G_CB, G_CC, G_OP, G_Z, G_NU, G_R, G_G, G_B };
+
+struct GaussPtrs {
+    const float *means, *log_scales, *quats, *opacity_logit, *colors, *nu;
+};
+
+struct ImagePtrs {
+    float *color, *depth, *alpha, *unc, *nu_map, *median, *T_final;
+    int32_t *n_last;
+};
+
+struct LossParams {
+    int fused;  // 1: compute dL from the loss spec, 0: read upstream maps
+    float w_color, w_depth, w_unc, w_nu, unc_tau;
+    const float *target_color, *target_depth;
+    const float *g_color, *g_depth, *g_alpha, *g_unc, *g_nu;
+};
+
+// frame of a global tile id (frames are few: linear scan of a uniform table)
+__device__ __forceinline__ int frame_of_tile(const FrameTable &ft, int gtile) {
+    int f = 0;
+    while (f + 1 < ft.n && gtile >= ft.f[f + 1].tile_off) ++f;
+    return f;
+}
+
+// ----------------------------------------------------------------- launchers
+// project.cu
+cudaError_t launch_project(const GaussPtrs &g, int n, const FrameTable &ft, const float *T_cw, float jclamp,
+                           float nu_cull, int mode, float *rec, int *touched, float *jac, const int32_t *status,
+                           cudaStream_t s);
+cudaError_t launch_project_bwd(const GaussPtrs &g, int n, const FrameTable &ft, const float *T_cw, float jclamp,
+                               const float *rec, const float *grad2d, gs_grads grads, double *pose_partials,
+                               int per_frame, const int32_t *status, cudaStream_t s);
+// binning.cu
+size_t bin_workspace_bytes(int n_records, int capacity);
+cudaError_t launch_bin_tiles(const float *rec, const int *touched, int n_records, int n_per_frame,
+                             const FrameTable &ft, int capacity, uint32_t *values, uint64_t *keys_out,
+                             uint32_t *ranges, int32_t *status, void *ws, cudaStream_t s);
+// render_fwd.cu
+cudaError_t launch_render_fwd(const float *rec, const uint32_t *values, const uint32_t *ranges, const FrameTable &ft,
+                              const float *obs_depth, const ImagePtrs &out, const int32_t *status, cudaStream_t s);
+// render_bwd.cu
+cudaError_t launch_render_bwd(int mode, const float *rec, const float *jac, const uint32_t *values,
+                              const uint32_t *ranges, const FrameTable &ft, const float *obs_depth,
+                              const ImagePtrs &fwd, const LossParams &lp, float *grad2d, double *pose_partials,
+                              int per_frame, const int32_t *status, cudaStream_t s);
+// pose.cu
+cudaError_t launch_pose_reduce(const double *partials, int n_frames, int per_frame, double *out,
+                               const int32_t *status, cudaStream_t s);
+cudaError_t launch_pose_adam(double *state, const double *grad, float *T_cw, int n_frames, gs_adam adam,
+                             const int32_t *status, cudaStream_t s);
+
+}  // namespace gs

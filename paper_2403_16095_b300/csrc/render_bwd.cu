@@ -1,0 +1,246 @@
+// Adjoint of the front-to-back blend (CG-SLAM Eq. 3-10), walking each tile's
+// depth-sorted list from the pixel's last blended entry back to the front.
+//
+// Per pixel the transmittance in front of entry j is recovered from the one
+// behind it, T_j = T_{j+1} / (1 - alpha_j), starting from the stored T_final;
+// nothing per entry is stored by the forward pass. With g the per-pixel
+// gradient of the loss w.r.t. the blended channels f = (R, G, B, depth, opacity,
+// U, nu) and GS_j = sum_{i > j} w_i <g, f_i> (one running scalar, since g does
+// not depend on the entry):
+//     dL/dalpha_j = T_j <g, f_j> - GS_j / (1 - alpha_j),
+//     dL/dz_j     = w_j (g_depth + 2 g_U (z_j - D)),   dL/dc_j = w_j g_color,
+//     dL/d(power) = alpha_j dL/dalpha_j  (0 when alpha is clamped at 0.99),
+// and the power -q/2 gives the gradients of the 2D centre and the conic.
+//
+// POSE mode: each pixel contracts (d mean2d, d conic, dz) of every entry with
+// that record's 6x6 pose Jacobian into six FP32 accumulators; at the end the
+// tile reduces them in FP64 by warp shuffles and a fixed block tree into one
+// partial per tile (deterministic, no atomics).
+// FULL mode: the eleven per-entry gradients are reduced across the warp (only
+// when some lane contributed) and lane 0 adds them to the record's accumulators.
+#include "gs_internal.cuh"
+#include "blend_common.cuh"
+
+namespace gs {
+namespace {
+
+__device__ __forceinline__ float sgnf(float v) { return v > 0.f ? 1.f : (v < 0.f ? -1.f : 0.f); }
+
+template <int TILE, int MODE>
+__global__ void __launch_bounds__(TILE *TILE)
+    k_render_bwd(const float4 *__restrict__ rec, const float4 *__restrict__ jac, const uint32_t *__restrict__ values,
+                 const uint2 *__restrict__ ranges, FrameTable ft, const float *__restrict__ obs_depth, ImagePtrs fwd,
+                 LossParams lp, float *__restrict__ grad2d, double *__restrict__ pose_partials, int per_frame,
+                 const int32_t *__restrict__ status) {
+    constexpr int NT = TILE * TILE;
+    constexpr bool POSE = MODE == GS_MODE_POSE;
+    constexpr int BATCH = POSE ? (NT < 128 ? NT : 128) : (NT < 256 ? NT : 256);
+    constexpr int NWARP = NT / 32 > 0 ? NT / 32 : 1;
+    __shared__ float4 s_a[BATCH], s_b[BATCH], s_c[BATCH];
+    __shared__ int4 s_r[BATCH];
+    __shared__ float4 s_j[POSE ? BATCH * 9 : 1];
+    __shared__ uint32_t s_idx[BATCH];
+    __shared__ uint32_t s_wmax[NWARP];
+    __shared__ double s_red[NWARP][6];
+    if (status[0] != 0) return;
+
+    const int gtile = blockIdx.x;
+    const int f = frame_of_tile(ft, gtile);
+    const FrameDesc &fd = ft.f[f];
+    const int lt = gtile - fd.tile_off;
+    const int tx = lt % fd.tiles_x, ty = lt / fd.tiles_x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int WPR = TILE / 8;
+    const int wx0 = tx * TILE + (warp % WPR) * 8, wy0 = ty * TILE + (warp / WPR) * 4;
+    const int px = wx0 + (lane & 7), py = wy0 + (lane >> 3);
+    const bool inside = px < fd.W && py < fd.H;
+    const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+    const size_t pix = (size_t)fd.pix_off + (size_t)py * fd.W + px;
+    const int HW = fd.W * fd.H;
+    const size_t cbase = 3 * (size_t)fd.pix_off + (size_t)py * fd.W + px;
+    const uint2 range = ranges[gtile];
+
+    // ---- per-pixel loss gradient w.r.t. the blended channels
+    float gc0 = 0.f, gc1 = 0.f, gc2 = 0.f, gD = 0.f, gO = 0.f, gU = 0.f, gN = 0.f;
+    float T = 1.f, Dp = 0.f;
+    uint32_t my_last = range.x;
+    if (inside) {
+        T = fwd.T_final[pix];
+        my_last = min(max((uint32_t)fwd.n_last[pix], range.x), range.y);  // stay inside this tile's list
+        Dp = obs_depth ? obs_depth[pix] : 0.f;
+        if (lp.fused) {
+            const float inv_hw = 1.f / (float)HW;
+            float m = 1.f;
+            if (lp.unc_tau > 0.f) m = 1.f / (1.f + fwd.nu_map[pix] / lp.unc_tau);
+            const float kc = inv_hw * m * lp.w_color, kd = inv_hw * m * lp.w_depth;
+            if (lp.w_color != 0.f) {
+                gc0 = kc * sgnf(fwd.color[cbase] - lp.target_color[cbase]);
+                gc1 = kc * sgnf(fwd.color[cbase + HW] - lp.target_color[cbase + HW]);
+                gc2 = kc * sgnf(fwd.color[cbase + 2 * (size_t)HW] - lp.target_color[cbase + 2 * (size_t)HW]);
+            }
+            if (lp.w_depth != 0.f) gD = kd * sgnf(fwd.depth[pix] - lp.target_depth[pix]);
+            if (lp.w_unc != 0.f) gU = inv_hw * lp.w_unc * sgnf(fwd.unc[pix]);
+            gN = inv_hw * lp.w_nu;
+        } else {
+            if (lp.g_color) {
+                gc0 = lp.g_color[cbase];
+                gc1 = lp.g_color[cbase + HW];
+                gc2 = lp.g_color[cbase + 2 * (size_t)HW];
+            }
+            if (lp.g_depth) gD = lp.g_depth[pix];
+            if (lp.g_alpha) gO = lp.g_alpha[pix];
+            if (lp.g_unc) gU = lp.g_unc[pix];
+            if (lp.g_nu) gN = lp.g_nu[pix];
+        }
+    }
+    // ---- extent of the walk: block max and warp max of the last blended entry
+    const uint32_t warp_last = __reduce_max_sync(0xffffffffu, my_last);
+    if (lane == 0) s_wmax[warp] = warp_last;
+    __syncthreads();
+    uint32_t block_last = range.x;
+#pragma unroll
+    for (int w = 0; w < NWARP; ++w) block_last = max(block_last, s_wmax[w]);
+
+    float GS = 0.f;
+    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+
+    for (int bend = (int)block_last; bend > (int)range.x; bend -= BATCH) {
+        const int bstart = max((int)range.x, bend - BATCH);
+        __syncthreads();
+        if (tid < bend - bstart) {
+            const uint32_t r = values[bstart + tid];
+            const float4 *R = rec + (size_t)r * 4;
+            s_a[tid] = R[0];
+            s_b[tid] = R[1];
+            s_c[tid] = R[2];
+            s_r[tid] = reinterpret_cast<const int4 *>(R)[3];
+            s_idx[tid] = r;
+            if (POSE) {
+                const float4 *J = jac + (size_t)r * 9;
+#pragma unroll
+                for (int q = 0; q < 9; ++q) s_j[tid * 9 + q] = J[q];
+            }
+        }
+        __syncthreads();
+        for (int j = bend - 1; j >= bstart; --j) {
+            if ((uint32_t)j >= warp_last) continue;  // warp-uniform
+            const int k = j - bstart;
+            const int4 rc = s_r[k];
+            if (rc.x > wx0 + 7 || rc.z < wx0 || rc.y > wy0 + 3 || rc.w < wy0) continue;  // warp-uniform
+            const float4 a = s_a[k];
+            const float4 b = s_b[k];
+            float dx = 0.f, dy = 0.f, G = 0.f, sg = 0.f, alpha = 0.f;
+            bool act = (uint32_t)j < my_last && in_rect(px, py, rc);
+            if (act) act = eval_alpha(pxc, pyc, a, b, dx, dy, G, sg, alpha);
+            float v[11];
+            if (act) {
+                const float one_m = __fsub_rn(1.f, alpha);
+                const float inv = __frcp_rn(one_m);
+                T = T * inv;  // transmittance in front of entry j
+                const float w = alpha * T;
+                const float4 c = s_c[k];
+                const float dz = b.z - Dp;
+                const float dot = gc0 * c.x + gc1 * c.y + gc2 * c.z + gD * b.z + gO + gU * dz * dz + gN * b.w;
+                const float dal = T * dot - inv * GS;
+                GS = fmaf(w, dot, GS);
+                const bool clamped = sg >= kAlphaMax;
+                const float dpow = clamped ? 0.f : dal * alpha;
+                v[G_MX] = dpow * (a.z * dx + a.w * dy);
+                v[G_MY] = dpow * (a.w * dx + b.x * dy);
+                v[G_CA] = -0.5f * dpow * dx * dx;
+                v[G_CB] = -dpow * dx * dy;
+                v[G_CC] = -0.5f * dpow * dy * dy;
+                v[G_Z] = w * (gD + 2.f * gU * dz);
+                if (!POSE) {
+                    v[G_OP] = clamped ? 0.f : dal * G;
+                    v[G_NU] = w * gN;
+                    v[G_R] = w * gc0;
+                    v[G_G] = w * gc1;
+                    v[G_B] = w * gc2;
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < 11; ++m) v[m] = 0.f;
+            }
+            if (POSE) {
+                if (act) {
+                    const float th[6] = {v[G_MX], v[G_MY], v[G_CA], v[G_CB], v[G_CC], v[G_Z]};
+                    const float4 *J = &s_j[k * 9];
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) {
+                        const float4 jq = J[q];
+                        const int e = 4 * q;
+                        acc[(e + 0) % 6] = fmaf(th[(e + 0) / 6], jq.x, acc[(e + 0) % 6]);
+                        acc[(e + 1) % 6] = fmaf(th[(e + 1) / 6], jq.y, acc[(e + 1) % 6]);
+                        acc[(e + 2) % 6] = fmaf(th[(e + 2) / 6], jq.z, acc[(e + 2) % 6]);
+                        acc[(e + 3) % 6] = fmaf(th[(e + 3) / 6], jq.w, acc[(e + 3) % 6]);
+                    }
+                }
+            } else {
+                if (__any_sync(0xffffffffu, act)) {
+#pragma unroll
+                    for (int m = 0; m < 11; ++m) {
+                        float s = v[m];
+#pragma unroll
+                        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+                        v[m] = s;
+                    }
+                    if (lane == 0) {
+                        float *gp = grad2d + (size_t)s_idx[k] * kGrad2d;
+#pragma unroll
+                        for (int m = 0; m < 11; ++m) atomicAdd(gp + m, v[m]);
+                    }
+                }
+            }
+        }
+    }
+    if (POSE) {
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+            double s = (double)acc[m];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+            if (lane == 0) s_red[warp][m] = s;
+        }
+        __syncthreads();
+        if (tid < 6) {
+            double s = 0.0;
+#pragma unroll
+            for (int w = 0; w < NWARP; ++w) s += s_red[w][tid];
+            pose_partials[((size_t)f * per_frame + lt) * 6 + tid] = s;
+        }
+    }
+}
+
+template <int TILE>
+cudaError_t launch_tile(int mode, const float4 *rec, const float4 *jac, const uint32_t *values, const uint2 *ranges,
+                        const FrameTable &ft, const float *obs_depth, const ImagePtrs &fwd, const LossParams &lp,
+                        float *grad2d, double *pp, int per_frame, const int32_t *status, cudaStream_t s) {
+    if (mode == GS_MODE_POSE)
+        k_render_bwd<TILE, GS_MODE_POSE><<<ft.total_tiles, TILE * TILE, 0, s>>>(
+            rec, jac, values, ranges, ft, obs_depth, fwd, lp, grad2d, pp, per_frame, status);
+    else
+        k_render_bwd<TILE, GS_MODE_FULL><<<ft.total_tiles, TILE * TILE, 0, s>>>(
+            rec, jac, values, ranges, ft, obs_depth, fwd, lp, grad2d, pp, per_frame, status);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_render_bwd(int mode, const float *rec, const float *jac, const uint32_t *values,
+                              const uint32_t *ranges, const FrameTable &ft, const float *obs_depth,
+                              const ImagePtrs &fwd, const LossParams &lp, float *grad2d, double *pose_partials,
+                              int per_frame, const int32_t *status, cudaStream_t s) {
+    if (ft.total_tiles == 0) return cudaSuccess;
+    const float4 *r4 = reinterpret_cast<const float4 *>(rec);
+    const float4 *j4 = reinterpret_cast<const float4 *>(jac);
+    const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
+    switch (ft.tile) {
+        case 8: return launch_tile<8>(mode, r4, j4, values, rg, ft, obs_depth, fwd, lp, grad2d, pose_partials, per_frame, status, s);
+        case 16: return launch_tile<16>(mode, r4, j4, values, rg, ft, obs_depth, fwd, lp, grad2d, pose_partials, per_frame, status, s);
+        case 32: return launch_tile<32>(mode, r4, j4, values, rg, ft, obs_depth, fwd, lp, grad2d, pose_partials, per_frame, status, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace gs

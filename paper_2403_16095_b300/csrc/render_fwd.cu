@@ -1,0 +1,119 @@
+// Front-to-back alpha blending of the depth-sorted tile lists (CG-SLAM Eq. 3-10).
+//
+// One CTA per tile (TILE x TILE pixels, one thread per pixel). Each warp owns an
+// 8x4 pixel block so that the warp-uniform rectangle test against a Gaussian's
+// pixel rect skips most non-overlapping list entries without divergence. The
+// tile's list is staged in shared memory in batches of up to 256 records; a
+// pixel stops when the next entry would take T below 1e-4, a warp skips a batch
+// once all of its pixels are done, and the CTA exits once every pixel is done.
+//
+// The per-pixel arithmetic (q, G, alpha, T) is the same function as in the
+// backward pass, written with explicitly rounded operations, so both passes take
+// identical accept/stop decisions and the result does not depend on TILE.
+#include "gs_internal.cuh"
+#include "blend_common.cuh"
+
+namespace gs {
+namespace {
+
+template <int TILE>
+__global__ void __launch_bounds__(TILE *TILE)
+    k_render_fwd(const float4 *__restrict__ rec, const uint32_t *__restrict__ values,
+                 const uint2 *__restrict__ ranges, FrameTable ft, const float *__restrict__ obs_depth, ImagePtrs out,
+                 const int32_t *__restrict__ status) {
+    constexpr int NT = TILE * TILE;
+    constexpr int BATCH = NT < 256 ? NT : 256;
+    __shared__ float4 s_a[BATCH], s_b[BATCH], s_c[BATCH];
+    __shared__ int4 s_r[BATCH];
+    if (status[0] != 0) return;
+
+    const int gtile = blockIdx.x;
+    const int f = frame_of_tile(ft, gtile);
+    const FrameDesc &fd = ft.f[f];
+    const int lt = gtile - fd.tile_off;
+    const int tx = lt % fd.tiles_x, ty = lt / fd.tiles_x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int WPR = TILE / 8;
+    const int wx0 = tx * TILE + (warp % WPR) * 8, wy0 = ty * TILE + (warp / WPR) * 4;
+    const int px = wx0 + (lane & 7), py = wy0 + (lane >> 3);
+    const bool inside = px < fd.W && py < fd.H;
+    const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+    const size_t pix = (size_t)fd.pix_off + (size_t)py * fd.W + px;
+    const uint2 range = ranges[gtile];
+    const float Dp = (obs_depth != nullptr && inside) ? obs_depth[pix] : 0.f;
+
+    float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, dep = 0.f, opa = 0.f, unc = 0.f, nus = 0.f, med = 0.f;
+    uint32_t last = range.x;
+    bool done = !inside;
+
+    for (uint32_t base = range.x; base < range.y; base += BATCH) {
+        if (__syncthreads_count(done) == NT) break;  // also orders smem reuse
+        const uint32_t j = base + tid;
+        if (tid < BATCH && j < range.y) {
+            const float4 *R = rec + (size_t)values[j] * 4;
+            s_a[tid] = R[0];
+            s_b[tid] = R[1];
+            s_c[tid] = R[2];
+            s_r[tid] = reinterpret_cast<const int4 *>(R)[3];
+        }
+        __syncthreads();
+        const int cnt = min(BATCH, (int)(range.y - base));
+        if (!done) {
+            for (int k = 0; k < cnt; ++k) {
+                const int4 rc = s_r[k];
+                if (rc.x > wx0 + 7 || rc.z < wx0 || rc.y > wy0 + 3 || rc.w < wy0) continue;  // warp-uniform
+                if (!in_rect(px, py, rc)) continue;
+                const float4 a = s_a[k];
+                const float4 b = s_b[k];
+                float dx, dy, G, sg, alpha;
+                if (!eval_alpha(pxc, pyc, a, b, dx, dy, G, sg, alpha)) continue;
+                const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
+                if (Tn < kTMin) { done = true; break; }
+                const float w = __fmul_rn(alpha, T);
+                const float4 c = s_c[k];
+                c0 = fmaf(w, c.x, c0);
+                c1 = fmaf(w, c.y, c1);
+                c2 = fmaf(w, c.z, c2);
+                dep = fmaf(w, b.z, dep);
+                opa = __fadd_rn(opa, w);
+                const float dz = __fsub_rn(b.z, Dp);
+                unc = fmaf(w, __fmul_rn(dz, dz), unc);
+                nus = fmaf(w, b.w, nus);
+                if (T >= 0.5f && Tn < 0.5f) med = b.z;
+                T = Tn;
+                last = base + k + 1;
+            }
+        }
+    }
+    if (!inside) return;
+    const int HW = fd.W * fd.H;
+    const size_t cbase = 3 * (size_t)fd.pix_off + (size_t)py * fd.W + px;
+    out.color[cbase] = c0;
+    out.color[cbase + HW] = c1;
+    out.color[cbase + 2 * (size_t)HW] = c2;
+    if (out.depth) out.depth[pix] = dep;
+    if (out.alpha) out.alpha[pix] = opa;
+    if (out.unc && obs_depth) out.unc[pix] = unc;
+    if (out.nu_map) out.nu_map[pix] = nus;
+    if (out.median) out.median[pix] = med;
+    out.T_final[pix] = T;
+    out.n_last[pix] = (int32_t)last;
+}
+
+}  // namespace
+
+cudaError_t launch_render_fwd(const float *rec, const uint32_t *values, const uint32_t *ranges, const FrameTable &ft,
+                              const float *obs_depth, const ImagePtrs &out, const int32_t *status, cudaStream_t s) {
+    if (ft.total_tiles == 0) return cudaSuccess;
+    const float4 *r4 = reinterpret_cast<const float4 *>(rec);
+    const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
+    switch (ft.tile) {
+        case 8: k_render_fwd<8><<<ft.total_tiles, 64, 0, s>>>(r4, values, rg, ft, obs_depth, out, status); break;
+        case 16: k_render_fwd<16><<<ft.total_tiles, 256, 0, s>>>(r4, values, rg, ft, obs_depth, out, status); break;
+        case 32: k_render_fwd<32><<<ft.total_tiles, 1024, 0, s>>>(r4, values, rg, ft, obs_depth, out, status); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace gs

@@ -1,0 +1,307 @@
+"""PyTorch-side driver of libgs: device buffers, the call sequence of one
+iteration, a ``torch.autograd.Function`` (FULL backward) and the tracking loop
+(POSE backward + on-device Adam, captured in a CUDA graph).
+
+PyTorch supplies memory and streams only; every step of the rasterizer runs in
+the libgs kernels behind the C ABI (see ``_abi``).
+"""
+from __future__ import annotations
+
+import math
+from typing import Optional, Sequence
+
+import torch
+
+from . import _abi as A
+from ._abi import Gaussians
+
+CHANNELS = ("color", "depth", "alpha", "unc", "nu_map", "median", "T_final", "n_last")
+
+
+def _pix(cams) -> int:
+    return int(sum(int(c.width) * int(c.height) for c in cams))
+
+
+def _tiles(cams, tile) -> int:
+    return int(sum(((int(c.width) + tile - 1) // tile) * ((int(c.height) + tile - 1) // tile) for c in cams))
+
+
+class Rasterizer:
+    """Buffers and calls for one batch of frames (fixed cameras) and N Gaussians."""
+
+    def __init__(self, cams: Sequence, n_gaussians: int, tile: int = 16, mode: int = A.GS_MODE_POSE,
+                 capacity: Optional[int] = None, jclamp: float = 1.3, nu_cull: float = 0.0,
+                 keep_keys: bool = False, device=None):
+        self.cams = list(cams)
+        self.F = len(self.cams)
+        self.N = int(n_gaussians)
+        self.M = self.F * self.N
+        self.tile = tile
+        self.mode = mode
+        self.opts = A.gs_opts(tile, mode, jclamp, nu_cull)
+        self.device = torch.device(device or "cuda")
+        dev = self.device
+        self.rec = torch.empty(self.M * A.GS_REC_FLOATS, dtype=torch.float32, device=dev)
+        self.touched = torch.empty(self.M, dtype=torch.int32, device=dev)
+        self.jac = (torch.empty(self.M * A.GS_JAC_FLOATS, dtype=torch.float32, device=dev)
+                    if mode == A.GS_MODE_POSE else None)
+        self.status = torch.zeros(4, dtype=torch.int32, device=dev)
+        self.n_tiles = _tiles(self.cams, tile)
+        self.ranges = torch.empty(2 * self.n_tiles, dtype=torch.int32, device=dev)
+        self.pix_total = _pix(self.cams)
+        P = self.pix_total
+        self.img = {
+            "color": torch.empty(3 * P, dtype=torch.float32, device=dev),
+            "depth": torch.empty(P, dtype=torch.float32, device=dev),
+            "alpha": torch.empty(P, dtype=torch.float32, device=dev),
+            "unc": torch.zeros(P, dtype=torch.float32, device=dev),
+            "nu_map": torch.empty(P, dtype=torch.float32, device=dev),
+            "median": torch.empty(P, dtype=torch.float32, device=dev),
+            "T_final": torch.empty(P, dtype=torch.float32, device=dev),
+            "n_last": torch.empty(P, dtype=torch.int32, device=dev),
+        }
+        self.keep_keys = keep_keys
+        self.values = self.keys = self.bin_ws = None
+        self.set_capacity(capacity if capacity is not None else max(4096, 2 * self.M))
+        if mode != A.GS_MODE_FWD:
+            self.per_frame = A.gs_pose_partials_per_frame(mode, self.N, self.cams, tile)
+            self.pose_partials = torch.zeros(self.F * self.per_frame * 6, dtype=torch.float64, device=dev)
+            self.pose_grad = torch.zeros(self.F, 6, dtype=torch.float64, device=dev)
+            self.bwd_ws = torch.empty(A.gs_render_bwd_workspace_size(self.M, mode), dtype=torch.uint8, device=dev)
+
+    # --------------------------------------------------------------- buffers
+    def set_capacity(self, capacity: int) -> None:
+        self.capacity = int(capacity)
+        dev = self.device
+        self.values = torch.empty(self.capacity, dtype=torch.int32, device=dev)
+        self.keys = torch.empty(self.capacity, dtype=torch.int64, device=dev) if self.keep_keys else None
+        self.bin_ws = torch.empty(A.gs_bin_tiles_workspace_size(self.M, self.capacity), dtype=torch.uint8,
+                                  device=dev)
+
+    def reset_status(self) -> None:
+        self.status.zero_()
+
+    def read_status(self):
+        s = self.status.tolist()
+        return int(s[0]), int(s[1])
+
+    # --------------------------------------------------------------- stages
+    def project(self, g: Gaussians, T_cw: torch.Tensor, stream=None) -> None:
+        A.gs_project(g, self.cams, T_cw, self.opts, self.rec, self.touched, self.jac, self.status, stream)
+
+    def bin(self, stream=None) -> None:
+        A.gs_bin_tiles(self.N, self.cams, self.opts, self.rec, self.touched, self.values, self.keys, self.ranges,
+                       self.status, self.bin_ws, stream)
+
+    def forward(self, obs_depth: Optional[torch.Tensor] = None, stream=None) -> None:
+        A.gs_render_fwd(self.N, self.cams, self.opts, self.rec, self.values, self.ranges, obs_depth, self.img,
+                        self.status, stream)
+
+    def backward(self, *, obs_depth=None, loss: Optional[dict] = None, dL: Optional[dict] = None,
+                 g: Optional[Gaussians] = None, T_cw: Optional[torch.Tensor] = None, grads: Optional[dict] = None,
+                 stream=None) -> None:
+        A.gs_render_bwd(self.N, self.cams, self.opts, self.rec, self.jac, self.values, self.ranges, T_cw, g,
+                        obs_depth, self.img, dL, loss, grads, self.pose_partials, self.status, self.bwd_ws, stream)
+
+    def reduce_pose(self, stream=None) -> None:
+        A.gs_pose_grad_reduce(self.pose_partials, self.F, self.per_frame, self.pose_grad, self.status, stream)
+
+    def render(self, g: Gaussians, T_cw: torch.Tensor, obs_depth=None, max_retries: int = 3) -> None:
+        """project + bin + forward; grows the pair capacity and re-runs on overflow
+        (reads the status word, i.e. synchronises)."""
+        for _ in range(max_retries + 1):
+            self.reset_status()
+            self.project(g, T_cw)
+            self.bin()
+            self.forward(obs_depth)
+            code, need = self.read_status()
+            if code == 0:
+                return
+            if code != A.GS_ERR_CAPACITY:
+                raise A.GsError(code, "device status")
+            self.set_capacity(int(need * 1.25) + 1024)
+        raise A.GsError(A.GS_ERR_CAPACITY, "pair capacity still exceeded")
+
+    # --------------------------------------------------------------- views
+    def frame_images(self, f: int) -> dict:
+        """Per-frame views: color [3,H,W], the others [H,W]."""
+        c = self.cams[f]
+        H, W = int(c.height), int(c.width)
+        off = sum(int(x.width) * int(x.height) for x in self.cams[:f])
+        out = {"color": self.img["color"][3 * off: 3 * off + 3 * H * W].view(3, H, W)}
+        for k in CHANNELS[1:]:
+            out[k] = self.img[k][off: off + H * W].view(H, W)
+        return out
+
+    def tile_lists(self):
+        """(values[:P], ranges [n_tiles,2]) after a successful bin (synchronises)."""
+        P = self.read_status()[1]
+        return self.values[:P], self.ranges.view(-1, 2)
+
+
+# ===================================================================== autograd
+class GaussianRasterize(torch.autograd.Function):
+    """Renders colour, depth, opacity, U, nu map and median depth of F frames at
+    poses Exp(xi_f) T_cw_f (xi_f = 0 at the call) and differentiates w.r.t. every
+    Gaussian parameter and xi (left se(3) perturbation, (rho, phi))."""
+
+    @staticmethod
+    def forward(ctx, means, log_scales, quats, opacity_logit, colors, nu, xi, T_cw, rast: Rasterizer,
+                obs_depth=None):
+        g = Gaussians(means.contiguous(), log_scales.contiguous(), quats.contiguous(),
+                      opacity_logit.contiguous(), colors.contiguous(), nu.contiguous())
+        T_cw = T_cw.contiguous()
+        rast.render(g, T_cw, obs_depth)
+        ctx.rast, ctx.g, ctx.T_cw, ctx.obs_depth = rast, g, T_cw, obs_depth
+        im = rast.img
+        outs = tuple(im[k].clone() for k in ("color", "depth", "alpha", "unc", "nu_map", "median"))
+        ctx.mark_non_differentiable(outs[5])
+        return outs
+
+    @staticmethod
+    def backward(ctx, g_color, g_depth, g_alpha, g_unc, g_nu, g_median):
+        rast: Rasterizer = ctx.rast
+        g: Gaussians = ctx.g
+        dL = {}
+        for k, v in (("color", g_color), ("depth", g_depth), ("alpha", g_alpha), ("unc", g_unc), ("nu_map", g_nu)):
+            if v is not None:
+                dL[k] = v.contiguous()
+        if "unc" in dL and ctx.obs_depth is None:
+            dL.pop("unc")
+        dev = g.means.device
+        grads = {k: torch.empty_like(getattr(g, k)) for k in
+                 ("means", "log_scales", "quats", "opacity_logit", "colors", "nu")}
+        rast.backward(obs_depth=ctx.obs_depth, dL=dL, g=g, T_cw=ctx.T_cw, grads=grads)
+        rast.reduce_pose()
+        code, _ = rast.read_status()
+        if code:
+            raise A.GsError(code, "device status in backward")
+        gxi = rast.pose_grad.to(torch.float32).to(dev)
+        return (grads["means"], grads["log_scales"], grads["quats"], grads["opacity_logit"], grads["colors"],
+                grads["nu"], gxi, None, None, None)
+
+
+def rasterize(g: Gaussians, xi: torch.Tensor, T_cw: torch.Tensor, rast: Rasterizer, obs_depth=None):
+    """Differentiable render; returns dict of per-frame-concatenated channels."""
+    outs = GaussianRasterize.apply(g.means, g.log_scales, g.quats, g.opacity_logit, g.colors, g.nu, xi, T_cw,
+                                   rast, obs_depth)
+    return dict(zip(("color", "depth", "alpha", "unc", "nu_map", "median"), outs))
+
+
+# ===================================================================== tracking
+def pose_state(T: torch.Tensor) -> torch.Tensor:
+    """FP64 pose state [F, 25]: R (9), t (3), Adam m (6), v (6), step."""
+    T = T.reshape(-1, 3, 4).to(torch.float64)
+    st = torch.zeros(T.shape[0], A.GS_POSE_STATE_DOUBLES, dtype=torch.float64, device=T.device)
+    st[:, :9] = T[:, :, :3].reshape(-1, 9)
+    st[:, 9:12] = T[:, :, 3]
+    return st
+
+
+def state_pose(st: torch.Tensor) -> torch.Tensor:
+    T = torch.zeros(st.shape[0], 3, 4, dtype=torch.float64, device=st.device)
+    T[:, :, :3] = st[:, :9].view(-1, 3, 3)
+    T[:, :, 3] = st[:, 9:12]
+    return T
+
+
+class Tracker:
+    """Sequential tracking (Sec. 3.4, Eq. 19-20) of one frame: ``iters``
+    iterations of project -> bin -> forward -> POSE backward with the fused
+    uncertainty-weighted L1 colour + depth loss -> FP64 pose reduction -> Adam
+    step on the pose, all on the device. With ``graph=True`` one iteration is
+    captured once in a CUDA graph and replayed."""
+
+    def __init__(self, g: Gaussians, cam, tile: int = 16, iters: int = 30, lam=(0.2, 1.0), unc_tau: float = 0.025,
+                 lr_rot: float = 0.0015, lr_trans: float = 0.00215, jclamp: float = 1.3, graph: bool = True,
+                 capacity: Optional[int] = None):
+        self.g = g
+        self.cam = cam
+        self.iters = iters
+        self.graph_enabled = graph
+        dev = g.means.device
+        self.rast = Rasterizer([cam], g.n, tile=tile, mode=A.GS_MODE_POSE, capacity=capacity, jclamp=jclamp)
+        H, W = int(cam.height), int(cam.width)
+        self.target_color = torch.zeros(3 * H * W, dtype=torch.float32, device=dev)
+        self.target_depth = torch.zeros(H * W, dtype=torch.float32, device=dev)
+        self.loss = dict(w_color=lam[0], w_depth=lam[1], w_unc=0.0, w_nu=0.0, unc_tau=unc_tau,
+                         target_color=self.target_color, target_depth=self.target_depth)
+        self.adam = A.gs_adam(lr_rot, lr_trans, 0.9, 0.999, 1e-8)
+        self.state = torch.zeros(1, A.GS_POSE_STATE_DOUBLES, dtype=torch.float64, device=dev)
+        self.T_cw = torch.zeros(12, dtype=torch.float32, device=dev)
+        self.stream = torch.cuda.Stream(device=dev)
+        self.graph = None
+
+    # one iteration, enqueued on `stream`
+    def _iteration(self, stream=None):
+        r = self.rast
+        r.project(self.g, self.T_cw, stream)
+        r.bin(stream)
+        r.forward(self.target_depth, stream)
+        r.backward(obs_depth=self.target_depth, loss=self.loss, stream=stream)
+        r.reduce_pose(stream)
+        A.gs_pose_adam_step(self.state, r.pose_grad, self.T_cw, 1, self.adam, r.status, stream)
+
+    def launches_per_iteration(self) -> int:
+        """Kernel launches (and memsets) one iteration enqueues."""
+        bits = 32 + max(0, (self.rast.n_tiles - 1).bit_length())
+        passes = (bits + 7) // 8
+        return 1 + (1 + 3 + 3 * passes + 1 + 1) + 1 + 1 + 1 + 1
+
+    def _capture(self):
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(self.stream):
+            self._iteration(self.stream)  # warm-up outside capture
+        self.stream.synchronize()
+        with torch.cuda.graph(self.graph, stream=self.stream):
+            self._iteration(self.stream)
+
+    def set_frame(self, target_color: torch.Tensor, target_depth: torch.Tensor, T_init: torch.Tensor) -> None:
+        self.target_color.copy_(target_color.reshape(-1), non_blocking=True)
+        self.target_depth.copy_(target_depth.reshape(-1), non_blocking=True)
+        st = pose_state(T_init.to(self.state.device))
+        self.state.copy_(st)
+        self.T_cw.copy_(state_pose(st).reshape(-1).to(torch.float32))
+        self.rast.status.zero_()
+
+    def run(self) -> None:
+        """Enqueue ``iters`` iterations on the tracker's stream (no host sync)."""
+        cur = torch.cuda.current_stream()
+        self.stream.wait_stream(cur)
+        with torch.cuda.stream(self.stream):
+            for _ in range(self.iters):
+                if self.graph is not None:
+                    self.graph.replay()
+                else:
+                    self._iteration(self.stream)
+        cur.wait_stream(self.stream)
+
+    def track(self, target_color, target_depth, T_init, max_retries: int = 3) -> torch.Tensor:
+        """Track one frame; returns the refined pose [3,4] (FP64, on device).
+        Grows the pair capacity (and re-captures the graph) on overflow."""
+        for _ in range(max_retries + 1):
+            self.set_frame(target_color, target_depth, T_init)
+            if self.graph_enabled and self.graph is None:
+                self._capture()
+                self.set_frame(target_color, target_depth, T_init)
+            self.run()
+            code, need = self.rast.read_status()
+            if code == 0:
+                return state_pose(self.state)[0]
+            if code != A.GS_ERR_CAPACITY:
+                raise A.GsError(code, "device status during tracking")
+            self.rast.set_capacity(int(need * 1.5) + 4096)
+            self.graph = None
+        raise A.GsError(A.GS_ERR_CAPACITY, "pair capacity still exceeded")
+
+    def prepare(self, target_color, target_depth, T_init, headroom: float = 1.5) -> None:
+        """Size the pair buffer from one render at T_init (with headroom), then
+        capture the graph."""
+        self.set_frame(target_color, target_depth, T_init)
+        self.rast.render(self.g, self.T_cw, self.target_depth)
+        need = self.rast.read_status()[1]
+        self.rast.set_capacity(int(need * headroom) + 4096)
+        self.graph = None
+        if self.graph_enabled:
+            self.set_frame(target_color, target_depth, T_init)
+            self._capture()

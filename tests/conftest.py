@@ -27,3 +27,11 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+def pytest_sessionstart(session):
+    # build libgs.so in-tree if it is missing or older than its sources
+    import shutil
+    if shutil.which("nvcc"):
+        from paper_2403_16095_b300.build import build
+        build()

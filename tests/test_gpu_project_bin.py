@@ -1,0 +1,211 @@
+"""GPU parity of the projection (Eq. 1-2) and the tile binning (Sec. 3.1
+pre-sort) against the FP64 oracle, called through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from tests.gpu_util import f32_scene, poses_gpu, rec_fields, to_gpu_gaussians
+
+pytestmark = pytest.mark.gpu
+
+
+def _rast(cams, n, tile=16, mode=None, capacity=None, keep_keys=True):
+    from paper_2403_16095_b300 import Rasterizer
+    from paper_2403_16095_b300 import _abi as A
+    return Rasterizer(cams, n, tile=tile, mode=A.GS_MODE_POSE if mode is None else mode, capacity=capacity,
+                      keep_keys=keep_keys)
+
+
+def _rect_margin(ora):
+    """Distance of every floating rect bound to the integer it is rounded to."""
+    con = ora["conic"]
+    # largest eigenvalue of the 2D covariance = 1 / smallest eigenvalue of the conic
+    tr, det = con[:, 0] + con[:, 2], con[:, 0] * con[:, 2] - con[:, 1] ** 2
+    lam_min_conic = 0.5 * tr - np.sqrt(np.maximum(0.25 * tr ** 2 - det, 0))
+    r3 = 3.0 * np.sqrt(1.0 / np.maximum(lam_min_conic, 1e-300))
+    m = np.abs(r3 - np.round(r3))
+    r = ora["radius"]
+    for c in (0, 1):
+        for s in (-1, 1):
+            v = ora["mean2d"][:, c] - 0.5 + s * r
+            m = np.minimum(m, np.abs(v - np.round(v)))
+    return m
+
+
+def test_projection_matches_oracle():
+    sc, cam, T = synth.tiny_scene()
+    g = to_gpu_gaussians(sc)
+    r = _rast([cam], sc.n)
+    r.reset_status()
+    r.project(g, poses_gpu(T))
+    torch.cuda.synchronize()
+    got = rec_fields(r)
+    ora = oracle.project(f32_scene(sc), cam, T)
+    v = ora["valid"]
+    assert np.array_equal(got["valid"], v)
+    np.testing.assert_allclose(got["mean2d"][v], ora["mean2d"][v], rtol=1e-6, atol=2e-4)
+    np.testing.assert_allclose(got["depth"][v], ora["depth"][v], rtol=1e-6)
+    np.testing.assert_allclose(got["opacity"][v], ora["opacity"][v], rtol=1e-6, atol=1e-7)
+    scale = np.abs(ora["conic"][v]).max(1, keepdims=True)
+    np.testing.assert_allclose(got["conic"][v] / scale, ora["conic"][v] / scale, rtol=0, atol=2e-5)
+    same = np.all(got["rect"][v] == ora["rect"][v], axis=1) & (got["radius"][v] == ora["radius"][v])
+    bad = ~same
+    assert bad.sum() <= 2
+    assert np.all(_rect_margin(ora)[v][bad] < 1e-3), "rect mismatch away from a rounding boundary"
+
+
+def _exp_pose(T, xi):
+    rho, phi = xi[:3], xi[3:]
+    th = np.linalg.norm(phi)
+    K = np.array([[0, -phi[2], phi[1]], [phi[2], 0, -phi[0]], [-phi[1], phi[0], 0]])
+    R = np.eye(3) if th == 0 else np.eye(3) + math.sin(th) / th * K + (1 - math.cos(th)) / th ** 2 * K @ K
+    out = np.zeros((3, 4))
+    out[:, :3] = R @ T[:, :3]
+    out[:, 3] = R @ T[:, 3] + rho
+    return out
+
+
+def test_pose_jacobian_matches_oracle_finite_differences():
+    """The forward-mode d(mean2d, conic, z)/d(rho, phi) of gs_project (POSE mode)
+    equals central differences of the FP64 oracle projection under Exp(xi) T."""
+    sc, cam, _ = synth.fd_scene()
+    T = _exp_pose(np.c_[np.eye(3), np.zeros(3)], np.array([0.03, -0.02, 0.1, 0.05, -0.03, 0.02]))
+    g = to_gpu_gaussians(sc)
+    r = _rast([cam], sc.n)
+    r.reset_status()
+    r.project(g, poses_gpu(T))
+    torch.cuda.synchronize()
+    jac = r.jac.view(-1, 6, 6).cpu().numpy().astype(np.float64)
+    valid = rec_fields(r)["valid"]
+    s64 = f32_scene(sc)
+    h = 1e-6
+    fd = np.zeros((sc.n, 6, 6))
+    for k in range(6):
+        xi = np.zeros(6)
+        xi[k] = h
+        p = oracle.project(s64, cam, _exp_pose(T, xi))
+        m = oracle.project(s64, cam, _exp_pose(T, -xi))
+        for arr, sl in (("mean2d", slice(0, 2)), ("conic", slice(2, 5))):
+            fd[:, sl, k] = (p[arr] - m[arr]) / (2 * h)
+        fd[:, 5, k] = (p["depth"] - m["depth"]) / (2 * h)
+    for row in range(6):
+        scale = np.abs(fd[valid, row, :]).max(axis=1, keepdims=True) + 1e-30
+        err = np.abs(jac[valid, row, :] - fd[valid, row, :]) / scale
+        assert err.max() < 2e-3, (row, err.max())
+
+
+# ------------------------------------------------------------------ binning
+def _synthetic_records(n, cams, tile, seed, ties=True):
+    """Records with random pixel rects and depths (many exact ties)."""
+    rng = np.random.default_rng(seed)
+    F = len(cams)
+    rec = np.zeros((F * n, 16), np.float32)
+    rect = np.zeros((F * n, 4), np.int32)
+    for f, c in enumerate(cams):
+        x0 = rng.integers(0, c.width, n)
+        y0 = rng.integers(0, c.height, n)
+        rect[f * n:(f + 1) * n] = np.c_[x0, y0, np.minimum(c.width - 1, x0 + rng.integers(0, 50, n)),
+                                        np.minimum(c.height - 1, y0 + rng.integers(0, 50, n))]
+    culled = rng.uniform(size=F * n) < 0.1
+    rect[culled] = [1, 1, 0, 0]
+    depth = (rng.choice(np.float32([0.25, 1.0, 1.5, 7.0]), F * n) if ties
+             else rng.uniform(0.2, 50.0, F * n).astype(np.float32))
+    rec[:, 6] = depth
+    rec.view(np.int32)[:, 12:16] = rect
+    ok = rect[:, 0] <= rect[:, 2]
+    touched = np.where(ok, (rect[:, 2] // tile - rect[:, 0] // tile + 1) * (rect[:, 3] // tile - rect[:, 1] // tile + 1), 0)
+    return rec, rect, depth, touched.astype(np.int32)
+
+
+@pytest.mark.parametrize("cams,tile,ties", [
+    ([synth.Camera(128, 96, 1, 1, 0, 0)], 16, True),                        # 48 tiles: 5 radix passes
+    ([synth.Camera(640, 480, 1, 1, 0, 0)], 16, False),                      # 1200 tiles: 6 passes
+    ([synth.Camera(1200, 680, 1, 1, 0, 0)], 8, True),                       # 12750 tiles
+    ([synth.Camera(100, 70, 1, 1, 0, 0), synth.Camera(37, 53, 1, 1, 0, 0),
+      synth.Camera(64, 64, 1, 1, 0, 0)], 16, True),                         # uneven frames, ragged
+    ([synth.Camera(16, 16, 1, 1, 0, 0)], 16, True),                         # a single tile
+])
+def test_bin_tiles_bit_exact(cams, tile, ties):
+    n = 3000
+    rec, rect, depth, touched = _synthetic_records(n, cams, tile, seed=len(cams) * 7 + tile, ties=ties)
+    r = _rast(cams, n, tile=tile, capacity=int(touched.sum()) + 17)
+    r.rec.copy_(torch.from_numpy(rec.reshape(-1)))
+    r.touched.copy_(torch.from_numpy(touched))
+    r.reset_status()
+    r.bin()
+    torch.cuda.synchronize()
+    code, P = r.read_status()
+    assert code == 0 and P == touched.sum()
+    keys, vals, ranges = oracle.bin_tiles(rect, depth, n, tile, cams)
+    assert np.array_equal(r.keys[:P].cpu().numpy().view(np.uint64), keys)
+    assert np.array_equal(r.values[:P].cpu().numpy().view(np.uint32), vals)
+    assert np.array_equal(r.ranges.view(-1, 2).cpu().numpy().view(np.uint32), ranges)
+
+
+def test_bin_tiles_capacity_overflow_sets_status():
+    cams = [synth.Camera(128, 96, 1, 1, 0, 0)]
+    n = 500
+    rec, rect, depth, touched = _synthetic_records(n, cams, 16, seed=3)
+    P = int(touched.sum())
+    r = _rast(cams, n, capacity=P - 1)
+    r.rec.copy_(torch.from_numpy(rec.reshape(-1)))
+    r.touched.copy_(torch.from_numpy(touched))
+    r.reset_status()
+    r.bin()
+    r.forward()  # must be a no-op after the overflow
+    torch.cuda.synchronize()
+    code, need = r.read_status()
+    from paper_2403_16095_b300 import _abi as A
+    assert code == A.GS_ERR_CAPACITY and need == P
+    r.set_capacity(need)
+    r.reset_status()
+    r.bin()
+    torch.cuda.synchronize()
+    assert r.read_status() == (0, P)
+
+
+def test_bin_tiles_all_culled():
+    cams = [synth.Camera(64, 48, 1, 1, 0, 0)]
+    n = 100
+    rec = np.zeros((n, 16), np.float32)
+    rec.view(np.int32)[:, 12:16] = [1, 1, 0, 0]
+    r = _rast(cams, n, capacity=8)
+    r.rec.copy_(torch.from_numpy(rec.reshape(-1)))
+    r.touched.zero_()
+    r.reset_status()
+    r.bin()
+    torch.cuda.synchronize()
+    assert r.read_status() == (0, 0)
+    assert int(r.ranges.abs().sum()) == 0
+
+
+def test_end_to_end_tile_lists_match_oracle_projection():
+    """GPU projection + GPU binning vs oracle binning of the FP64 projection:
+    identical per-tile lists except for Gaussians whose rect sits within FP32
+    rounding of a pixel boundary, or whose depths tie in FP32."""
+    sc, cam, T = synth.tiny_scene()
+    g = to_gpu_gaussians(sc)
+    r = _rast([cam], sc.n, capacity=64)
+    r.render(g, poses_gpu(T))  # grows the pair buffer after the first overflow
+    torch.cuda.synchronize()
+    assert r.read_status()[0] == 0
+    ora = oracle.project(f32_scene(sc), cam, T)
+    rect = np.where(ora["valid"][:, None], ora["rect"], np.array([1, 1, 0, 0]))
+    keys, vals, ranges = oracle.bin_tiles(rect, ora["depth"].astype(np.float32), sc.n, 16, [cam])
+    P = r.read_status()[1]
+    gv = r.values[:P].cpu().numpy()
+    gr = r.ranges.view(-1, 2).cpu().numpy()
+    margin = _rect_margin(ora)
+    for t in range(gr.shape[0]):
+        a = gv[gr[t, 0]:gr[t, 1]]
+        b = vals[ranges[t, 0]:ranges[t, 1]].astype(np.int64)
+        if np.array_equal(a, b):
+            continue
+        diff = np.setxor1d(a, b)
+        assert np.all(margin[diff] < 1e-3), (t, diff)
+        common = [x for x in a if x in set(b)]
+        assert common == [x for x in b if x in set(a)], t
