@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Tracking benchmark of the B300 Gaussian rasterizer (CG-SLAM, arXiv 2403.16095).
+
+Workload: 640x480 frames (fx = fy = 600, principal point at the centre), 300,000
+Gaussians on the surfaces of a seeded 6x5x3 m room with 20 boxes, 10 ground-truth
+poses on a smooth path; each frame starts 2 cm / 1 degree off and runs 30
+tracking iterations (project -> bin -> forward -> POSE backward with the fused
+uncertainty-weighted L1 colour + depth loss, lambda = {0.2, 1.0} -> FP64 pose
+reduction -> Adam step on the pose), captured as one CUDA graph per frame.
+
+A step is one tracked frame (30 iterations). The metric is tracking iterations
+per second: value = 30 * steps * ranks / (max over ranks of the summed device
+time of the steps). L2 (126 MB) is flushed between steps by writing a 512 MB
+buffer outside the timed region; within a frame the iterations run back to back
+as tracking does.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --gpus N > 1 (under torchrun) every rank tracks its own frames
+(independent replicas, no data collective); timing uses a barrier and the max
+over ranks. ``--impl reference`` times the FP64 CPU oracle on this host's cores
+on a bounded sample of the same workload (one iteration per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ITERS = 30
+METRIC = "tracking iters/sec (fwd+pose-bwd) at 640x480/300k Gaussians"
+WORKLOAD = "track-640x480-300k-room"
+# FP32 operations the adjoint performs per blended (pixel, Gaussian) entry in
+# POSE mode: recompute q, G, alpha (13), transmittance recovery (4), channel dot
+# product for colour + depth (7), dL/dalpha and the running suffix sum (5),
+# gradients of mean2d, conic and depth (21), 6x6 pose-Jacobian contraction (72).
+BWD_FLOP_PER_CONTRIB = 122
+FP32_LANES_PER_SM = 128
+N_SM = 148
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    p.add_argument("--tile", type=int, default=16)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-iters", type=int, default=0, help="oracle iterations for the CPU baseline (0 = auto)")
+    return p.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["no samples"]}
+        busy = sorted(sm)[len(sm) // 2:] if len(sm) > 4 else sm  # under load: upper half
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- workload
+def _workload():
+    import synth
+    w = synth.workload("track")
+    starts = [synth.jitter_pose(T, seed=1002 * 100 + k, trans=0.02, rot_deg=1.0) for k, T in enumerate(w["poses"])]
+    return w["scene"], w["cams"][0], w["poses"], starts
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_oracle_iterations(sc, cam, gt_poses, starts, n_iter: int, targets=None):
+    """Times ``n_iter`` tracking iterations of the FP64 oracle (forward + analytic
+    pose gradient + Adam step) on this host's cores; returns (seconds, cores)."""
+    import numpy as np
+
+    import oracle
+    cores = oracle.threads()
+    if targets is None:
+        ref = oracle.render(sc, cam, gt_poses[0])
+        targets = (ref["color"], ref["depth"])
+    L = oracle.LossSpec(0.2, 1.0, 0.0, 0.0, 0.025, targets[0], targets[1])
+    st = np.zeros(25)
+    T = np.asarray(starts[0], np.float64)
+    st[:9] = T[:, :3].reshape(-1)
+    st[9:12] = T[:, 3]
+    t0 = time.perf_counter()
+    for _ in range(n_iter):
+        Tc = np.c_[st[:9].reshape(3, 3), st[9:12]]
+        g = oracle.grad(sc, cam, Tc, L)
+        oracle.adam_step(st, g["pose"])
+    return time.perf_counter() - t0, cores
+
+
+def run_reference(a):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    sc, cam, gt, starts = _workload()
+    import oracle
+    ref = oracle.render(sc, cam, gt[0])
+    targets = (ref["color"], ref["depth"])
+    cpu_oracle_iterations(sc, cam, gt, starts, max(0, a.warmup), targets)
+    secs, cores = cpu_oracle_iterations(sc, cam, gt, starts, a.steps, targets)
+    value = a.steps / secs
+    sample = f"{a.steps} oracle tracking iterations (1 per step) on frame 0 of the workload"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": 0,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * secs / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "frames": 1, "iters_per_frame": ITERS},
+            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU
+def run_ours(a):
+    import numpy as np
+    import torch
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2403_16095_b300.build import build
+    build()
+    from paper_2403_16095_b300 import Gaussians, Rasterizer, Tracker
+    from paper_2403_16095_b300 import _abi as A
+
+    sc, cam, gt, starts = _workload()
+    n_frames = len(gt)
+    g = Gaussians(*(torch.from_numpy(np.ascontiguousarray(getattr(sc, k))).to(dev)
+                    for k in ("means", "log_scales", "quats", "opacity_logit", "colors", "nu")))
+    my_frames = [(rank + k * ws) % n_frames for k in range(a.warmup + a.steps)]
+    # targets: renders at the ground-truth poses of the frames this rank uses
+    # (device-resident inputs of the timed region)
+    r0 = Rasterizer([cam], g.n, tile=a.tile, mode=A.GS_MODE_FWD)
+    tcol, tdep = [None] * n_frames, [None] * n_frames
+    for f in sorted(set(my_frames)):
+        r0.render(g, torch.from_numpy(np.asarray(gt[f], np.float32)).to(dev).reshape(-1))
+        im = r0.frame_images(0)
+        tcol[f] = im["color"].clone()
+        tdep[f] = im["depth"].clone()
+    del r0
+    starts_t = [torch.from_numpy(np.asarray(T, np.float64)).to(dev) for T in starts]
+
+    tr = Tracker(g, cam, tile=a.tile, iters=ITERS, graph=True, timing=True)
+    f0 = my_frames[0]
+    tr.prepare(tcol[f0], tdep[f0], starts_t[f0], headroom=1.6)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def one_step(f, ev0, ev1):
+        ev0.record()
+        tr.set_frame(tcol[f], tdep[f], starts_t[f])
+        tr.run()
+        ev1.record()
+
+    for k in range(a.warmup):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        one_step(my_frames[k], e0, e1)
+    torch.cuda.synchronize()
+    assert tr.rast.read_status()[0] == 0, "warm-up failed (pair capacity?)"
+
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    step_ms, bwd_ms, contrib, t_wall0 = [], [], [], time.perf_counter()
+    for k in range(a.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        one_step(my_frames[a.warmup + k], e0, e1)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        bwd_ms.extend(tr.backward_ms())
+        contrib.append(int(tr.rast.img["n_contrib"].sum()))
+        code, _ = tr.rast.read_status()
+        if code:
+            raise RuntimeError(f"device status {code} during the timed region")
+    barrier()
+    wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t)
+    value = ITERS * a.steps * ws / (total_ms / 1e3)
+
+    # ---- end to end through the public call with pinned host buffers
+    e2e = None
+    if not a.no_e2e:
+        hc = [None if t is None else t.cpu().pin_memory() for t in tcol]
+        hd = [None if t is None else t.cpu().pin_memory() for t in tdep]
+        hT = [torch.from_numpy(np.asarray(T, np.float64)).pin_memory() for T in starts]
+        out = torch.empty(3, 4, dtype=torch.float64).pin_memory()
+        for k in range(a.warmup):
+            f = my_frames[k]
+            tr.track_host(hc[f], hd[f], hT[f], out)
+        barrier()
+        e2e_s = 0.0
+        for k in range(a.steps):
+            f = my_frames[a.warmup + k]
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tr.track_host(hc[f], hd[f], hT[f], out)
+            e2e_s += time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([e2e_s], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(t)
+        h2d = hc[f0].numel() * 4 + hd[f0].numel() * 4 + 12 * 8
+        e2e = {"value": ITERS * a.steps * ws / e2e_s, "unit": "iters/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": 12 * 8 + 4 * 4,
+               "note": "per step: frame RGB-D + start pose host->device, 30 iterations, pose + status device->host"}
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel (the POSE-mode backward)
+    peaks = _peaks()
+    mhz = peaks.get("sm_max_mhz", 2032.0)
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12  # TFLOP/s
+    bwd_avg_ms = statistics.mean(bwd_ms)
+    E = statistics.mean(contrib)
+    achieved = E * BWD_FLOP_PER_CONTRIB / (bwd_avg_ms * 1e-3) / 1e12
+    roof = {"kernel": "k_render_bwd<16,POSE>", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+            "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+            "peak_source": f"148 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (max SM clock)",
+            "flop_per_contribution": BWD_FLOP_PER_CONTRIB, "contributions_per_launch": E,
+            "avg_launch_ms": bwd_avg_ms, "launches": len(bwd_ms)}
+    bwd_share = sum(bwd_ms) / sum(step_ms)
+
+    cpu = None
+    if not a.no_cpu_baseline:
+        n_it = a.cpu_iters or 3
+        import oracle
+        ref = oracle.render(sc, cam, gt[0])
+        secs, cores = cpu_oracle_iterations(sc, cam, gt, starts, n_it, (ref["color"], ref["depth"]))
+        cpu = {"value": n_it / secs, "unit": "iters/s", "cores": cores, "kind": "oracle",
+               "sample": f"{n_it} FP64 oracle tracking iterations (forward + analytic pose gradient + Adam) "
+                         f"on frame 0, 640x480, 300k Gaussians"}
+
+    launches = tr.kernel_launches_per_iteration() * ITERS * a.steps
+    line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "width": 640, "height": 480, "gaussians": int(g.n),
+                       "iters_per_frame": ITERS, "step": "one tracked frame (30 iterations)", "tile": a.tile,
+                       "l2": "flushed between steps (512 MB write, untimed)", "parallelism": f"replicas x{ws}",
+                       "ms_per_iteration": total_ms / (a.steps * ITERS), "wall_s": wall,
+                       "pairs_per_iteration": int(tr.rast.read_status()[1]),
+                       "contributions_per_iteration": E, "bwd_share_of_step": bwd_share},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "context": "paper: 7.89 ms x 15 tracking iterations on an RTX 4090 (Table 5, Replica office-0)"}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -138,6 +138,7 @@ typedef struct {
     float *median;   /* median depth, Eq. 7-8 (0 if T never drops below 0.5)     */
     float *T_final;  /* transmittance after the last blended Gaussian            */
     int32_t *n_last; /* one past the tile-list position of the last blended entry */
+    int32_t *n_contrib; /* number of blended entries per pixel, or NULL            */
 } gs_image;
 
 /* Upstream gradients dL/d(channel) per pixel (same layouts); NULL = zero. */

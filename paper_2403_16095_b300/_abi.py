@@ -64,7 +64,7 @@ class gs_tiles(C.Structure):
 
 class gs_image(C.Structure):
     _fields_ = [("color", _vp), ("depth", _vp), ("alpha", _vp), ("unc", _vp), ("nu_map", _vp),
-                ("median", _vp), ("T_final", _vp), ("n_last", _vp)]
+                ("median", _vp), ("T_final", _vp), ("n_last", _vp), ("n_contrib", _vp)]
 
 
 class gs_image_grad(C.Structure):
@@ -218,8 +218,9 @@ def gs_bin_tiles(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tensor, tiles
 
 
 def _image(img: dict) -> gs_image:
-    return gs_image(*(_ptr(img.get(k), torch.int32 if k == "n_last" else torch.float32, k)
-                      for k in ("color", "depth", "alpha", "unc", "nu_map", "median", "T_final", "n_last")))
+    return gs_image(*(_ptr(img.get(k), torch.int32 if k in ("n_last", "n_contrib") else torch.float32, k)
+                      for k in ("color", "depth", "alpha", "unc", "nu_map", "median", "T_final", "n_last",
+                                "n_contrib")))
 
 
 def gs_render_fwd(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tensor, values: torch.Tensor,

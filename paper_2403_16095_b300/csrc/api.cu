@@ -165,7 +165,8 @@ gs_status gs_render_fwd(const gs_projected *proj, const gs_tiles *tiles, int n_f
     GS_TRY(check_tiles(tiles, ft));
     if (!out || !out->color || !out->T_final || !out->n_last) return fail(GS_ERR_INVALID_ARG, "image color/T_final/n_last required");
     if (!status) return fail(GS_ERR_INVALID_ARG, "status NULL");
-    gs::ImagePtrs ip{out->color, out->depth, out->alpha, out->unc, out->nu_map, out->median, out->T_final, out->n_last};
+    gs::ImagePtrs ip{out->color, out->depth, out->alpha, out->unc, out->nu_map, out->median, out->T_final, out->n_last,
+                     out->n_contrib};
     return cuda_status(gs::launch_render_fwd(proj->rec, tiles->values, tiles->ranges, ft, obs_depth, ip, status, stream),
                        "gs_render_fwd");
 }
@@ -212,7 +213,8 @@ gs_status gs_render_bwd(const gs_projected *proj, const gs_tiles *tiles, int n_f
     } else {
         return fail(GS_ERR_INVALID_ARG, "either dL or loss is required");
     }
-    gs::ImagePtrs ip{fwd->color, fwd->depth, fwd->alpha, fwd->unc, fwd->nu_map, fwd->median, fwd->T_final, fwd->n_last};
+    gs::ImagePtrs ip{fwd->color, fwd->depth, fwd->alpha, fwd->unc, fwd->nu_map, fwd->median, fwd->T_final, fwd->n_last,
+                     fwd->n_contrib};
     const int N = proj->n_gaussians;
     const int M = N * n_frames;
     const int per_frame = gs_pose_partials_per_frame(mode, N, n_frames, cams, opts->tile);

@@ -44,7 +44,7 @@ struct GaussPtrs {
 
 struct ImagePtrs {
     float *color, *depth, *alpha, *unc, *nu_map, *median, *T_final;
-    int32_t *n_last;
+    int32_t *n_last, *n_contrib;
 };
 
 struct LossParams {

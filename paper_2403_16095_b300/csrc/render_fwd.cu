@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(TILE *TILE)
 
     float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, dep = 0.f, opa = 0.f, unc = 0.f, nus = 0.f, med = 0.f;
     uint32_t last = range.x;
+    int n_blend = 0;
     bool done = !inside;
 
     for (uint32_t base = range.x; base < range.y; base += BATCH) {
@@ -82,6 +83,7 @@ __global__ void __launch_bounds__(TILE *TILE)
                 if (T >= 0.5f && Tn < 0.5f) med = b.z;
                 T = Tn;
                 last = base + k + 1;
+                ++n_blend;
             }
         }
     }
@@ -98,6 +100,7 @@ __global__ void __launch_bounds__(TILE *TILE)
     if (out.median) out.median[pix] = med;
     out.T_final[pix] = T;
     out.n_last[pix] = (int32_t)last;
+    if (out.n_contrib) out.n_contrib[pix] = n_blend;
 }
 
 }  // namespace

@@ -15,7 +15,7 @@ import torch
 from . import _abi as A
 from ._abi import Gaussians
 
-CHANNELS = ("color", "depth", "alpha", "unc", "nu_map", "median", "T_final", "n_last")
+CHANNELS = ("color", "depth", "alpha", "unc", "nu_map", "median", "T_final", "n_last", "n_contrib")
 
 
 def _pix(cams) -> int:
@@ -59,6 +59,7 @@ class Rasterizer:
             "median": torch.empty(P, dtype=torch.float32, device=dev),
             "T_final": torch.empty(P, dtype=torch.float32, device=dev),
             "n_last": torch.empty(P, dtype=torch.int32, device=dev),
+            "n_contrib": torch.empty(P, dtype=torch.int32, device=dev),
         }
         self.keep_keys = keep_keys
         self.values = self.keys = self.bin_ws = None
@@ -214,11 +215,17 @@ class Tracker:
 
     def __init__(self, g: Gaussians, cam, tile: int = 16, iters: int = 30, lam=(0.2, 1.0), unc_tau: float = 0.025,
                  lr_rot: float = 0.0015, lr_trans: float = 0.00215, jclamp: float = 1.3, graph: bool = True,
-                 capacity: Optional[int] = None):
+                 capacity: Optional[int] = None, timing: bool = False):
         self.g = g
         self.cam = cam
         self.iters = iters
         self.graph_enabled = graph
+        # optional per-iteration CUDA events around each backward launch (recorded
+        # inside the captured graph as event nodes), for per-kernel timing
+        self.timing = timing
+        self.bwd_events = ([(torch.cuda.Event(enable_timing=True, external=True),
+                             torch.cuda.Event(enable_timing=True, external=True)) for _ in range(iters)]
+                           if timing else None)
         dev = g.means.device
         self.rast = Rasterizer([cam], g.n, tile=tile, mode=A.GS_MODE_POSE, capacity=capacity, jclamp=jclamp)
         H, W = int(cam.height), int(cam.width)
@@ -233,28 +240,41 @@ class Tracker:
         self.graph = None
 
     # one iteration, enqueued on `stream`
-    def _iteration(self, stream=None):
+    def _iteration(self, stream=None, it: int = 0):
         r = self.rast
         r.project(self.g, self.T_cw, stream)
         r.bin(stream)
         r.forward(self.target_depth, stream)
+        if self.bwd_events is not None:
+            self.bwd_events[it][0].record(stream)
         r.backward(obs_depth=self.target_depth, loss=self.loss, stream=stream)
+        if self.bwd_events is not None:
+            self.bwd_events[it][1].record(stream)
         r.reduce_pose(stream)
         A.gs_pose_adam_step(self.state, r.pose_grad, self.T_cw, 1, self.adam, r.status, stream)
 
-    def launches_per_iteration(self) -> int:
-        """Kernel launches (and memsets) one iteration enqueues."""
+    def kernel_launches_per_iteration(self) -> int:
+        """libgs kernels one iteration launches (memsets not counted): project,
+        count + scan + emit, 3 per radix pass, ranges, forward, backward,
+        pose reduction, Adam step."""
         bits = 32 + max(0, (self.rast.n_tiles - 1).bit_length())
         passes = (bits + 7) // 8
-        return 1 + (1 + 3 + 3 * passes + 1 + 1) + 1 + 1 + 1 + 1
+        return 1 + 3 + 3 * passes + 1 + 1 + 1 + 1 + 1
 
     def _capture(self):
+        """Capture all ``iters`` iterations of a frame in one CUDA graph."""
         self.graph = torch.cuda.CUDAGraph()
         with torch.cuda.stream(self.stream):
             self._iteration(self.stream)  # warm-up outside capture
         self.stream.synchronize()
         with torch.cuda.graph(self.graph, stream=self.stream):
-            self._iteration(self.stream)
+            for it in range(self.iters):
+                self._iteration(self.stream, it)
+
+    def backward_ms(self) -> list:
+        """Per-iteration duration of the backward kernel in the last frame (needs
+        timing=True and a completed frame)."""
+        return [a.elapsed_time(b) for a, b in self.bwd_events]
 
     def set_frame(self, target_color: torch.Tensor, target_depth: torch.Tensor, T_init: torch.Tensor) -> None:
         self.target_color.copy_(target_color.reshape(-1), non_blocking=True)
@@ -269,12 +289,27 @@ class Tracker:
         cur = torch.cuda.current_stream()
         self.stream.wait_stream(cur)
         with torch.cuda.stream(self.stream):
-            for _ in range(self.iters):
-                if self.graph is not None:
-                    self.graph.replay()
-                else:
-                    self._iteration(self.stream)
+            if self.graph is not None:
+                self.graph.replay()
+            else:
+                for it in range(self.iters):
+                    self._iteration(self.stream, it)
         cur.wait_stream(self.stream)
+
+    def track_host(self, target_color, target_depth, T_init, out=None) -> torch.Tensor:
+        """End-to-end call with host buffers: copies the frame's RGB-D target and
+        initial pose (pinned host tensors) to the device, tracks, and copies the
+        refined pose (FP64 [3,4]) back to ``out`` (pinned host) or a new tensor."""
+        dev = self.state.device
+        tc = target_color.to(dev, non_blocking=True)
+        td = target_depth.to(dev, non_blocking=True)
+        T0 = T_init.to(dev, non_blocking=True)
+        T = self.track(tc, td, T0)
+        if out is None:
+            return T.cpu()
+        out.copy_(T, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return out
 
     def track(self, target_color, target_depth, T_init, max_retries: int = 3) -> torch.Tensor:
         """Track one frame; returns the refined pose [3,4] (FP64, on device).
