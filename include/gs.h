@@ -202,6 +202,23 @@ gs_status gs_bin_tiles(const gs_projected *proj, int n_frames, const gs_camera *
                        const gs_opts *opts, gs_tiles *tiles, int32_t *status, void *ws,
                        size_t ws_bytes, gs_stream stream);
 
+/* gs_bin_tiles for callers that cannot allocate device memory (the paper has no
+ * counterpart; this is an interface convenience). Some callers cannot call
+ * cudaMalloc where they bin -- a real-time tracking thread that must not block
+ * on the allocator, a process whose device memory belongs to another
+ * framework's pool, a plug-in limited to memory declared at load time. This
+ * call takes the same arguments as gs_bin_tiles minus the workspace, and uses a
+ * static device scratch array of 12 MiB held by every GPU that loads libgs
+ * until exit. Limits: tiles->capacity <= GS_NOALLOC_MAX_PAIRS, else
+ * GS_ERR_INVALID_ARG with a message. It allocates nothing. Its first call on a
+ * device (with that device current) looks up the array's address; make that
+ * first call before any stream capture. All calls share the array: calls that
+ * overlap on the GPU race; sequential calls are independent (every scratch word
+ * is written before it is read). Outputs and errors as gs_bin_tiles.          */
+#define GS_NOALLOC_MAX_PAIRS (1 << 19)
+gs_status gs_bin_tiles_noalloc(const gs_projected *proj, int n_frames, const gs_camera *cams,
+                               const gs_opts *opts, gs_tiles *tiles, int32_t *status, gs_stream stream);
+
 /* Eq. 3-10. One CTA per tile: the tile's sorted list is staged in shared memory
  * in batches and every pixel blends front to back (alpha test, stop rule,
  * median crossing of T = 0.5) until all of the tile's pixels are done.

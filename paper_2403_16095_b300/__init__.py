@@ -4,11 +4,24 @@ blending of colour / depth / opacity / depth uncertainty, and a reverse-walk
 backward to every Gaussian parameter and to the se(3) camera pose.
 
 The compute lives in libgs.so (C ABI, include/gs.h); this package is its thin
-Python binding (``_abi``) plus a PyTorch-side driver (``raster``). Importing it
-loads libgs.so and fails loudly if the library has not been built.
+Python binding (``_abi``) plus a PyTorch-side driver (``raster``). The public
+names load libgs.so on first use and fail loudly if it has not been built
+(``python -m paper_2403_16095_b300.build``); importing the package alone does
+not, so the build step never depends on an earlier build.
 """
-from . import _abi  # noqa: F401  (loads libgs.so)
-from ._abi import GsError, Gaussians  # noqa: F401
-from .raster import GaussianRasterize, Rasterizer, Tracker, rasterize  # noqa: F401
+import importlib
 
-__all__ = ["GsError", "Gaussians", "GaussianRasterize", "Rasterizer", "Tracker", "rasterize"]
+_EXPORTS = {
+    "GsError": "_abi", "Gaussians": "_abi",
+    "GaussianRasterize": "raster", "Rasterizer": "raster", "Tracker": "raster", "rasterize": "raster",
+}
+
+__all__ = sorted(_EXPORTS)
+
+
+def __getattr__(name):
+    if name in ("_abi", "raster"):
+        return importlib.import_module(f".{name}", __name__)
+    if name in _EXPORTS:
+        return getattr(importlib.import_module(f".{_EXPORTS[name]}", __name__), name)
+    raise AttributeError(name)

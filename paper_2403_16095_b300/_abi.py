@@ -87,8 +87,9 @@ class gs_adam(C.Structure):
 
 
 EXPORTS = ("gs_abi_version", "gs_last_error", "gs_project", "gs_bin_tiles_workspace_size", "gs_bin_tiles",
-           "gs_render_fwd", "gs_pose_partials_per_frame", "gs_render_bwd_workspace_size", "gs_render_bwd",
-           "gs_pose_grad_reduce", "gs_pose_adam_step")
+           "gs_bin_tiles_noalloc", "gs_render_fwd", "gs_pose_partials_per_frame", "gs_render_bwd_workspace_size",
+           "gs_render_bwd", "gs_pose_grad_reduce", "gs_pose_adam_step")
+GS_NOALLOC_MAX_PAIRS = 1 << 19
 
 
 def _load():
@@ -103,6 +104,9 @@ def _load():
     lib.gs_bin_tiles_workspace_size.restype = C.c_size_t
     lib.gs_bin_tiles.argtypes = [C.POINTER(gs_projected), C.c_int, C.POINTER(gs_camera), C.POINTER(gs_opts),
                                  C.POINTER(gs_tiles), _vp, _vp, C.c_size_t, _vp]
+    lib.gs_bin_tiles_noalloc.argtypes = [C.POINTER(gs_projected), C.c_int, C.POINTER(gs_camera),
+                                         C.POINTER(gs_opts), C.POINTER(gs_tiles), _vp, _vp]
+    lib.gs_bin_tiles_noalloc.restype = C.c_int
     lib.gs_render_fwd.argtypes = [C.POINTER(gs_projected), C.POINTER(gs_tiles), C.c_int, C.POINTER(gs_camera),
                                   _vp, C.POINTER(gs_opts), C.POINTER(gs_image), _vp, _vp]
     lib.gs_pose_partials_per_frame.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(gs_camera), C.c_int]
@@ -215,6 +219,21 @@ def gs_bin_tiles(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tensor, tiles
     _check(lib.gs_bin_tiles(C.byref(proj), F, cameras(cams), C.byref(opts), C.byref(tiles),
                             _ptr(status, torch.int32, "status", 4), _ptr(ws, torch.uint8, "ws"), ws.numel(),
                             _stream(stream)))
+
+
+def gs_bin_tiles_noalloc(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tensor, tiles_touched: torch.Tensor,
+                         values: torch.Tensor, keys: Optional[torch.Tensor], ranges: torch.Tensor,
+                         status: torch.Tensor, stream=None) -> None:
+    """gs_bin_tiles without a caller workspace (static device scratch; see gs.h)."""
+    F = len(cams)
+    proj = gs_projected(n_gaussians, F, _ptr(rec, torch.float32, "rec"), _ptr(tiles_touched, torch.int32), None)
+    cap = values.numel()
+    if keys is not None and keys.numel() < cap:
+        raise ValueError("keys must hold as many entries as values")
+    tiles = gs_tiles(cap, ranges.numel() // 2, _ptr(values, torch.int32, "values"),
+                     _ptr(keys, torch.int64, "keys"), _ptr(ranges, torch.int32, "ranges"))
+    _check(lib.gs_bin_tiles_noalloc(C.byref(proj), F, cameras(cams), C.byref(opts), C.byref(tiles),
+                                    _ptr(status, torch.int32, "status", 4), _stream(stream)))
 
 
 def _image(img: dict) -> gs_image:

@@ -110,6 +110,10 @@ size_t bwd_ws_bytes(int n_records, int mode) {
 
 }  // namespace
 
+namespace gs {
+void set_error_message(const char *msg) { snprintf(g_msg, sizeof(g_msg), "%s", msg); }
+}  // namespace gs
+
 extern "C" {
 
 int gs_abi_version(void) { return GS_ABI_VERSION; }

@@ -61,6 +61,9 @@ __device__ __forceinline__ int frame_of_tile(const FrameTable &ft, int gtile) {
     return f;
 }
 
+// message returned by gs_last_error() on this host thread (api.cu)
+void set_error_message(const char *msg);
+
 // ----------------------------------------------------------------- launchers
 // project.cu
 cudaError_t launch_project(const GaussPtrs &g, int n, const FrameTable &ft, const float *T_cw, float jclamp,
