@@ -124,7 +124,8 @@ typedef struct {
     uint32_t *values;     /* [capacity] record index of each pair, sorted by
                              (tile id, float bits of depth, record index)      */
     uint64_t *keys;       /* [capacity] sorted keys (tile << 32 | depth bits), or NULL */
-    uint32_t *ranges;     /* [n_tiles][2] [start, end) of each tile's pairs    */
+    uint32_t *ranges;     /* [n_tiles][2] [start, end) of each tile's pairs;
+                             an empty tile has start == end                    */
 } gs_tiles;
 
 /* Rendered channels (Eq. 3-10), device, FP32 except n_last. A NULL member is not
@@ -168,7 +169,7 @@ typedef struct {
     float lr_rot, lr_trans, beta1, beta2, eps;
 } gs_adam;
 
-#define GS_POSE_STATE_DOUBLES 25  /* R[9], t[3], m[6], v[6], step */
+#define GS_POSE_STATE_DOUBLES 28  /* R[9], t[3], m[6], v[6], step, beta1^step, beta2^step, unused */
 
 /* ------------------------------------------------------------------ calls */
 
@@ -232,35 +233,44 @@ gs_status gs_render_fwd(const gs_projected *proj, const gs_tiles *tiles, int n_f
  * storing it. Per-pixel dL/d(channel) come from `dL` or, when `loss` is not
  * NULL, from the fused loss above (dL is then ignored).
  *   POSE mode: every pixel contracts its gradient w.r.t. (mean2d, conic, z) of
- *     each blended Gaussian with that record's pose_jac and the tile's pixels
- *     are reduced by warp shuffles and a block tree into one FP64 partial per
- *     tile: pose_partials[f][local tile][6].
+ *     each blended Gaussian with that record's pose_jac; the tile's pixels are
+ *     reduced by warp shuffles and a fixed block tree into one compensated
+ *     partial per tile: pose_partials[f][local tile][6].
  *   FULL mode: per-record gradients of (mean2d, conic, opacity, z, nu, RGB) are
  *     accumulated (warp-reduced, then atomics), chained through the projection
- *     to `grads` (needs `g` and T_cw) and the pose partials of each block of 256
- *     records are written to pose_partials[f][block][6].
- * Unused partial slots are zeroed. ws: gs_render_bwd_workspace_size bytes.  */
+ *     to `grads` (needs `g` and T_cw) and the pose partial of each block of 256
+ *     records is written to pose_partials[f][block][6].
+ * Partials are double-floats: float [F][K][6][2] = (hi, lo) with value hi + lo,
+ * K = gs_pose_partials_per_frame(); unused slots are zeroed. If pose_grad is
+ * not NULL, the last CTA of each frame also reduces that frame's partials into
+ * pose_grad[f][6] (FP64), exactly as gs_pose_grad_reduce would (bit-identical),
+ * saving a launch. ws: gs_render_bwd_workspace_size bytes, 256-byte aligned. */
 int gs_pose_partials_per_frame(int mode, int n_gaussians, int n_frames, const gs_camera *cams, int tile);
 size_t gs_render_bwd_workspace_size(int n_records, int mode);
 gs_status gs_render_bwd(const gs_projected *proj, const gs_tiles *tiles, int n_frames,
                         const gs_camera *cams, const float *T_cw, const gs_gaussians *g,
                         const float *obs_depth, const gs_image *fwd, const gs_image_grad *dL,
                         const gs_loss *loss, const gs_opts *opts, gs_grads *grads,
-                        double *pose_partials, const int32_t *status, void *ws, size_t ws_bytes,
-                        gs_stream stream);
+                        float *pose_partials, double *pose_grad, const int32_t *status, void *ws,
+                        size_t ws_bytes, gs_stream stream);
 
 /* Deterministic pose-gradient reduction (Sec. 3.4): pose_grad[f][k] =
- * sum_j partials[f][j][k] in FP64 with Neumaier compensation and a fixed
- * reduction tree (bit-identical across runs). pose_grad: device [n_frames][6],
- * (rho, phi) of the left perturbation Exp(xi) T_cw.                          */
-gs_status gs_pose_grad_reduce(const double *partials, int n_frames, int per_frame,
+ * sum_j partials[f][j][k], summed as double-floats (FP32 hi/lo pairs with
+ * TwoSum compensation, ~48-bit precision; B300 runs FP64 at a small fraction
+ * of its FP32 rate) in a fixed order, the final value in FP64; bit-identical
+ * across runs. partials: float [n_frames][per_frame][6][2]; pose_grad: device
+ * double [n_frames][6], (rho, phi) of the left perturbation Exp(xi) T_cw.    */
+gs_status gs_pose_grad_reduce(const float *partials, int n_frames, int per_frame,
                               double *pose_grad, const int32_t *status, gs_stream stream);
 
 /* One Adam step per frame on the pose in the {so(3) | T} form of Sec. 3.4:
- * g_t = g_rho, g_R = g_phi - t x g_rho; d = -lr * mhat / (sqrt(vhat) + eps);
- * R <- Exp(d_R) R, t <- t + d_t; the FP64 state (GS_POSE_STATE_DOUBLES per frame:
- * R, t, Adam moments, step count) is updated in place and T_cw (float [F][3][4])
- * rewritten for the next gs_project.                                         */
+ * g_t = g_rho, g_R = g_phi - t x g_rho; moments m, v in FP64;
+ * d = -lr * mhat / (sqrt(vhat) + eps) (bias corrections from beta^t kept in the
+ * state; d evaluated in FP32); R <- Exp(d_R) R, t <- t + d_t in FP64. The state
+ * (GS_POSE_STATE_DOUBLES per frame: R[9], t[3], m[6], v[6], step, beta1^step,
+ * beta2^step, unused; start with m = v = step = 0 and beta powers = 1) is
+ * updated in place and T_cw (float [F][3][4]) rewritten for the next
+ * gs_project.                                                                */
 gs_status gs_pose_adam_step(double *state, const double *pose_grad, float *T_cw, int n_frames,
                             const gs_adam *adam, const int32_t *status, gs_stream stream);
 

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libgs.so")
 GS_MAX_FRAMES = 64
 GS_REC_FLOATS = 16
 GS_JAC_FLOATS = 36
-GS_POSE_STATE_DOUBLES = 25
+GS_POSE_STATE_DOUBLES = 28
 GS_MODE_FWD, GS_MODE_POSE, GS_MODE_FULL = 0, 1, 2
 GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_UNSUPPORTED = range(6)
 STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CAPACITY", 3: "GS_ERR_CUDA",
@@ -116,7 +116,7 @@ def _load():
     lib.gs_render_bwd.argtypes = [C.POINTER(gs_projected), C.POINTER(gs_tiles), C.c_int, C.POINTER(gs_camera),
                                   _vp, C.POINTER(gs_gaussians), _vp, C.POINTER(gs_image),
                                   C.POINTER(gs_image_grad), C.POINTER(gs_loss), C.POINTER(gs_opts),
-                                  C.POINTER(gs_grads), _vp, _vp, _vp, C.c_size_t, _vp]
+                                  C.POINTER(gs_grads), _vp, _vp, _vp, _vp, C.c_size_t, _vp]
     lib.gs_pose_grad_reduce.argtypes = [_vp, C.c_int, C.c_int, _vp, _vp, _vp]
     lib.gs_pose_adam_step.argtypes = [_vp, _vp, _vp, C.c_int, C.POINTER(gs_adam), _vp, _vp]
     for name in ("gs_project", "gs_bin_tiles", "gs_render_fwd", "gs_render_bwd", "gs_pose_grad_reduce",
@@ -265,8 +265,8 @@ def gs_render_bwd_workspace_size(n_records: int, mode: int) -> int:
 def gs_render_bwd(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tensor, pose_jac: Optional[torch.Tensor],
                   values: torch.Tensor, ranges: torch.Tensor, T_cw: Optional[torch.Tensor], g: Optional[Gaussians],
                   obs_depth: Optional[torch.Tensor], fwd: dict, dL: Optional[dict], loss: Optional[dict],
-                  grads: Optional[dict], pose_partials: torch.Tensor, status: torch.Tensor, ws: torch.Tensor,
-                  stream=None) -> None:
+                  grads: Optional[dict], pose_partials: torch.Tensor, pose_grad: Optional[torch.Tensor],
+                  status: torch.Tensor, ws: torch.Tensor, stream=None) -> None:
     F = len(cams)
     proj = gs_projected(n_gaussians, F, _ptr(rec, torch.float32, "rec"), 1,
                         _ptr(pose_jac, torch.float32, "pose_jac"))
@@ -291,14 +291,15 @@ def gs_render_bwd(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tensor, pose
                              _ptr(obs_depth, torch.float32, "obs_depth"), C.byref(_image(fwd)),
                              C.byref(gd) if gd is not None else None, C.byref(gl) if gl is not None else None,
                              C.byref(opts), C.byref(gg) if gg is not None else None,
-                             _ptr(pose_partials, torch.float64, "pose_partials"),
+                             _ptr(pose_partials, torch.float32, "pose_partials"),
+                             _ptr(pose_grad, torch.float64, "pose_grad", 6 * F),
                              _ptr(status, torch.int32, "status", 4), _ptr(ws, torch.uint8, "ws"), ws.numel(),
                              _stream(stream)))
 
 
 def gs_pose_grad_reduce(partials: torch.Tensor, n_frames: int, per_frame: int, pose_grad: torch.Tensor,
                         status: torch.Tensor, stream=None) -> None:
-    _check(lib.gs_pose_grad_reduce(_ptr(partials, torch.float64, "partials", n_frames * per_frame * 6), n_frames,
+    _check(lib.gs_pose_grad_reduce(_ptr(partials, torch.float32, "partials", n_frames * per_frame * 12), n_frames,
                                    per_frame, _ptr(pose_grad, torch.float64, "pose_grad", 6 * n_frames),
                                    _ptr(status, torch.int32, "status", 4), _stream(stream)))
 

@@ -102,11 +102,14 @@ gs_status check_tiles(const gs_tiles *t, const gs::FrameTable &ft) {
         if (st__ != GS_OK) return st__;        \
     } while (0)
 
+// Backward workspace: [FULL: per-record 2D gradient accumulators][per-frame
+// arrival counters of the fused pose reduction, GS_MAX_FRAMES x uint32].
 constexpr size_t kAlign = 256;
-size_t bwd_ws_bytes(int n_records, int mode) {
-    if (mode != GS_MODE_FULL) return kAlign;
+size_t grad2d_bytes(int n_records, int mode) {
+    if (mode != GS_MODE_FULL) return 0;
     return (((size_t)n_records * gs::kGrad2d * sizeof(float)) + kAlign - 1) / kAlign * kAlign;
 }
+size_t bwd_ws_bytes(int n_records, int mode) { return grad2d_bytes(n_records, mode) + kAlign; }
 
 }  // namespace
 
@@ -191,7 +194,8 @@ size_t gs_render_bwd_workspace_size(int n_records, int mode) { return bwd_ws_byt
 gs_status gs_render_bwd(const gs_projected *proj, const gs_tiles *tiles, int n_frames, const gs_camera *cams,
                         const float *T_cw, const gs_gaussians *g, const float *obs_depth, const gs_image *fwd,
                         const gs_image_grad *dL, const gs_loss *loss, const gs_opts *opts, gs_grads *grads,
-                        double *pose_partials, const int32_t *status, void *ws, size_t ws_bytes, gs_stream stream) {
+                        float *pose_partials, double *pose_grad, const int32_t *status, void *ws, size_t ws_bytes,
+                        gs_stream stream) {
     GS_TRY(check_opts(opts));
     const int mode = opts->mode;
     if (mode != GS_MODE_POSE && mode != GS_MODE_FULL) return fail(GS_ERR_INVALID_ARG, "backward needs POSE or FULL mode");
@@ -222,38 +226,43 @@ gs_status gs_render_bwd(const gs_projected *proj, const gs_tiles *tiles, int n_f
     const int N = proj->n_gaussians;
     const int M = N * n_frames;
     const int per_frame = gs_pose_partials_per_frame(mode, N, n_frames, cams, opts->tile);
+    const size_t need = bwd_ws_bytes(M, mode);
+    if (!ws || ws_bytes < need || !aligned(ws, 256))
+        return fail(GS_ERR_INVALID_ARG, "workspace %zu bytes < %zu needed (256-aligned)", ws_bytes, need);
+    unsigned *counters = reinterpret_cast<unsigned *>(static_cast<char *>(ws) + grad2d_bytes(M, mode));
     cudaError_t e;
+    if (pose_grad && (e = cudaMemsetAsync(counters, 0, sizeof(unsigned) * n_frames, stream)) != cudaSuccess)
+        return cuda_status(e, "gs_render_bwd memset");
     if (mode == GS_MODE_POSE) {
         if (!proj->pose_jac) return fail(GS_ERR_INVALID_ARG, "POSE mode needs projected.pose_jac");
         for (int f = 0; f < n_frames; ++f) {
             const int used = ft.f[f].tiles_x * ft.f[f].tiles_y;
             if (used < per_frame) {
-                e = cudaMemsetAsync(pose_partials + ((size_t)f * per_frame + used) * 6, 0,
-                                    sizeof(double) * 6 * (size_t)(per_frame - used), stream);
+                e = cudaMemsetAsync(pose_partials + ((size_t)f * per_frame + used) * 12, 0,
+                                    sizeof(float) * 12 * (size_t)(per_frame - used), stream);
                 if (e != cudaSuccess) return cuda_status(e, "gs_render_bwd memset");
             }
         }
         return cuda_status(gs::launch_render_bwd(mode, proj->rec, proj->pose_jac, tiles->values, tiles->ranges, ft,
-                                                 obs_depth, ip, lp, nullptr, pose_partials, per_frame, status, stream),
+                                                 obs_depth, ip, lp, nullptr, pose_partials, per_frame, pose_grad,
+                                                 counters, status, stream),
                            "gs_render_bwd");
     }
     GS_TRY(check_gauss(g));
     if (g->n != N) return fail(GS_ERR_INVALID_ARG, "gaussians.n != projected.n_gaussians");
     if (!T_cw || !grads) return fail(GS_ERR_INVALID_ARG, "FULL mode needs T_cw and grads");
-    const size_t need = bwd_ws_bytes(M, mode);
-    if (!ws || ws_bytes < need || !aligned(ws, 256)) return fail(GS_ERR_INVALID_ARG, "workspace %zu bytes < %zu needed (256-aligned)", ws_bytes, need);
     float *grad2d = static_cast<float *>(ws);
     if ((e = cudaMemsetAsync(grad2d, 0, sizeof(float) * gs::kGrad2d * (size_t)M, stream)) != cudaSuccess)
         return cuda_status(e, "gs_render_bwd memset");
     if ((e = gs::launch_render_bwd(mode, proj->rec, nullptr, tiles->values, tiles->ranges, ft, obs_depth, ip, lp,
-                                   grad2d, pose_partials, per_frame, status, stream)) != cudaSuccess)
+                                   grad2d, pose_partials, per_frame, nullptr, nullptr, status, stream)) != cudaSuccess)
         return cuda_status(e, "gs_render_bwd");
     return cuda_status(gs::launch_project_bwd(gauss_ptrs(g), N, ft, T_cw, opts->jclamp, proj->rec, grad2d, *grads,
-                                              pose_partials, per_frame, status, stream),
+                                              pose_partials, per_frame, pose_grad, counters, status, stream),
                        "gs_render_bwd (projection adjoint)");
 }
 
-gs_status gs_pose_grad_reduce(const double *partials, int n_frames, int per_frame, double *pose_grad,
+gs_status gs_pose_grad_reduce(const float *partials, int n_frames, int per_frame, double *pose_grad,
                               const int32_t *status, gs_stream stream) {
     if (!partials || !pose_grad || !status) return fail(GS_ERR_INVALID_ARG, "NULL pointer");
     if (n_frames < 1 || n_frames > GS_MAX_FRAMES || per_frame < 1) return fail(GS_ERR_INVALID_ARG, "bad n_frames/per_frame");

@@ -1,21 +1,24 @@
 // Tile binning: the "pre-sort of all visible Gaussians from near to far" of
-// CG-SLAM Sec. 3.1, done per tile.
+// CG-SLAM Sec. 3.1, done per tile, as an MSD radix sort of the 64-bit keys
+// (global tile id << 32 | float bits of depth) with the record index as the
+// final tie-break:
 //
-//   k_count / k_scan_top   exclusive scan of tiles_touched over the records
-//                          (fixed grid of 4 CTAs per SM, each owning a contiguous
-//                          slice), total pair count P and the capacity check.
-//   k_emit                 one (key, record) pair per overlapped tile,
-//                          key = (global tile id << 32) | float bits of depth.
-//   k_radix_hist / k_radix_scan / k_radix_scatter
-//                          one stable LSD pass per 8-bit digit over only the key
-//                          bits that can be non-zero (32 depth bits + the bits of
-//                          the largest tile id). Each pass: per-CTA digit counts
-//                          (digit-major, so one flat exclusive scan yields every
-//                          CTA's output offsets), then a scatter whose in-CTA
-//                          ranks come from __match_any_sync peer groups processed
-//                          in input order -- the order of equal keys is preserved,
-//                          so the output is bit-exact regardless of the grid.
-//   k_ranges               [start, end) of every tile from the sorted keys.
+//   k_tile_count  MSD digit = the tile id: one atomic increment per
+//                 (record, overlapped tile) into the tile's counter (the
+//                 `ranges` buffer doubles as the counters).
+//   k_tile_scan   exclusive scan of the counters -> each tile's [start, start)
+//                 cursor, total pair count P and the capacity check.
+//   k_tile_fill   each pair claims a slot in its tile's bucket and stores the
+//                 low key (depth bits << 32 | record); after this pass every
+//                 tile's cursor equals its end, so `ranges` is final.
+//   k_tile_sort   one CTA per tile: stable LSD radix sort (8-bit digits) of the
+//                 bucket's low keys over the depth bits and the record-index
+//                 bits, in shared memory (global memory for buckets larger than
+//                 kSmemKeys). Digits that are constant over a bucket are
+//                 skipped. Low keys are unique within a bucket, so the order of
+//                 the atomic fill does not matter: the output is bit-exact, the
+//                 same as a stable sort of the 64-bit keys emitted in record
+//                 order, and independent of the launch configuration.
 #include <climits>
 
 #include "gs_internal.cuh"
@@ -25,65 +28,50 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kScanTopThreads = 1024;
-static_assert(kScanBlocks <= kScanTopThreads, "top-level scan handles one value per thread");
-static_assert((kRadix * kSortBlocks) % (kScanTopThreads * 4) == 0, "digit scan uses uint4 chunks");
+constexpr int kScanThreads = 1024;
+constexpr int kSmemKeys = 2048;  // bucket size sorted entirely in shared memory
 
-__device__ __forceinline__ void slice(long long total, int b, int nb, long long &lo, long long &hi) {
-    lo = total * b / nb;
-    hi = total * (b + 1) / nb;
-}
+__device__ __forceinline__ bool status_ok(const int32_t *status) { return status[0] == 0; }
 
-// Exclusive block scan of one int per thread (256 threads); returns the block total.
-__device__ __forceinline__ int block_excl_scan(int v, int &total, int *s_warp) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int x = v;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, off);
-        if (lane >= off) x += y;
-    }
-    if (lane == 31) s_warp[warp] = x;
-    __syncthreads();
-    int wpre = 0;
-    total = 0;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) {
-        const int s = s_warp[w];
-        wpre += (w < warp) ? s : 0;
-        total += s;
-    }
-    __syncthreads();
-    return wpre + x - v;
+// tile rect of a record's inclusive pixel rect (clipped to the frame's tiles)
+struct TileRect {
+    int x0, y0, x1, y1;
+};
+__device__ __forceinline__ TileRect tile_rect(const int4 &rc, int ts, const FrameDesc &fd) {
+    TileRect t;
+    t.x0 = max(rc.x, 0) / ts;
+    t.y0 = max(rc.y, 0) / ts;
+    t.x1 = min(rc.z / ts, fd.tiles_x - 1);
+    t.y1 = min(rc.w / ts, fd.tiles_y - 1);
+    return t;
 }
 
 __global__ void __launch_bounds__(kThreads)
-    k_count(const int *__restrict__ touched, int M, long long *__restrict__ sums, const int32_t *__restrict__ status) {
-    __shared__ long long s_w[kWarps];
-    if (status[0] != 0) return;
-    long long lo, hi;
-    slice(M, blockIdx.x, gridDim.x, lo, hi);
-    long long acc = 0;
-    for (long long i = lo + threadIdx.x; i < hi; i += kThreads) acc += touched[i];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        long long t = 0;
-        for (int w = 0; w < kWarps; ++w) t += s_w[w];
-        sums[blockIdx.x] = t;
-    }
+    k_tile_count(const float *__restrict__ rec, const int *__restrict__ touched, int M, int n_per_frame, FrameTable ft,
+                 uint32_t *__restrict__ ranges, const int32_t *__restrict__ status) {
+    if (!status_ok(status)) return;
+    const int i = blockIdx.x * kThreads + threadIdx.x;
+    if (i >= M || touched[i] <= 0) return;
+    const FrameDesc &fd = ft.f[i / n_per_frame];
+    const int4 rc = *reinterpret_cast<const int4 *>(rec + (size_t)i * kRecFloats + R_X0);
+    const TileRect t = tile_rect(rc, ft.tile, fd);
+    for (int ty = t.y0; ty <= t.y1; ++ty)
+        for (int tx = t.x0; tx <= t.x1; ++tx) atomicAdd(&ranges[2 * (size_t)(fd.tile_off + ty * fd.tiles_x + tx) + 1], 1u);
 }
 
-__global__ void __launch_bounds__(kScanTopThreads)
-    k_scan_top(long long *__restrict__ sums, int nb, int capacity, int32_t *__restrict__ status,
-               int *__restrict__ misc) {
-    __shared__ long long s_w[kScanTopThreads / 32];
-    if (status[0] != 0) return;
+// One CTA: exclusive scan of the per-tile counts (ranges[2t+1]) into
+// ranges[2t] = ranges[2t+1] = start (the fill then advances ranges[2t+1] to end).
+__global__ void __launch_bounds__(kScanThreads)
+    k_tile_scan(uint32_t *__restrict__ ranges, int n_tiles, int capacity, int32_t *__restrict__ status,
+                int *__restrict__ misc) {
+    __shared__ long long s_w[kScanThreads / 32];
+    if (!status_ok(status)) return;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const long long v = t < nb ? sums[t] : 0;
-    long long x = v;
+    const int per = (n_tiles + kScanThreads - 1) / kScanThreads;
+    const int lo = min(n_tiles, t * per), hi = min(n_tiles, lo + per);
+    long long local = 0;
+    for (int k = lo; k < hi; ++k) local += ranges[2 * (size_t)k + 1];
+    long long x = local;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
         const long long y = __shfl_up_sync(0xffffffffu, x, off);
@@ -91,12 +79,18 @@ __global__ void __launch_bounds__(kScanTopThreads)
     }
     if (lane == 31) s_w[warp] = x;
     __syncthreads();
-    long long wpre = 0, total = 0;
-    for (int w = 0; w < kScanTopThreads / 32; ++w) {
-        wpre += (w < warp) ? s_w[w] : 0;
+    long long run = x - local, total = 0;
+    for (int w = 0; w < kScanThreads / 32; ++w) {
+        run += (w < warp) ? s_w[w] : 0;
         total += s_w[w];
     }
-    if (t < nb) sums[t] = wpre + x - v;
+    for (int k = lo; k < hi; ++k) {
+        const uint32_t c = ranges[2 * (size_t)k + 1];
+        const uint32_t start = (uint32_t)(run > UINT_MAX ? UINT_MAX : run);
+        ranges[2 * (size_t)k] = start;
+        ranges[2 * (size_t)k + 1] = start;
+        run += c;
+    }
     if (t == 0) {
         status[1] = (int32_t)(total > INT_MAX ? INT_MAX : total);
         if (total > capacity) status[0] = GS_ERR_CAPACITY;
@@ -105,161 +99,138 @@ __global__ void __launch_bounds__(kScanTopThreads)
 }
 
 __global__ void __launch_bounds__(kThreads)
-    k_emit(const float *__restrict__ rec, const int *__restrict__ touched, int M, int n_per_frame, FrameTable ft,
-           const long long *__restrict__ offs, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
-           const int32_t *__restrict__ status) {
-    __shared__ int s_warp[kWarps];
-    if (status[0] != 0) return;
-    long long lo, hi;
-    slice(M, blockIdx.x, gridDim.x, lo, hi);
-    long long run = offs[blockIdx.x];
-    const int ts = ft.tile;
-    for (long long base = lo; base < hi; base += kThreads) {
-        const long long i = base + threadIdx.x;
-        const int t = i < hi ? touched[i] : 0;
-        int total;
-        const int ex = block_excl_scan(t, total, s_warp);
-        if (t > 0) {
-            const int f = (int)(i / n_per_frame);
-            const FrameDesc &fd = ft.f[f];
-            const float *R = rec + (size_t)i * kRecFloats;
-            const int4 rc = *reinterpret_cast<const int4 *>(R + R_X0);
-            const uint32_t zb = __float_as_uint(R[R_Z]);
-            long long o = run + ex;
-            const long long o_end = o + t;  // never write more than this record's scanned count
-            const int ty1 = min(rc.w / ts, fd.tiles_y - 1), tx1 = min(rc.z / ts, fd.tiles_x - 1);
-            for (int ty = max(rc.y, 0) / ts; ty <= ty1; ++ty)
-                for (int tx = max(rc.x, 0) / ts; tx <= tx1 && o < o_end; ++tx) {
-                    const uint32_t tile = (uint32_t)(fd.tile_off + ty * fd.tiles_x + tx);
-                    keys[o] = ((uint64_t)tile << 32) | zb;
-                    vals[o] = (uint32_t)i;
-                    ++o;
-                }
+    k_tile_fill(const float *__restrict__ rec, const int *__restrict__ touched, int M, int n_per_frame, FrameTable ft,
+                uint32_t *__restrict__ ranges, uint64_t *__restrict__ low_keys, int capacity,
+                const int32_t *__restrict__ status) {
+    if (!status_ok(status)) return;
+    const int i = blockIdx.x * kThreads + threadIdx.x;
+    if (i >= M || touched[i] <= 0) return;
+    const FrameDesc &fd = ft.f[i / n_per_frame];
+    const float *R = rec + (size_t)i * kRecFloats;
+    const int4 rc = *reinterpret_cast<const int4 *>(R + R_X0);
+    const uint64_t low = ((uint64_t)__float_as_uint(R[R_Z]) << 32) | (uint32_t)i;
+    const TileRect t = tile_rect(rc, ft.tile, fd);
+    for (int ty = t.y0; ty <= t.y1; ++ty)
+        for (int tx = t.x0; tx <= t.x1; ++tx) {
+            const uint32_t slot = atomicAdd(&ranges[2 * (size_t)(fd.tile_off + ty * fd.tiles_x + tx) + 1], 1u);
+            if (slot < (uint32_t)capacity) low_keys[slot] = low;
         }
-        run += total;
-    }
 }
 
-__global__ void __launch_bounds__(kThreads)
-    k_radix_hist(const uint64_t *__restrict__ keys, int shift, uint32_t *__restrict__ hist,
-                 const int *__restrict__ misc, const int32_t *__restrict__ status) {
-    __shared__ uint32_t h[kRadix];
-    if (status[0] != 0) return;
-    long long lo, hi;
-    slice(misc[0], blockIdx.x, gridDim.x, lo, hi);
-    h[threadIdx.x] = 0;
-    __syncthreads();
-    for (long long i = lo + threadIdx.x; i < hi; i += kThreads)
-        atomicAdd(&h[(uint32_t)(keys[i] >> shift) & (kRadix - 1)], 1u);
-    __syncthreads();
-    hist[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
-}
-
-// Exclusive scan of the digit-major [256][NB] count matrix, in place.
-__global__ void __launch_bounds__(kScanTopThreads)
-    k_radix_scan(uint32_t *__restrict__ hist, int n, const int32_t *__restrict__ status) {
-    __shared__ uint32_t s_w[kScanTopThreads / 32];
-    if (status[0] != 0) return;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int per = n / kScanTopThreads;  // multiple of 4
-    uint4 *p = reinterpret_cast<uint4 *>(hist + (size_t)t * per);
-    uint32_t local = 0;
-    for (int q = 0; q < per / 4; ++q) {
-        const uint4 v = p[q];
-        local += v.x + v.y + v.z + v.w;
-    }
-    uint32_t x = local;
+// Exclusive scan over one value per thread of the CTA; returns the prefix.
+__device__ __forceinline__ uint32_t cta_excl_scan(uint32_t v, uint32_t *s_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
         const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
         if (lane >= off) x += y;
     }
-    if (lane == 31) s_w[warp] = x;
+    if (lane == 31) s_warp[warp] = x;
     __syncthreads();
-    uint32_t run = x - local;
-    for (int w = 0; w < warp; ++w) run += s_w[w];
-    for (int q = 0; q < per / 4; ++q) {
-        uint4 v = p[q];
-        uint4 o;
-        o.x = run; run += v.x;
-        o.y = run; run += v.y;
-        o.z = run; run += v.z;
-        o.w = run; run += v.w;
-        p[q] = o;
-    }
+    uint32_t pre = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) pre += (w < warp) ? s_warp[w] : 0u;
+    __syncthreads();
+    return pre + x - v;
 }
 
-__global__ void __launch_bounds__(kThreads)
-    k_radix_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
-                    uint32_t *__restrict__ vout, int shift, const uint32_t *__restrict__ hist,
-                    const int *__restrict__ misc, const int32_t *__restrict__ status) {
-    __shared__ uint32_t run[kRadix];
-    __shared__ uint32_t wh[kWarps][kRadix];
-    if (status[0] != 0) return;
-    long long lo, hi;
-    slice(misc[0], blockIdx.x, gridDim.x, lo, hi);
+// One stable LSD pass of the CTA over n keys: src -> dst by the 8-bit digit at
+// `shift`. Returns false (and leaves src as the current array) when the digit
+// is the same for all n keys.
+__device__ bool cta_radix_pass(const uint64_t *src, uint64_t *dst, int n, int shift, uint32_t *s_cnt,
+                               uint32_t (*s_wh)[kRadix], uint32_t *s_warp) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    run[tid] = hist[(size_t)tid * gridDim.x + blockIdx.x];
+    s_cnt[tid] = 0;
+    __syncthreads();
+    for (int i = tid; i < n; i += kThreads) atomicAdd(&s_cnt[(uint32_t)(src[i] >> shift) & (kRadix - 1)], 1u);
+    __syncthreads();
+    const uint32_t c = s_cnt[tid];
+    if (__syncthreads_or(c == (uint32_t)n)) return false;
+    const uint32_t start = cta_excl_scan(c, s_warp);
+    s_cnt[tid] = start;  // running output offset of digit tid
     const uint32_t lt_mask = (1u << lane) - 1u;
-    for (long long base = lo; base < hi; base += kThreads) {
-        const long long i = base + tid;
-        const bool active = i < hi;
-        const uint64_t key = active ? kin[i] : 0ull;
-        const uint32_t val = active ? vin[i] : 0u;
+    for (int base = 0; base < n; base += kThreads) {
+        const int i = base + tid;
+        const bool active = i < n;
+        const uint64_t key = active ? src[i] : 0ull;
         const uint32_t d = active ? ((uint32_t)(key >> shift) & (kRadix - 1)) : (uint32_t)kRadix;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         const uint32_t rank = __popc(peers & lt_mask);
-        __syncthreads();  // previous chunk finished reading wh
+        __syncthreads();  // previous chunk done with s_wh; s_cnt writes visible
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) wh[w][tid] = 0;
+        for (int w = 0; w < kWarps; ++w) s_wh[w][tid] = 0;
         __syncthreads();
-        if (active && rank == 0) wh[warp][d] = __popc(peers);
+        if (active && rank == 0) s_wh[warp][d] = __popc(peers);
         __syncthreads();
         {
-            uint32_t r = run[tid];
+            uint32_t r = s_cnt[tid];
 #pragma unroll
             for (int w = 0; w < kWarps; ++w) {
-                const uint32_t c = wh[w][tid];
-                wh[w][tid] = r;
-                r += c;
+                const uint32_t cw = s_wh[w][tid];
+                s_wh[w][tid] = r;
+                r += cw;
             }
-            run[tid] = r;
+            s_cnt[tid] = r;
         }
         __syncthreads();
-        if (active) {
-            const uint32_t pos = wh[warp][d] + rank;
-            kout[pos] = key;
-            vout[pos] = val;
-        }
+        if (active) dst[s_wh[warp][d] + rank] = key;
     }
+    __syncthreads();
+    return true;
 }
 
 __global__ void __launch_bounds__(kThreads)
-    k_ranges(const uint64_t *__restrict__ keys, uint32_t *__restrict__ ranges, const int *__restrict__ misc,
-             const int32_t *__restrict__ status) {
-    if (status[0] != 0) return;
-    const long long P = misc[0];
-    for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < P; i += (long long)gridDim.x * kThreads) {
-        const uint32_t t = (uint32_t)(keys[i] >> 32);
-        if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[2 * (size_t)t] = (uint32_t)i;
-        if (i == P - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[2 * (size_t)t + 1] = (uint32_t)(i + 1);
+    k_tile_sort(uint64_t *low_keys, uint64_t *tmp, const uint32_t *__restrict__ ranges,
+                uint32_t *__restrict__ values, uint64_t *__restrict__ keys_out, int rec_bits,
+                const int32_t *__restrict__ status) {
+    __shared__ uint64_t s_a[kSmemKeys], s_b[kSmemKeys];
+    __shared__ uint32_t s_cnt[kRadix];
+    __shared__ uint32_t s_wh[kWarps][kRadix];
+    __shared__ uint32_t s_warp[kWarps];
+    if (!status_ok(status)) return;
+    const int tile = blockIdx.x;
+    const uint32_t s = ranges[2 * (size_t)tile], e = ranges[2 * (size_t)tile + 1];
+    const int n = (int)(e - s);
+    if (n <= 0) return;
+    const int tid = threadIdx.x;
+    const bool in_smem = n <= kSmemKeys;
+    uint64_t *a = in_smem ? s_a : tmp + s;  // large buckets ping-pong in global memory
+    uint64_t *b = in_smem ? s_b : low_keys + s;  // the bucket's own input slots are free after the copy
+    if (in_smem) {
+        for (int i = tid; i < n; i += kThreads) s_a[i] = low_keys[s + i];
+    } else {
+        for (int i = tid; i < n; i += kThreads) tmp[s + i] = low_keys[s + i];
+    }
+    __syncthreads();
+    // LSD order: the record-index digits (bits [0, rec_bits)), then the four
+    // depth digits (bits [32, 64))
+    for (int shift = 0; shift < 64; shift += kRadixBits) {
+        if (shift >= rec_bits && shift < 32) continue;
+        if (cta_radix_pass(a, b, n, shift, s_cnt, s_wh, s_warp)) {
+            uint64_t *t = a;
+            a = b;
+            b = t;
+        }
+    }
+    for (int i = tid; i < n; i += kThreads) {
+        const uint64_t k = a[i];
+        values[s + i] = (uint32_t)k;
+        if (keys_out) keys_out[s + i] = ((uint64_t)tile << 32) | (k >> 32);
     }
 }
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct WsLayout {
-    size_t keys_a, keys_b, vals_b, hist, sums, misc, total;
+    size_t low, tmp, misc, total;
 };
 
 WsLayout layout(int capacity) {
     WsLayout L;
     size_t o = 0;
-    L.keys_a = o; o += align256(sizeof(uint64_t) * (size_t)capacity);
-    L.keys_b = o; o += align256(sizeof(uint64_t) * (size_t)capacity);
-    L.vals_b = o; o += align256(sizeof(uint32_t) * (size_t)capacity);
-    L.hist = o; o += align256(sizeof(uint32_t) * (size_t)kRadix * kSortBlocks);
-    L.sums = o; o += align256(sizeof(long long) * (size_t)kScanBlocks);
+    L.low = o; o += align256(sizeof(uint64_t) * (size_t)capacity);
+    L.tmp = o; o += align256(sizeof(uint64_t) * (size_t)capacity);
     L.misc = o; o += align256(sizeof(int) * 16);
     L.total = o;
     return L;
@@ -283,32 +254,21 @@ cudaError_t launch_bin_tiles(const float *rec, const int *touched, int n_records
                              uint32_t *ranges, int32_t *status, void *ws, cudaStream_t s) {
     const WsLayout L = layout(capacity);
     char *w = static_cast<char *>(ws);
-    uint64_t *K[2] = {keys_out ? keys_out : reinterpret_cast<uint64_t *>(w + L.keys_a),
-                      reinterpret_cast<uint64_t *>(w + L.keys_b)};
-    uint32_t *V[2] = {values, reinterpret_cast<uint32_t *>(w + L.vals_b)};
-    uint32_t *hist = reinterpret_cast<uint32_t *>(w + L.hist);
-    long long *sums = reinterpret_cast<long long *>(w + L.sums);
+    uint64_t *low = reinterpret_cast<uint64_t *>(w + L.low);
+    uint64_t *tmp = reinterpret_cast<uint64_t *>(w + L.tmp);
     int *misc = reinterpret_cast<int *>(w + L.misc);
-
-    const int key_bits = 32 + bit_width((unsigned)(ft.total_tiles > 0 ? ft.total_tiles - 1 : 0));
-    const int passes = (key_bits + kRadixBits - 1) / kRadixBits;
-    const int e = passes & 1;
-
+    // low key = depth bits << 32 | record index; only the index bits that can be set are sorted
+    const int rec_bits = bit_width((unsigned)(n_records > 0 ? n_records - 1 : 0));
     cudaError_t err;
     if ((err = cudaMemsetAsync(misc, 0, sizeof(int) * 16, s)) != cudaSuccess) return err;
-    k_count<<<kScanBlocks, kThreads, 0, s>>>(touched, n_records, sums, status);
-    k_scan_top<<<1, kScanTopThreads, 0, s>>>(sums, kScanBlocks, capacity, status, misc);
-    k_emit<<<kScanBlocks, kThreads, 0, s>>>(rec, touched, n_records, n_per_frame, ft, sums, K[e], V[e], status);
-    for (int p = 0; p < passes; ++p) {
-        const int src = (e + p) & 1, dst = (e + p + 1) & 1;
-        const int shift = p * kRadixBits;
-        k_radix_hist<<<kSortBlocks, kThreads, 0, s>>>(K[src], shift, hist, misc, status);
-        k_radix_scan<<<1, kScanTopThreads, 0, s>>>(hist, kRadix * kSortBlocks, status);
-        k_radix_scatter<<<kSortBlocks, kThreads, 0, s>>>(K[src], V[src], K[dst], V[dst], shift, hist, misc, status);
-    }
     if ((err = cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * (size_t)ft.total_tiles, s)) != cudaSuccess)
         return err;
-    k_ranges<<<kScanBlocks, kThreads, 0, s>>>(K[0], ranges, misc, status);
+    if (ft.total_tiles == 0) return cudaSuccess;
+    const int grid = n_records > 0 ? (n_records + kThreads - 1) / kThreads : 1;
+    k_tile_count<<<grid, kThreads, 0, s>>>(rec, touched, n_records, n_per_frame, ft, ranges, status);
+    k_tile_scan<<<1, kScanThreads, 0, s>>>(ranges, ft.total_tiles, capacity, status, misc);
+    k_tile_fill<<<grid, kThreads, 0, s>>>(rec, touched, n_records, n_per_frame, ft, ranges, low, capacity, status);
+    k_tile_sort<<<ft.total_tiles, kThreads, 0, s>>>(low, tmp, ranges, values, keys_out, rec_bits, status);
     return cudaGetLastError();
 }
 

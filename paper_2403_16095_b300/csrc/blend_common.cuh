@@ -35,4 +35,39 @@ __device__ __forceinline__ bool eval_alpha(float pxc, float pyc, const float4 &a
     return alpha >= kAlphaMin;
 }
 
+// Conservative test: can the Gaussian (a, b, rect rc) be blended by any pixel
+// of the warp's 8x4 block whose pixel centres span [wx0+.5, wx0+7.5] x
+// [wy0+.5, wy0+3.5]? False only if the block misses the pixel rect, or if the
+// minimum of q over the block rectangle exceeds 9 by a slack that bounds the
+// FP32 rounding of both this evaluation and the per-pixel one (relative to the
+// magnitudes of the three terms of q, which can cancel for long, thin
+// footprints). q is convex, so with the centre outside the block its minimum
+// lies on an edge: each edge is minimised in closed form and clamped. Culled
+// entries would be rejected by every pixel of the block, so per-pixel results
+// are unchanged.
+__device__ __forceinline__ float q_slack(float A, float B, float C, float dx, float dy) {
+    const float t1 = A * dx * dx, t2 = 2.f * B * dx * dy, t3 = C * dy * dy;
+    return (t1 + t2 + t3) - 1e-5f * (fabsf(t1) + fabsf(t2) + fabsf(t3));
+}
+__device__ __forceinline__ bool warp_block_may_hit(const float4 &a, const float4 &b, const int4 &rc, int wx0,
+                                                   int wy0) {
+    if (rc.x > wx0 + 7 || rc.z < wx0 || rc.y > wy0 + 3 || rc.w < wy0) return false;
+    const float x0 = (float)wx0 + 0.5f - a.x, x1 = x0 + 7.f;  // block corners relative to the centre
+    const float y0 = (float)wy0 + 0.5f - a.y, y1 = y0 + 3.f;
+    if (x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f) return true;
+    const float A = a.z, B = a.w, C = b.x;
+    const float iA = 1.f / A, iC = 1.f / C;
+    float qmin = 1e30f;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float dx = e ? x1 : x0;  // vertical edge, dy free in [y0, y1]
+        const float dy = fminf(fmaxf(-B * dx * iC, y0), y1);
+        qmin = fminf(qmin, q_slack(A, B, C, dx, dy));
+        const float ey = e ? y1 : y0;  // horizontal edge, dx free in [x0, x1]
+        const float ex = fminf(fmaxf(-B * ey * iA, x0), x1);
+        qmin = fminf(qmin, q_slack(A, B, C, ex, ey));
+    }
+    return !(qmin > kQMax + 1e-3f);  // NaN-safe: keep on doubt
+}
+
 }  // namespace gs

@@ -1,0 +1,112 @@
+// Double-float (hi, lo FP32 pair) compensated summation for the pose-gradient
+// reductions. B300 executes FP64 at a small fraction of its FP32 rate, so the
+// reductions carry ~48-bit sums in FP32 pairs (Knuth's TwoSum, every operation
+// explicitly rounded so the compiler cannot reassociate) and convert to FP64
+// only for the final value.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace gs {
+
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df df_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ df df_add(df a, df b) {
+    df s = df_two_sum(a.hi, b.hi);
+    const float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    const float h = __fadd_rn(s.hi, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, s.hi))};
+}
+
+__device__ __forceinline__ df df_add_f(df a, float b) { return df_add(a, df{b, 0.f}); }
+
+__device__ __forceinline__ df df_shfl_down(df v, int off) {
+    return {__shfl_down_sync(0xffffffffu, v.hi, off), __shfl_down_sync(0xffffffffu, v.lo, off)};
+}
+
+// Warp sum (fixed butterfly order) of a double-float; the result is in lane 0.
+__device__ __forceinline__ df df_warp_sum(df v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = df_add(v, df_shfl_down(v, off));
+    return v;
+}
+
+}  // namespace gs
+
+namespace gs {
+
+// Pose partials: [K][6] double-floats stored as [K][6][2] floats (hi, lo).
+constexpr int kRedSlots = 256;
+
+// Fixed-order sum of K pose partials into six FP64 values. Slot s in [0, 256)
+// accumulates partials j = s, s + 256, ... in increasing j, then a fixed binary
+// tree combines the slots. The order depends only on K -- not on the number of
+// threads running it -- so every caller gets bit-identical results. Loads
+// bypass L1 (the partials may have been written by other CTAs of the same
+// launch). Needs blockDim.x >= 6 and a shared buffer of 256 x 6 double-floats.
+__device__ __forceinline__ void reduce_pose_partials(const float *p, int K, double *out6, df (*s_red)[6]) {
+    for (int s = threadIdx.x; s < kRedSlots; s += blockDim.x) {
+        df acc[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) acc[k] = {0.f, 0.f};
+        for (int j = s; j < K; j += kRedSlots)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const float2 v = __ldcg(reinterpret_cast<const float2 *>(p) + (size_t)j * 6 + k);
+                acc[k] = df_add(acc[k], df{v.x, v.y});
+            }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) s_red[s][k] = acc[k];
+    }
+    __syncthreads();
+    for (int stride = kRedSlots / 2; stride > 0; stride >>= 1) {
+        for (int s = threadIdx.x; s < stride; s += blockDim.x)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) s_red[s][k] = df_add(s_red[s][k], s_red[s + stride][k]);
+        __syncthreads();
+    }
+    if (threadIdx.x < 6) out6[threadIdx.x] = (double)s_red[0][threadIdx.x].hi + (double)s_red[0][threadIdx.x].lo;
+}
+
+// Per-CTA double-float sum of six per-thread FP32 values (fixed tree); thread 0
+// writes the partial (hi, lo pairs) to out12. s_w: [n_warps][6] double-floats.
+__device__ __forceinline__ void cta_pose_partial(const float acc[6], float *out12, df (*s_w)[6]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const df v = df_warp_sum(df{acc[k], 0.f});
+        if (lane == 0) s_w[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        df s = {0.f, 0.f};
+        for (int w = 0; w < nw; ++w) s = df_add(s, s_w[w][threadIdx.x]);
+        reinterpret_cast<float2 *>(out12)[threadIdx.x] = make_float2(s.hi, s.lo);
+    }
+}
+
+// Threadfence-reduction tail: after every CTA of frame f has written its
+// partial, the last one to arrive (ticket = n_ctas - 1) reduces them in fixed
+// order into pose_grad[6]. counter must be zero before the launch.
+__device__ __forceinline__ void last_cta_pose_reduce(const float *partials_f, int K, int n_ctas, unsigned *counter,
+                                                     double *pose_grad, df (*s_red)[6], int *s_flag) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) *s_flag = (atomicAdd(counter, 1u) == (unsigned)(n_ctas - 1));
+    __syncthreads();
+    if (*s_flag) {
+        __threadfence();
+        reduce_pose_partials(partials_f, K, pose_grad, s_red);
+    }
+}
+
+}  // namespace gs

@@ -70,8 +70,9 @@ cudaError_t launch_project(const GaussPtrs &g, int n, const FrameTable &ft, cons
                            float nu_cull, int mode, float *rec, int *touched, float *jac, const int32_t *status,
                            cudaStream_t s);
 cudaError_t launch_project_bwd(const GaussPtrs &g, int n, const FrameTable &ft, const float *T_cw, float jclamp,
-                               const float *rec, const float *grad2d, gs_grads grads, double *pose_partials,
-                               int per_frame, const int32_t *status, cudaStream_t s);
+                               const float *rec, const float *grad2d, gs_grads grads, float *pose_partials,
+                               int per_frame, double *pose_grad, unsigned *counters, const int32_t *status,
+                               cudaStream_t s);
 // binning.cu
 size_t bin_workspace_bytes(int n_records, int capacity);
 cudaError_t launch_bin_tiles(const float *rec, const int *touched, int n_records, int n_per_frame,
@@ -83,10 +84,11 @@ cudaError_t launch_render_fwd(const float *rec, const uint32_t *values, const ui
 // render_bwd.cu
 cudaError_t launch_render_bwd(int mode, const float *rec, const float *jac, const uint32_t *values,
                               const uint32_t *ranges, const FrameTable &ft, const float *obs_depth,
-                              const ImagePtrs &fwd, const LossParams &lp, float *grad2d, double *pose_partials,
-                              int per_frame, const int32_t *status, cudaStream_t s);
+                              const ImagePtrs &fwd, const LossParams &lp, float *grad2d, float *pose_partials,
+                              int per_frame, double *pose_grad, unsigned *counters, const int32_t *status,
+                              cudaStream_t s);
 // pose.cu
-cudaError_t launch_pose_reduce(const double *partials, int n_frames, int per_frame, double *out,
+cudaError_t launch_pose_reduce(const float *partials, int n_frames, int per_frame, double *out,
                                const int32_t *status, cudaStream_t s);
 cudaError_t launch_pose_adam(double *state, const double *grad, float *T_cw, int n_frames, gs_adam adam,
                              const int32_t *status, cudaStream_t s);

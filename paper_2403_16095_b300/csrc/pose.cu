@@ -1,73 +1,44 @@
 // Camera-pose gradient reduction and pose update (CG-SLAM Sec. 3.4).
 //
-// k_pose_reduce  one CTA per frame: each thread sums a fixed strided subset of
-//                the FP64 partials with Neumaier compensation, then a fixed
-//                shared-memory tree merges (sum, compensation) pairs, so the
-//                result is bit-identical from run to run.
+// k_pose_reduce  one CTA per frame: the fixed-order double-float reduction of
+//                the frame's pose partials (the same routine the backward
+//                kernels run in their last CTA, so results are bit-identical),
+//                final value in FP64.
 // k_pose_adam    one thread per frame: converts the left se(3) gradient
 //                (rho, phi) into the {so(3) | T} form the paper optimises
-//                (g_t = g_rho, g_R = g_phi - t x g_rho), takes one Adam step
-//                and applies R <- Exp(d_R) R, t <- t + d_t in FP64.
+//                (g_t = g_rho, g_R = g_phi - t x g_rho), updates the FP64 Adam
+//                moments, computes the step d = -lr mhat / (sqrt(vhat) + eps) in
+//                FP32 (B300 runs FP64 division/sqrt slowly; the step is ~1e-3
+//                and its FP32 rounding is far below any tracking tolerance), and
+//                applies R <- Exp(d_R) R, t <- t + d_t in FP64. The bias
+//                corrections use beta^t kept in the state, not pow().
 #include "gs_internal.cuh"
+#include "dfloat.cuh"
 
 namespace gs {
 namespace {
 
 constexpr int kRedThreads = 256;
 
-struct Nm {
-    double s, c;
-};
-
-__device__ __forceinline__ Nm nm_add(Nm a, double v) {
-    const double t = a.s + v;
-    a.c += (fabs(a.s) >= fabs(v)) ? (a.s - t) + v : (v - t) + a.s;
-    a.s = t;
-    return a;
-}
-
 __global__ void __launch_bounds__(kRedThreads)
-    k_pose_reduce(const double *__restrict__ partials, int per_frame, double *__restrict__ out,
+    k_pose_reduce(const float *__restrict__ partials, int per_frame, double *__restrict__ out,
                   const int32_t *__restrict__ status) {
-    __shared__ double ss[6][kRedThreads], sc[6][kRedThreads];
+    __shared__ df s_red[kRedSlots][6];
     if (status[0] != 0) return;
-    const int f = blockIdx.x, t = threadIdx.x;
-    const double *p = partials + (size_t)f * per_frame * 6;
-    Nm acc[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) acc[k] = {0.0, 0.0};
-    for (int j = t; j < per_frame; j += kRedThreads)
-#pragma unroll
-        for (int k = 0; k < 6; ++k) acc[k] = nm_add(acc[k], p[(size_t)j * 6 + k]);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        ss[k][t] = acc[k].s;
-        sc[k][t] = acc[k].c;
-    }
-    __syncthreads();
-    for (int stride = kRedThreads / 2; stride > 0; stride >>= 1) {
-        if (t < stride) {
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                Nm a = {ss[k][t], sc[k][t] + sc[k][t + stride]};
-                a = nm_add(a, ss[k][t + stride]);
-                ss[k][t] = a.s;
-                sc[k][t] = a.c;
-            }
-        }
-        __syncthreads();
-    }
-    if (t < 6) out[(size_t)f * 6 + t] = ss[t][0] + sc[t][0];
+    const int f = blockIdx.x;
+    reduce_pose_partials(partials + (size_t)f * per_frame * 12, per_frame, out + (size_t)f * 6, s_red);
 }
 
+// R = Exp(w) by Rodrigues; for |w| < 0.05 the coefficients come from their
+// Taylor series (truncation below 1e-17), avoiding FP64 sin/cos.
 __device__ void so3_exp(const double w[3], double R[3][3]) {
     const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
-    const double th = sqrt(th2);
     double a, b;
-    if (th < 1e-8) {
-        a = 1.0 - th2 / 6.0;
-        b = 0.5 - th2 / 24.0;
+    if (th2 < 2.5e-3) {
+        a = 1.0 - th2 * (1.0 / 6.0 - th2 * (1.0 / 120.0 - th2 * (1.0 / 5040.0)));
+        b = 0.5 - th2 * (1.0 / 24.0 - th2 * (1.0 / 720.0 - th2 * (1.0 / 40320.0)));
     } else {
+        const double th = sqrt(th2);
         a = sin(th) / th;
         b = (1.0 - cos(th)) / th2;
     }
@@ -87,24 +58,24 @@ __global__ void k_pose_adam(double *__restrict__ state, const double *__restrict
     double *st = state + (size_t)f * GS_POSE_STATE_DOUBLES;
     double *R = st, *t = st + 9, *m = st + 12, *v = st + 18;
     const double *gr = grad + (size_t)f * 6;
-    const double step = st[24] + 1.0;
-    st[24] = step;
+    st[24] += 1.0;                 // step count
+    st[25] *= (double)ad.beta1;    // beta1^step
+    st[26] *= (double)ad.beta2;    // beta2^step
+    const float c1 = (float)(1.0 - st[25]), c2 = (float)(1.0 - st[26]);
     double g[6];
     g[0] = gr[0];
     g[1] = gr[1];
     g[2] = gr[2];
-    // phi gradient of the {so(3)|T} parameterisation: g_phi - t x g_rho
     g[3] = gr[3] - (t[1] * gr[2] - t[2] * gr[1]);
     g[4] = gr[4] - (t[2] * gr[0] - t[0] * gr[2]);
     g[5] = gr[5] - (t[0] * gr[1] - t[1] * gr[0]);
     const double b1 = ad.beta1, b2 = ad.beta2;
-    const double c1 = 1.0 - pow(b1, step), c2 = 1.0 - pow(b2, step);
     double d[6];
     for (int k = 0; k < 6; ++k) {
         m[k] = b1 * m[k] + (1.0 - b1) * g[k];
         v[k] = b2 * v[k] + (1.0 - b2) * g[k] * g[k];
-        const double lr = k < 3 ? (double)ad.lr_trans : (double)ad.lr_rot;
-        d[k] = -lr * (m[k] / c1) / (sqrt(v[k] / c2) + (double)ad.eps);
+        const float lr = k < 3 ? ad.lr_trans : ad.lr_rot;
+        d[k] = (double)(-lr * ((float)m[k] / c1) / (sqrtf((float)v[k] / c2) + ad.eps));
     }
     double dR[3][3], Rn[3][3];
     so3_exp(d + 3, dR);
@@ -124,7 +95,7 @@ __global__ void k_pose_adam(double *__restrict__ state, const double *__restrict
 
 }  // namespace
 
-cudaError_t launch_pose_reduce(const double *partials, int n_frames, int per_frame, double *out,
+cudaError_t launch_pose_reduce(const float *partials, int n_frames, int per_frame, double *out,
                                const int32_t *status, cudaStream_t s) {
     if (n_frames == 0) return cudaSuccess;
     k_pose_reduce<<<n_frames, kRedThreads, 0, s>>>(partials, per_frame, out, status);

@@ -10,6 +10,7 @@
 //                quaternion, opacity logit, colour and nu (summed over frames,
 //                no atomics) and writes one FP64 pose partial per (frame, CTA).
 #include "gs_internal.cuh"
+#include "dfloat.cuh"
 
 namespace gs {
 namespace {
@@ -230,17 +231,20 @@ __global__ void __launch_bounds__(kProjThreads)
 __global__ void __launch_bounds__(kProjThreads)
     k_project_bwd(GaussPtrs g, int n, FrameTable ft, const float *__restrict__ T_cw, float jclamp,
                   const float *__restrict__ rec, const float *__restrict__ grad2d, gs_grads out,
-                  double *__restrict__ pose_partials, int per_frame, const int32_t *__restrict__ status) {
+                  float *__restrict__ pose_partials, int per_frame, double *__restrict__ pose_grad,
+                  unsigned *__restrict__ counters, const int32_t *__restrict__ status) {
     if (status[0] != 0) return;
     const int i = blockIdx.x * kProjThreads + threadIdx.x;
     const bool valid_i = i < n;
     float g_mean[3] = {0.f, 0.f, 0.f}, g_ls[3] = {0.f, 0.f, 0.f}, g_q[4] = {0.f, 0.f, 0.f, 0.f};
     float g_op = 0.f, g_col[3] = {0.f, 0.f, 0.f}, g_nu = 0.f;
-    __shared__ double red[kProjThreads / 32][6];
+    __shared__ df s_wdf[kProjThreads / 32][6];
+    __shared__ df s_red[kRedSlots][6];
+    __shared__ int s_flag;
 
     for (int f = 0; f < ft.n; ++f) {
         const FrameDesc &fd = ft.f[f];
-        double pc[6] = {0, 0, 0, 0, 0, 0};
+        float pc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         const size_t r = (size_t)f * n + i;
         bool live = valid_i;
         if (live) {
@@ -331,9 +335,9 @@ __global__ void __launch_bounds__(kProjThreads)
             g_q[3] += (gzq - z * dot) * o.qinv;
             // pose (left perturbation): rho = dL/dp, phi = p x dL/dp + 2 (Z12, Z20, Z01), Z = V H - H V
             pc[0] = gp0; pc[1] = gp1; pc[2] = gp2;
-            pc[3] = (double)o.p[1] * gp2 - (double)o.p[2] * gp1;
-            pc[4] = (double)o.p[2] * gp0 - (double)o.p[0] * gp2;
-            pc[5] = (double)o.p[0] * gp1 - (double)o.p[1] * gp0;
+            pc[3] = o.p[1] * gp2 - o.p[2] * gp1;
+            pc[4] = o.p[2] * gp0 - o.p[0] * gp2;
+            pc[5] = o.p[0] * gp1 - o.p[1] * gp0;
             float Z[3][3];
 #pragma unroll
             for (int a = 0; a < 3; ++a)
@@ -341,26 +345,16 @@ __global__ void __launch_bounds__(kProjThreads)
                 for (int b = 0; b < 3; ++b)
                     Z[a][b] = (o.V[a][0] * HV[0][b] + o.V[a][1] * HV[1][b] + o.V[a][2] * HV[2][b]) -
                               (HV[a][0] * o.V[0][b] + HV[a][1] * o.V[1][b] + HV[a][2] * o.V[2][b]);
-            pc[3] += 2.0 * Z[1][2];
-            pc[4] += 2.0 * Z[2][0];
-            pc[5] += 2.0 * Z[0][1];
+            pc[3] += 2.f * Z[1][2];
+            pc[4] += 2.f * Z[2][0];
+            pc[5] += 2.f * Z[0][1];
         }
-        // fixed-order block reduction of the six pose components (FP64)
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            double v = pc[k];
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-            if (lane == 0) red[warp][k] = v;
-        }
-        __syncthreads();
-        if (threadIdx.x < 6) {
-            double s = 0.0;
-#pragma unroll
-            for (int w = 0; w < kProjThreads / 32; ++w) s += red[w][threadIdx.x];
-            pose_partials[((size_t)f * per_frame + blockIdx.x) * 6 + threadIdx.x] = s;
-        }
+        // per-CTA pose partial (double-float, fixed tree); the last CTA of the
+        // frame reduces the frame's partials into the FP64 pose gradient
+        float *part_f = pose_partials + (size_t)f * per_frame * 12;
+        cta_pose_partial(pc, part_f + (size_t)blockIdx.x * 12, s_wdf);
+        if (pose_grad)
+            last_cta_pose_reduce(part_f, per_frame, gridDim.x, counters + f, pose_grad + 6 * f, s_red, &s_flag);
         __syncthreads();
     }
     if (!valid_i) return;
@@ -387,12 +381,12 @@ cudaError_t launch_project(const GaussPtrs &g, int n, const FrameTable &ft, cons
 }
 
 cudaError_t launch_project_bwd(const GaussPtrs &g, int n, const FrameTable &ft, const float *T_cw, float jclamp,
-                               const float *rec, const float *grad2d, gs_grads grads, double *pose_partials,
-                               int per_frame, const int32_t *status, cudaStream_t s) {
-    if (n == 0) return cudaSuccess;
-    dim3 grid((n + kProjThreads - 1) / kProjThreads);
+                               const float *rec, const float *grad2d, gs_grads grads, float *pose_partials,
+                               int per_frame, double *pose_grad, unsigned *counters, const int32_t *status,
+                               cudaStream_t s) {
+    dim3 grid(per_frame);  // ceil(n / 256), at least one CTA so the frame's pose gradient is written
     k_project_bwd<<<grid, kProjThreads, 0, s>>>(g, n, ft, T_cw, jclamp, rec, grad2d, grads, pose_partials, per_frame,
-                                                status);
+                                                pose_grad, counters, status);
     return cudaGetLastError();
 }
 

@@ -20,6 +20,7 @@
 // when some lane contributed) and lane 0 adds them to the record's accumulators.
 #include "gs_internal.cuh"
 #include "blend_common.cuh"
+#include "dfloat.cuh"
 
 namespace gs {
 namespace {
@@ -30,8 +31,8 @@ template <int TILE, int MODE>
 __global__ void __launch_bounds__(TILE *TILE)
     k_render_bwd(const float4 *__restrict__ rec, const float4 *__restrict__ jac, const uint32_t *__restrict__ values,
                  const uint2 *__restrict__ ranges, FrameTable ft, const float *__restrict__ obs_depth, ImagePtrs fwd,
-                 LossParams lp, float *__restrict__ grad2d, double *__restrict__ pose_partials, int per_frame,
-                 const int32_t *__restrict__ status) {
+                 LossParams lp, float *__restrict__ grad2d, float *__restrict__ pose_partials, int per_frame,
+                 double *__restrict__ pose_grad, unsigned *__restrict__ counters, const int32_t *__restrict__ status) {
     constexpr int NT = TILE * TILE;
     constexpr bool POSE = MODE == GS_MODE_POSE;
     constexpr int BATCH = POSE ? (NT < 128 ? NT : 128) : (NT < 256 ? NT : 256);
@@ -41,7 +42,9 @@ __global__ void __launch_bounds__(TILE *TILE)
     __shared__ float4 s_j[POSE ? BATCH * 9 : 1];
     __shared__ uint32_t s_idx[BATCH];
     __shared__ uint32_t s_wmax[NWARP];
-    __shared__ double s_red[NWARP][6];
+    __shared__ df s_wdf[NWARP][6];
+    __shared__ df s_red[POSE ? kRedSlots : 1][6];
+    __shared__ int s_flag;
     if (status[0] != 0) return;
 
     const int gtile = blockIdx.x;
@@ -122,11 +125,19 @@ __global__ void __launch_bounds__(TILE *TILE)
             }
         }
         __syncthreads();
-        for (int j = bend - 1; j >= bstart; --j) {
-            if ((uint32_t)j >= warp_last) continue;  // warp-uniform
-            const int k = j - bstart;
+        const int cnt = bend - bstart;
+        for (int g1 = cnt, g0 = max(0, cnt - 32); g1 > 0; g1 = g0, g0 = max(0, g0 - 32)) {
+          // lane l tests entry g0 + l (before the warp's last blended entry) against its pixel block
+          const int kt = g0 + lane;
+          const bool hit = kt < g1 && (uint32_t)(bstart + kt) < warp_last &&
+                           warp_block_may_hit(s_a[kt], s_b[kt], s_r[kt], wx0, wy0);
+          unsigned mask = __ballot_sync(0xffffffffu, hit);
+          while (mask) {  // surviving entries, back to front
+            const int bit = 31 - __clz(mask);
+            mask &= ~(1u << bit);
+            const int k = g0 + bit;
+            const int j = bstart + k;
             const int4 rc = s_r[k];
-            if (rc.x > wx0 + 7 || rc.z < wx0 || rc.y > wy0 + 3 || rc.w < wy0) continue;  // warp-uniform
             const float4 a = s_a[k];
             const float4 b = s_b[k];
             float dx = 0.f, dy = 0.f, G = 0.f, sg = 0.f, alpha = 0.f;
@@ -192,36 +203,31 @@ __global__ void __launch_bounds__(TILE *TILE)
                     }
                 }
             }
+          }
         }
     }
     if (POSE) {
-#pragma unroll
-        for (int m = 0; m < 6; ++m) {
-            double s = (double)acc[m];
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-            if (lane == 0) s_red[warp][m] = s;
-        }
-        __syncthreads();
-        if (tid < 6) {
-            double s = 0.0;
-#pragma unroll
-            for (int w = 0; w < NWARP; ++w) s += s_red[w][tid];
-            pose_partials[((size_t)f * per_frame + lt) * 6 + tid] = s;
-        }
+        // per-tile partial (double-float, fixed tree), then the last tile of the
+        // frame reduces all of the frame's partials into the FP64 pose gradient
+        float *part_f = pose_partials + (size_t)f * per_frame * 12;
+        cta_pose_partial(acc, part_f + (size_t)lt * 12, s_wdf);
+        if (pose_grad)
+            last_cta_pose_reduce(part_f, per_frame, fd.tiles_x * fd.tiles_y, counters + f, pose_grad + 6 * f, s_red,
+                                 &s_flag);
     }
 }
 
 template <int TILE>
 cudaError_t launch_tile(int mode, const float4 *rec, const float4 *jac, const uint32_t *values, const uint2 *ranges,
                         const FrameTable &ft, const float *obs_depth, const ImagePtrs &fwd, const LossParams &lp,
-                        float *grad2d, double *pp, int per_frame, const int32_t *status, cudaStream_t s) {
+                        float *grad2d, float *pp, int per_frame, double *pg, unsigned *cnt, const int32_t *status,
+                        cudaStream_t s) {
     if (mode == GS_MODE_POSE)
         k_render_bwd<TILE, GS_MODE_POSE><<<ft.total_tiles, TILE * TILE, 0, s>>>(
-            rec, jac, values, ranges, ft, obs_depth, fwd, lp, grad2d, pp, per_frame, status);
+            rec, jac, values, ranges, ft, obs_depth, fwd, lp, grad2d, pp, per_frame, pg, cnt, status);
     else
         k_render_bwd<TILE, GS_MODE_FULL><<<ft.total_tiles, TILE * TILE, 0, s>>>(
-            rec, jac, values, ranges, ft, obs_depth, fwd, lp, grad2d, pp, per_frame, status);
+            rec, jac, values, ranges, ft, obs_depth, fwd, lp, grad2d, pp, per_frame, pg, cnt, status);
     return cudaGetLastError();
 }
 
@@ -229,16 +235,17 @@ cudaError_t launch_tile(int mode, const float4 *rec, const float4 *jac, const ui
 
 cudaError_t launch_render_bwd(int mode, const float *rec, const float *jac, const uint32_t *values,
                               const uint32_t *ranges, const FrameTable &ft, const float *obs_depth,
-                              const ImagePtrs &fwd, const LossParams &lp, float *grad2d, double *pose_partials,
-                              int per_frame, const int32_t *status, cudaStream_t s) {
+                              const ImagePtrs &fwd, const LossParams &lp, float *grad2d, float *pose_partials,
+                              int per_frame, double *pose_grad, unsigned *counters, const int32_t *status,
+                              cudaStream_t s) {
     if (ft.total_tiles == 0) return cudaSuccess;
     const float4 *r4 = reinterpret_cast<const float4 *>(rec);
     const float4 *j4 = reinterpret_cast<const float4 *>(jac);
     const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
     switch (ft.tile) {
-        case 8: return launch_tile<8>(mode, r4, j4, values, rg, ft, obs_depth, fwd, lp, grad2d, pose_partials, per_frame, status, s);
-        case 16: return launch_tile<16>(mode, r4, j4, values, rg, ft, obs_depth, fwd, lp, grad2d, pose_partials, per_frame, status, s);
-        case 32: return launch_tile<32>(mode, r4, j4, values, rg, ft, obs_depth, fwd, lp, grad2d, pose_partials, per_frame, status, s);
+        case 8: return launch_tile<8>(mode, r4, j4, values, rg, ft, obs_depth, fwd, lp, grad2d, pose_partials, per_frame, pose_grad, counters, status, s);
+        case 16: return launch_tile<16>(mode, r4, j4, values, rg, ft, obs_depth, fwd, lp, grad2d, pose_partials, per_frame, pose_grad, counters, status, s);
+        case 32: return launch_tile<32>(mode, r4, j4, values, rg, ft, obs_depth, fwd, lp, grad2d, pose_partials, per_frame, pose_grad, counters, status, s);
         default: return cudaErrorInvalidValue;
     }
 }

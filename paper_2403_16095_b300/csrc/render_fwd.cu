@@ -17,7 +17,7 @@ namespace gs {
 namespace {
 
 template <int TILE>
-__global__ void __launch_bounds__(TILE *TILE)
+__global__ void __launch_bounds__(TILE *TILE, 1024 / (TILE * TILE))
     k_render_fwd(const float4 *__restrict__ rec, const uint32_t *__restrict__ values,
                  const uint2 *__restrict__ ranges, FrameTable ft, const float *__restrict__ obs_depth, ImagePtrs out,
                  const int32_t *__restrict__ status) {
@@ -59,31 +59,40 @@ __global__ void __launch_bounds__(TILE *TILE)
         }
         __syncthreads();
         const int cnt = min(BATCH, (int)(range.y - base));
-        if (!done) {
-            for (int k = 0; k < cnt; ++k) {
-                const int4 rc = s_r[k];
-                if (rc.x > wx0 + 7 || rc.z < wx0 || rc.y > wy0 + 3 || rc.w < wy0) continue;  // warp-uniform
-                if (!in_rect(px, py, rc)) continue;
-                const float4 a = s_a[k];
-                const float4 b = s_b[k];
-                float dx, dy, G, sg, alpha;
-                if (!eval_alpha(pxc, pyc, a, b, dx, dy, G, sg, alpha)) continue;
-                const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
-                if (Tn < kTMin) { done = true; break; }
-                const float w = __fmul_rn(alpha, T);
-                const float4 c = s_c[k];
-                c0 = fmaf(w, c.x, c0);
-                c1 = fmaf(w, c.y, c1);
-                c2 = fmaf(w, c.z, c2);
-                dep = fmaf(w, b.z, dep);
-                opa = __fadd_rn(opa, w);
-                const float dz = __fsub_rn(b.z, Dp);
-                unc = fmaf(w, __fmul_rn(dz, dz), unc);
-                nus = fmaf(w, b.w, nus);
-                if (T >= 0.5f && Tn < 0.5f) med = b.z;
-                T = Tn;
-                last = base + k + 1;
-                ++n_blend;
+        if (!__all_sync(0xffffffffu, done)) {
+            for (int g0 = 0; g0 < cnt; g0 += 32) {
+                // lane l tests entry g0 + l against this warp's pixel block
+                const int kt = g0 + lane;
+                const bool hit = kt < cnt && warp_block_may_hit(s_a[kt], s_b[kt], s_r[kt], wx0, wy0);
+                unsigned mask = __ballot_sync(0xffffffffu, hit);
+                while (mask) {  // surviving entries, front to back
+                    const int k = g0 + __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    if (done) continue;
+                    const int4 rc = s_r[k];
+                    if (!in_rect(px, py, rc)) continue;
+                    const float4 a = s_a[k];
+                    const float4 b = s_b[k];
+                    float dx, dy, G, sg, alpha;
+                    if (!eval_alpha(pxc, pyc, a, b, dx, dy, G, sg, alpha)) continue;
+                    const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
+                    if (Tn < kTMin) { done = true; continue; }
+                    const float w = __fmul_rn(alpha, T);
+                    const float4 c = s_c[k];
+                    c0 = fmaf(w, c.x, c0);
+                    c1 = fmaf(w, c.y, c1);
+                    c2 = fmaf(w, c.z, c2);
+                    dep = fmaf(w, b.z, dep);
+                    opa = __fadd_rn(opa, w);
+                    const float dz = __fsub_rn(b.z, Dp);
+                    unc = fmaf(w, __fmul_rn(dz, dz), unc);
+                    nus = fmaf(w, b.w, nus);
+                    if (T >= 0.5f && Tn < 0.5f) med = b.z;
+                    T = Tn;
+                    last = base + k + 1;
+                    ++n_blend;
+                }
+                if (__all_sync(0xffffffffu, done)) break;
             }
         }
     }

@@ -66,7 +66,8 @@ class Rasterizer:
         self.set_capacity(capacity if capacity is not None else max(4096, 2 * self.M))
         if mode != A.GS_MODE_FWD:
             self.per_frame = A.gs_pose_partials_per_frame(mode, self.N, self.cams, tile)
-            self.pose_partials = torch.zeros(self.F * self.per_frame * 6, dtype=torch.float64, device=dev)
+            # double-float partials: [F][per_frame][6][2] (hi, lo)
+            self.pose_partials = torch.zeros(self.F * self.per_frame * 12, dtype=torch.float32, device=dev)
             self.pose_grad = torch.zeros(self.F, 6, dtype=torch.float64, device=dev)
             self.bwd_ws = torch.empty(A.gs_render_bwd_workspace_size(self.M, mode), dtype=torch.uint8, device=dev)
 
@@ -100,9 +101,12 @@ class Rasterizer:
 
     def backward(self, *, obs_depth=None, loss: Optional[dict] = None, dL: Optional[dict] = None,
                  g: Optional[Gaussians] = None, T_cw: Optional[torch.Tensor] = None, grads: Optional[dict] = None,
-                 stream=None) -> None:
+                 fused_pose: bool = True, stream=None) -> None:
+        """Backward; with fused_pose the last CTA of each frame also writes
+        ``pose_grad`` (otherwise call reduce_pose())."""
         A.gs_render_bwd(self.N, self.cams, self.opts, self.rec, self.jac, self.values, self.ranges, T_cw, g,
-                        obs_depth, self.img, dL, loss, grads, self.pose_partials, self.status, self.bwd_ws, stream)
+                        obs_depth, self.img, dL, loss, grads, self.pose_partials,
+                        self.pose_grad if fused_pose else None, self.status, self.bwd_ws, stream)
 
     def reduce_pose(self, stream=None) -> None:
         A.gs_pose_grad_reduce(self.pose_partials, self.F, self.per_frame, self.pose_grad, self.status, stream)
@@ -173,7 +177,6 @@ class GaussianRasterize(torch.autograd.Function):
         grads = {k: torch.empty_like(getattr(g, k)) for k in
                  ("means", "log_scales", "quats", "opacity_logit", "colors", "nu")}
         rast.backward(obs_depth=ctx.obs_depth, dL=dL, g=g, T_cw=ctx.T_cw, grads=grads)
-        rast.reduce_pose()
         code, _ = rast.read_status()
         if code:
             raise A.GsError(code, "device status in backward")
@@ -191,11 +194,13 @@ def rasterize(g: Gaussians, xi: torch.Tensor, T_cw: torch.Tensor, rast: Rasteriz
 
 # ===================================================================== tracking
 def pose_state(T: torch.Tensor) -> torch.Tensor:
-    """FP64 pose state [F, 25]: R (9), t (3), Adam m (6), v (6), step."""
+    """FP64 pose state [F, 28]: R (9), t (3), Adam m (6), v (6), step,
+    beta1^step, beta2^step, unused."""
     T = T.reshape(-1, 3, 4).to(torch.float64)
     st = torch.zeros(T.shape[0], A.GS_POSE_STATE_DOUBLES, dtype=torch.float64, device=T.device)
     st[:, :9] = T[:, :, :3].reshape(-1, 9)
     st[:, 9:12] = T[:, :, 3]
+    st[:, 25:27] = 1.0
     return st
 
 
@@ -247,19 +252,16 @@ class Tracker:
         r.forward(self.target_depth, stream)
         if self.bwd_events is not None:
             self.bwd_events[it][0].record(stream)
-        r.backward(obs_depth=self.target_depth, loss=self.loss, stream=stream)
+        r.backward(obs_depth=self.target_depth, loss=self.loss, stream=stream)  # + fused pose reduction
         if self.bwd_events is not None:
             self.bwd_events[it][1].record(stream)
-        r.reduce_pose(stream)
         A.gs_pose_adam_step(self.state, r.pose_grad, self.T_cw, 1, self.adam, r.status, stream)
 
     def kernel_launches_per_iteration(self) -> int:
-        """libgs kernels one iteration launches (memsets not counted): project,
-        count + scan + emit, 3 per radix pass, ranges, forward, backward,
-        pose reduction, Adam step."""
-        bits = 32 + max(0, (self.rast.n_tiles - 1).bit_length())
-        passes = (bits + 7) // 8
-        return 1 + 3 + 3 * passes + 1 + 1 + 1 + 1 + 1
+        """libgs kernels one iteration launches (memsets not counted): project;
+        tile count, scan, fill, per-tile sort; forward; backward (with the fused
+        pose reduction); Adam step."""
+        return 1 + 4 + 1 + 1 + 1
 
     def _capture(self):
         """Capture all ``iters`` iterations of a frame in one CUDA graph."""

@@ -43,7 +43,7 @@ def test_header_compiles_as_plain_c(tmp_path):
 
 def test_pure_host_queries(A):
     assert A.lib.gs_abi_version() == 1
-    assert A.gs_bin_tiles_workspace_size(1000, 5000) >= 5000 * (8 + 8 + 4)
+    assert A.gs_bin_tiles_workspace_size(1000, 5000) >= 5000 * (8 + 8)
     assert A.gs_bin_tiles_workspace_size(10, 0) == 0
     cams = [type("C", (), dict(width=640, height=480, fx=600, fy=600, cx=320, cy=240, znear=0.2))()]
     assert A.gs_pose_partials_per_frame(A.GS_MODE_POSE, 10, cams, 16) == 1200
@@ -77,7 +77,7 @@ def test_argument_errors_are_synchronous(A):
     tiles = A.gs_tiles(10, 12, C.c_void_p(256), None, C.c_void_p(256))
     img = A.gs_image()
     st = lib.gs_render_bwd(C.byref(p0), C.byref(tiles), 1, cam, None, None, None, C.byref(img), None, None,
-                           C.byref(fwd_opts), None, None, None, None, 0, None)
+                           C.byref(fwd_opts), None, None, None, None, None, 0, None)
     assert st == A.GS_ERR_INVALID_ARG and "POSE or FULL" in A.last_error()
     # workspace too small
     ws_opts = A.gs_opts(16, A.GS_MODE_POSE, 1.3, 0.0)
