@@ -5,20 +5,22 @@
 //
 //   k_tile_count  MSD digit = the tile id: one atomic increment per
 //                 (record, overlapped tile) into the tile's counter (the
-//                 `ranges` buffer doubles as the counters).
+//                 `ranges` buffer doubles as the counters); pairs are spread
+//                 over the lanes of a warp so large footprints do not serialise.
 //   k_tile_scan   exclusive scan of the counters -> each tile's [start, start)
 //                 cursor, total pair count P and the capacity check.
 //   k_tile_fill   each pair claims a slot in its tile's bucket and stores the
 //                 low key (depth bits << 32 | record); after this pass every
 //                 tile's cursor equals its end, so `ranges` is final.
-//   k_tile_sort   one CTA per tile: stable LSD radix sort (8-bit digits) of the
-//                 bucket's low keys over the depth bits and the record-index
-//                 bits, in shared memory (global memory for buckets larger than
-//                 kSmemKeys). Digits that are constant over a bucket are
-//                 skipped. Low keys are unique within a bucket, so the order of
-//                 the atomic fill does not matter: the output is bit-exact, the
-//                 same as a stable sort of the 64-bit keys emitted in record
-//                 order, and independent of the launch configuration.
+//   k_tile_sort   one CTA per tile sorts the bucket's low keys: buckets of
+//                 <= 2048 keys with a bitonic network in shared memory, larger
+//                 ones with a stable LSD radix sort (8-bit digits over the
+//                 record-index and depth bits; digits constant over the bucket
+//                 are skipped) ping-ponging in global memory. Low keys are
+//                 unique within a bucket, so the order of the atomic fill does
+//                 not matter: the output is bit-exact, the same as a stable sort
+//                 of the 64-bit keys emitted in record order, and independent of
+//                 the launch configuration.
 #include <climits>
 
 #include "gs_internal.cuh"
@@ -46,17 +48,78 @@ __device__ __forceinline__ TileRect tile_rect(const int4 &rc, int ts, const Fram
     return t;
 }
 
+// One record per lane; its (record, tile) pairs are spread over the warp's
+// lanes (warp prefix sum of the per-record tile counts, then lane l handles
+// pairs l, l + 32, ...), so one large footprint does not serialise its warp.
+struct PairSrc {
+    bool valid;
+    TileRect t;
+    int tile_off, tiles_x;
+    uint32_t payload;  // per-record value handed to the pair callback (depth bits)
+};
+
+__device__ __forceinline__ PairSrc pair_source(const float *__restrict__ rec, const int *__restrict__ touched, int i,
+                                               int M, int n_per_frame, const FrameTable &ft) {
+    PairSrc p{};
+    p.valid = i < M && touched[i] > 0;
+    if (p.valid) {
+        const FrameDesc &fd = ft.f[i / n_per_frame];
+        const int4 rc = *reinterpret_cast<const int4 *>(rec + (size_t)i * kRecFloats + R_X0);
+        p.t = tile_rect(rc, ft.tile, fd);
+        p.tile_off = fd.tile_off;
+        p.tiles_x = fd.tiles_x;
+    }
+    return p;
+}
+
+// Calls f(owner_lane, global_tile, owner_payload) for every pair of the warp's
+// records; all shuffles happen with the whole warp converged.
+template <class F>
+__device__ __forceinline__ void warp_for_each_pair(const PairSrc &s, F &&f) {
+    const int lane = threadIdx.x & 31;
+    const int w = s.valid ? s.t.x1 - s.t.x0 + 1 : 0;
+    const int cnt = s.valid ? w * (s.t.y1 - s.t.y0 + 1) : 0;
+    int incl = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int base = 0; base < total; base += 32) {
+        const int p = base + lane;
+        // owner = first lane whose inclusive prefix exceeds p (binary search)
+        int lo = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int probe = __shfl_sync(0xffffffffu, incl, lo + step - 1);
+            if (probe <= p) lo += step;
+        }
+        const int owner = lo;
+        const int o_incl = __shfl_sync(0xffffffffu, incl, owner);
+        const int o_cnt = __shfl_sync(0xffffffffu, cnt, owner);
+        const int o_w = __shfl_sync(0xffffffffu, w, owner);
+        const int o_x0 = __shfl_sync(0xffffffffu, s.t.x0, owner);
+        const int o_y0 = __shfl_sync(0xffffffffu, s.t.y0, owner);
+        const int o_off = __shfl_sync(0xffffffffu, s.tile_off, owner);
+        const int o_tx = __shfl_sync(0xffffffffu, s.tiles_x, owner);
+        const uint32_t o_pl = __shfl_sync(0xffffffffu, s.payload, owner);
+        if (p < total) {
+            const int j = p - (o_incl - o_cnt);
+            const int ty = o_y0 + j / o_w, tx = o_x0 + j % o_w;
+            f(owner, o_off + ty * o_tx + tx, o_pl);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kThreads)
     k_tile_count(const float *__restrict__ rec, const int *__restrict__ touched, int M, int n_per_frame, FrameTable ft,
                  uint32_t *__restrict__ ranges, const int32_t *__restrict__ status) {
     if (!status_ok(status)) return;
     const int i = blockIdx.x * kThreads + threadIdx.x;
-    if (i >= M || touched[i] <= 0) return;
-    const FrameDesc &fd = ft.f[i / n_per_frame];
-    const int4 rc = *reinterpret_cast<const int4 *>(rec + (size_t)i * kRecFloats + R_X0);
-    const TileRect t = tile_rect(rc, ft.tile, fd);
-    for (int ty = t.y0; ty <= t.y1; ++ty)
-        for (int tx = t.x0; tx <= t.x1; ++tx) atomicAdd(&ranges[2 * (size_t)(fd.tile_off + ty * fd.tiles_x + tx) + 1], 1u);
+    const PairSrc src = pair_source(rec, touched, i, M, n_per_frame, ft);
+    if (!__any_sync(0xffffffffu, src.valid)) return;
+    warp_for_each_pair(src, [&](int, int gt, uint32_t) { atomicAdd(&ranges[2 * (size_t)gt + 1], 1u); });
 }
 
 // One CTA: exclusive scan of the per-tile counts (ranges[2t+1]) into
@@ -104,17 +167,14 @@ __global__ void __launch_bounds__(kThreads)
                 const int32_t *__restrict__ status) {
     if (!status_ok(status)) return;
     const int i = blockIdx.x * kThreads + threadIdx.x;
-    if (i >= M || touched[i] <= 0) return;
-    const FrameDesc &fd = ft.f[i / n_per_frame];
-    const float *R = rec + (size_t)i * kRecFloats;
-    const int4 rc = *reinterpret_cast<const int4 *>(R + R_X0);
-    const uint64_t low = ((uint64_t)__float_as_uint(R[R_Z]) << 32) | (uint32_t)i;
-    const TileRect t = tile_rect(rc, ft.tile, fd);
-    for (int ty = t.y0; ty <= t.y1; ++ty)
-        for (int tx = t.x0; tx <= t.x1; ++tx) {
-            const uint32_t slot = atomicAdd(&ranges[2 * (size_t)(fd.tile_off + ty * fd.tiles_x + tx) + 1], 1u);
-            if (slot < (uint32_t)capacity) low_keys[slot] = low;
-        }
+    PairSrc src = pair_source(rec, touched, i, M, n_per_frame, ft);
+    if (!__any_sync(0xffffffffu, src.valid)) return;
+    src.payload = src.valid ? __float_as_uint(rec[(size_t)i * kRecFloats + R_Z]) : 0u;
+    warp_for_each_pair(src, [&](int owner, int gt, uint32_t o_zb) {
+        const uint32_t o_i = (uint32_t)(i - (threadIdx.x & 31) + owner);
+        const uint32_t slot = atomicAdd(&ranges[2 * (size_t)gt + 1], 1u);
+        if (slot < (uint32_t)capacity) low_keys[slot] = ((uint64_t)o_zb << 32) | o_i;
+    });
 }
 
 // Exclusive scan over one value per thread of the CTA; returns the prefix.
@@ -180,11 +240,17 @@ __device__ bool cta_radix_pass(const uint64_t *src, uint64_t *dst, int n, int sh
     return true;
 }
 
+// ---------------------------------------------------------------------------
+// k_tile_sort: one CTA per tile. Buckets of at most kSmemKeys keys are sorted
+// in shared memory by a bitonic network (padding = the all-ones key, which
+// sorts last; low keys are unique within a bucket, so the result is the same
+// as a stable radix sort). Larger buckets take a stable LSD radix sort that
+// ping-pongs in global memory.
 __global__ void __launch_bounds__(kThreads)
     k_tile_sort(uint64_t *low_keys, uint64_t *tmp, const uint32_t *__restrict__ ranges,
                 uint32_t *__restrict__ values, uint64_t *__restrict__ keys_out, int rec_bits,
                 const int32_t *__restrict__ status) {
-    __shared__ uint64_t s_a[kSmemKeys], s_b[kSmemKeys];
+    __shared__ uint64_t s_a[kSmemKeys];
     __shared__ uint32_t s_cnt[kRadix];
     __shared__ uint32_t s_wh[kWarps][kRadix];
     __shared__ uint32_t s_warp[kWarps];
@@ -194,14 +260,35 @@ __global__ void __launch_bounds__(kThreads)
     const int n = (int)(e - s);
     if (n <= 0) return;
     const int tid = threadIdx.x;
-    const bool in_smem = n <= kSmemKeys;
-    uint64_t *a = in_smem ? s_a : tmp + s;  // large buckets ping-pong in global memory
-    uint64_t *b = in_smem ? s_b : low_keys + s;  // the bucket's own input slots are free after the copy
-    if (in_smem) {
-        for (int i = tid; i < n; i += kThreads) s_a[i] = low_keys[s + i];
-    } else {
-        for (int i = tid; i < n; i += kThreads) tmp[s + i] = low_keys[s + i];
+    if (n <= kSmemKeys) {
+        int np = 2;
+        while (np < n) np <<= 1;
+        for (int i = tid; i < np; i += kThreads) s_a[i] = i < n ? low_keys[s + i] : ~0ull;
+        __syncthreads();
+        for (int size = 2; size <= np; size <<= 1)
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int t = tid; t < (np >> 1); t += kThreads) {
+                    const int i = ((t & ~(stride - 1)) << 1) | (t & (stride - 1));  // lower index of pair t
+                    const int j = i + stride;
+                    const uint64_t x = s_a[i], y = s_a[j];
+                    const bool up = (i & size) == 0;
+                    if ((x > y) == up) {
+                        s_a[i] = y;
+                        s_a[j] = x;
+                    }
+                }
+                __syncthreads();
+            }
+        for (int i = tid; i < n; i += kThreads) {
+            const uint64_t k = s_a[i];
+            values[s + i] = (uint32_t)k;
+            if (keys_out) keys_out[s + i] = ((uint64_t)tile << 32) | (k >> 32);
+        }
+        return;
     }
+    uint64_t *a = tmp + s;       // large buckets ping-pong in global memory;
+    uint64_t *b = low_keys + s;  // the bucket's own input slots are free after the copy
+    for (int i = tid; i < n; i += kThreads) tmp[s + i] = low_keys[s + i];
     __syncthreads();
     // LSD order: the record-index digits (bits [0, rec_bits)), then the four
     // depth digits (bits [32, 64))
