@@ -18,6 +18,8 @@
 // partial per tile (deterministic, no atomics).
 // FULL mode: the eleven per-entry gradients are reduced across the warp (only
 // when some lane contributed) and lane 0 adds them to the record's accumulators.
+#include <atomic>
+
 #include "gs_internal.cuh"
 #include "blend_common.cuh"
 #include "dfloat.cuh"
@@ -27,23 +29,43 @@ namespace {
 
 __device__ __forceinline__ float sgnf(float v) { return v > 0.f ? 1.f : (v < 0.f ? -1.f : 0.f); }
 
+// Entries staged per batch and the dynamic shared memory that holds them:
+// record (4 x 16 B) + index (4 B), plus the 144-B pose Jacobian in POSE mode.
+// The last CTA of a frame reuses the same bytes for the pose reduction.
 template <int TILE, int MODE>
+struct BwdSmem {
+    static constexpr int NT = TILE * TILE;
+    static constexpr bool POSE = MODE == GS_MODE_POSE;
+    static constexpr int BATCH = NT < 256 ? NT : 256;
+    static constexpr size_t kEntry = 4 * sizeof(float4) + sizeof(uint32_t) + (POSE ? 9 * sizeof(float4) : 0);
+    static constexpr size_t kStage = BATCH * kEntry;
+    static constexpr size_t kRed = POSE ? sizeof(df) * kRedSlots * 6 : 0;
+    static constexpr size_t bytes = kStage > kRed ? kStage : kRed;
+};
+
+// CD: the loss touches only colour and depth (the tracking loss), so the
+// opacity, U and nu terms of every contribution are compiled out.
+template <int TILE, int MODE, bool CD>
 __global__ void __launch_bounds__(TILE *TILE)
     k_render_bwd(const float4 *__restrict__ rec, const float4 *__restrict__ jac, const uint32_t *__restrict__ values,
                  const uint2 *__restrict__ ranges, FrameTable ft, const float *__restrict__ obs_depth, ImagePtrs fwd,
                  LossParams lp, float *__restrict__ grad2d, float *__restrict__ pose_partials, int per_frame,
                  double *__restrict__ pose_grad, unsigned *__restrict__ counters, const int32_t *__restrict__ status) {
-    constexpr int NT = TILE * TILE;
-    constexpr bool POSE = MODE == GS_MODE_POSE;
-    constexpr int BATCH = POSE ? (NT < 128 ? NT : 128) : (NT < 256 ? NT : 256);
+    using SM = BwdSmem<TILE, MODE>;
+    constexpr int NT = SM::NT;
+    constexpr bool POSE = SM::POSE;
+    constexpr int BATCH = SM::BATCH;
     constexpr int NWARP = NT / 32 > 0 ? NT / 32 : 1;
-    __shared__ float4 s_a[BATCH], s_b[BATCH], s_c[BATCH];
-    __shared__ int4 s_r[BATCH];
-    __shared__ float4 s_j[POSE ? BATCH * 9 : 1];
-    __shared__ uint32_t s_idx[BATCH];
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    float4 *s_a = reinterpret_cast<float4 *>(s_dyn);
+    float4 *s_b = s_a + BATCH;
+    float4 *s_c = s_b + BATCH;
+    int4 *s_r = reinterpret_cast<int4 *>(s_c + BATCH);
+    float4 *s_j = reinterpret_cast<float4 *>(s_r + BATCH);                   // POSE only
+    uint32_t *s_idx = reinterpret_cast<uint32_t *>(s_j + (POSE ? 9 * BATCH : 0));
+    df(*s_red)[6] = reinterpret_cast<df(*)[6]>(s_dyn);                       // tail only
     __shared__ uint32_t s_wmax[NWARP];
     __shared__ df s_wdf[NWARP][6];
-    __shared__ df s_red[POSE ? kRedSlots : 1][6];
     __shared__ int s_flag;
     if (status[0] != 0) return;
 
@@ -96,6 +118,11 @@ __global__ void __launch_bounds__(TILE *TILE)
             if (lp.g_nu) gN = lp.g_nu[pix];
         }
     }
+    if (CD) {  // the launcher picked this variant because these are zero
+        gO = 0.f;
+        gU = 0.f;
+        gN = 0.f;
+    }
     // ---- extent of the walk: block max and warp max of the last blended entry
     const uint32_t warp_last = __reduce_max_sync(0xffffffffu, my_last);
     if (lane == 0) s_wmax[warp] = warp_last;
@@ -146,7 +173,7 @@ __global__ void __launch_bounds__(TILE *TILE)
             float v[11];
             if (act) {
                 const float one_m = __fsub_rn(1.f, alpha);
-                const float inv = __frcp_rn(one_m);
+                const float inv = __fdividef(1.f, one_m);
                 T = T * inv;  // transmittance in front of entry j
                 const float w = alpha * T;
                 const float4 c = s_c[k];
@@ -217,18 +244,43 @@ __global__ void __launch_bounds__(TILE *TILE)
     }
 }
 
+// Raises the dynamic shared-memory limit of one kernel instance once per
+// device (a host-side attribute; the first call happens outside any capture).
+template <int TILE, int MODE, bool CD>
+cudaError_t launch_variant(const float4 *rec, const float4 *jac, const uint32_t *values, const uint2 *ranges,
+                           const FrameTable &ft, const float *obs_depth, const ImagePtrs &fwd, const LossParams &lp,
+                           float *grad2d, float *pp, int per_frame, double *pg, unsigned *cnt, const int32_t *status,
+                           cudaStream_t s) {
+    // raise the dynamic shared-memory limit once per device (a host-side
+    // attribute; the first call happens outside any stream capture)
+    static std::atomic<uint64_t> done{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    constexpr size_t smem = BwdSmem<TILE, MODE>::bytes;
+    if (dev >= 64 || !((done.load() >> dev) & 1)) {
+        e = cudaFuncSetAttribute(k_render_bwd<TILE, MODE, CD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (dev < 64) done.fetch_or(1ull << dev);
+    }
+    k_render_bwd<TILE, MODE, CD><<<ft.total_tiles, TILE * TILE, smem, s>>>(rec, jac, values, ranges, ft, obs_depth, fwd,
+                                                                           lp, grad2d, pp, per_frame, pg, cnt, status);
+    return cudaGetLastError();
+}
+
 template <int TILE>
 cudaError_t launch_tile(int mode, const float4 *rec, const float4 *jac, const uint32_t *values, const uint2 *ranges,
                         const FrameTable &ft, const float *obs_depth, const ImagePtrs &fwd, const LossParams &lp,
                         float *grad2d, float *pp, int per_frame, double *pg, unsigned *cnt, const int32_t *status,
                         cudaStream_t s) {
+    const bool cd = lp.fused ? (lp.w_unc == 0.f && lp.w_nu == 0.f) : (!lp.g_alpha && !lp.g_unc && !lp.g_nu);
+#define GS_BWD_ARGS rec, jac, values, ranges, ft, obs_depth, fwd, lp, grad2d, pp, per_frame, pg, cnt, status, s
     if (mode == GS_MODE_POSE)
-        k_render_bwd<TILE, GS_MODE_POSE><<<ft.total_tiles, TILE * TILE, 0, s>>>(
-            rec, jac, values, ranges, ft, obs_depth, fwd, lp, grad2d, pp, per_frame, pg, cnt, status);
-    else
-        k_render_bwd<TILE, GS_MODE_FULL><<<ft.total_tiles, TILE * TILE, 0, s>>>(
-            rec, jac, values, ranges, ft, obs_depth, fwd, lp, grad2d, pp, per_frame, pg, cnt, status);
-    return cudaGetLastError();
+        return cd ? launch_variant<TILE, GS_MODE_POSE, true>(GS_BWD_ARGS)
+                  : launch_variant<TILE, GS_MODE_POSE, false>(GS_BWD_ARGS);
+    return cd ? launch_variant<TILE, GS_MODE_FULL, true>(GS_BWD_ARGS)
+              : launch_variant<TILE, GS_MODE_FULL, false>(GS_BWD_ARGS);
+#undef GS_BWD_ARGS
 }
 
 }  // namespace
