@@ -140,22 +140,27 @@ typedef struct {
     float *T_final;  /* transmittance after the last blended Gaussian            */
     int32_t *n_last; /* one past the tile-list position of the last blended entry */
     int32_t *n_contrib; /* number of blended entries per pixel, or NULL            */
+    int32_t *median_pos; /* tile-list position of the median entry (-1: none), or
+                            NULL; needed by a backward with a median-depth gradient */
 } gs_image;
 
-/* Upstream gradients dL/d(channel) per pixel (same layouts); NULL = zero. */
+/* Upstream gradients dL/d(channel) per pixel (same layouts); NULL = zero. A
+ * median-depth gradient flows to the depth of the median entry (Eq. 7-8). */
 typedef struct {
-    const float *color, *depth, *alpha, *unc, *nu_map;
+    const float *color, *depth, *alpha, *unc, *nu_map, *median;
 } gs_image_grad;
 
-/* Fused per-pixel loss (Eq. 14, 16, 19; Eq. 11 optional), per frame f:
+/* Fused per-pixel loss (Eq. 14, 16, 19; Eq. 11 and 12 optional), per frame f:
  *   L_f = 1/(H W) sum_p [ m_p (w_color sum_c |C - C*| + w_depth |D - D*|)
- *                          + w_unc |U| + w_nu nu_map ],
+ *                          + w_unc |U| + w_nu nu_map + w_align |D - D_median| ],
  *   m_p = 1 / (1 + nu_map_p / unc_tau) if unc_tau > 0 else 1 (no gradient through m).
- * The total loss is sum_f L_f. sign(0) = 0. */
+ * The total loss is sum_f L_f. sign(0) = 0. w_align needs the forward's median
+ * and median_pos channels. */
 typedef struct {
     float w_color, w_depth, w_unc, w_nu, unc_tau;
     const float *target_color;  /* [.][3][H][W] device                        */
     const float *target_depth;  /* [.][H][W] device (also the sensor depth of U) */
+    float w_align;              /* L_align of Eq. 12                          */
 } gs_loss;
 
 /* Parameter gradients (FULL mode), device, same layouts as gs_gaussians,

@@ -42,7 +42,7 @@ class _Opts(C.Structure):
 class _Loss(C.Structure):
     _fields_ = [("w_color", C.c_double), ("w_depth", C.c_double), ("w_unc", C.c_double),
                 ("w_nu", C.c_double), ("unc_tau", C.c_double), ("target_color", _dp),
-                ("target_depth", _dp)]
+                ("target_depth", _dp), ("w_align", C.c_double)]
 
 
 class _Image(C.Structure):
@@ -128,7 +128,8 @@ def _cam(cam):
 
 @dataclasses.dataclass
 class LossSpec:
-    """L = sum_p 1/(HW) [ m_p (w_color sum_ch |C-C*| + w_depth |D-D*|) + w_unc |U| + w_nu nu_map ],
+    """L = sum_p 1/(HW) [ m_p (w_color sum_ch |C-C*| + w_depth |D-D*|) + w_unc |U| + w_nu nu_map
+                          + w_align |D_alpha - D_median| ],
     m_p = 1/(1 + nu_map/unc_tau) if unc_tau > 0 else 1 (held constant in the gradient)."""
     w_color: float = 1.0
     w_depth: float = 1.0
@@ -137,13 +138,14 @@ class LossSpec:
     unc_tau: float = 0.0
     target_color: np.ndarray | None = None   # [3,H,W]
     target_depth: np.ndarray | None = None   # [H,W] (also the sensor depth of U)
+    w_align: float = 0.0                     # L_align of Eq. 12
 
 
 class _KeepLoss:
     def __init__(self, L: LossSpec):
         self.tc = None if L.target_color is None else _f64(L.target_color)
         self.td = None if L.target_depth is None else _f64(L.target_depth)
-        self.s = _Loss(L.w_color, L.w_depth, L.w_unc, L.w_nu, L.unc_tau, _p(self.tc), _p(self.td))
+        self.s = _Loss(L.w_color, L.w_depth, L.w_unc, L.w_nu, L.unc_tau, _p(self.tc), _p(self.td), L.w_align)
 
 
 # ----------------------------------------------------------------- API

@@ -63,6 +63,7 @@ typedef struct {
     double w_color, w_depth, w_unc, w_nu, unc_tau;
     const double *target_color; /* [3][H][W]                            */
     const double *target_depth; /* [H][W]; also the sensor depth D of U */
+    double w_align;             /* weight of L_align (Eq. 12)           */
 } orc_loss;
 
 typedef struct { /* optional outputs; NULL members are skipped */
@@ -247,6 +248,7 @@ typedef struct { int k; double alpha, T, G, dx, dy; int clamped; } contrib;
 typedef struct {
     double color[3], depth, alpha, unc, nu, median, T;
     int n;
+    int med;  /* index (among the blended entries) of the median Gaussian, -1 if none */
     double margin[6];
     uint64_t hash;
 } pixout;
@@ -260,6 +262,7 @@ static uint64_t fnv(uint64_t h, uint64_t v) {
 static void blend_pixel(const orc_scene *sc, const gproj *G, const zent *list, int nl, int px, int py,
                         double Dp, int has_D, pixout *o, contrib *cb) {
     memset(o, 0, sizeof(*o));
+    o->med = -1;
     for (int k = 0; k < 6; ++k) o->margin[k] = INFINITY;
     o->hash = 1469598103934665603ULL;
     double T = 1.0;
@@ -298,7 +301,7 @@ static void blend_pixel(const orc_scene *sc, const gproj *G, const zent *list, i
         o->alpha += w;
         if (has_D) o->unc += w * (g->p[2] - Dp) * (g->p[2] - Dp);
         o->nu += w * sc->nu[k];
-        if (T >= 0.5 && Tn < 0.5) o->median = g->p[2];
+        if (T >= 0.5 && Tn < 0.5) { o->median = g->p[2]; o->med = o->n; }
         if (cb) {
             contrib *c = &cb[o->n];
             c->k = k; c->alpha = a; c->T = T; c->G = Gv; c->dx = dx; c->dy = dy; c->clamped = clamped;
@@ -345,12 +348,18 @@ static void store_pixel(orc_image *im, int HW, int p, const pixout *o) {
 static double sgn(double v) { return v > 0 ? 1.0 : (v < 0 ? -1.0 : 0.0); }
 
 /* per-pixel loss value and its gradient w.r.t. the 7 blended channels
- * (r, g, b, depth, opacity, U, nu_map). */
-static double pixel_loss(const orc_loss *L, const pixout *o, int p, int HW, double g[7]) {
+ * (r, g, b, depth, opacity, U, nu_map) and, in g[7], the median depth. */
+static double pixel_loss(const orc_loss *L, const pixout *o, int p, int HW, double g[8]) {
     double inv = 1.0 / HW;
     double m = L->unc_tau > 0 ? 1.0 / (1.0 + o->nu / L->unc_tau) : 1.0;
     double val = 0;
-    for (int c = 0; c < 7; ++c) g[c] = 0;
+    for (int c = 0; c < 8; ++c) g[c] = 0;
+    if (L->w_align != 0) { /* Eq. 12: |D_alpha - D_median| */
+        double d = o->depth - o->median;
+        val += inv * L->w_align * fabs(d);
+        g[3] += inv * L->w_align * sgn(d);
+        g[7] = -inv * L->w_align * sgn(d);
+    }
     if (L->w_color != 0 && L->target_color)
         for (int c = 0; c < 3; ++c) {
             double d = o->color[c] - L->target_color[c * HW + p];
@@ -360,7 +369,7 @@ static double pixel_loss(const orc_loss *L, const pixout *o, int p, int HW, doub
     if (L->w_depth != 0 && L->target_depth) {
         double d = o->depth - L->target_depth[p];
         val += inv * m * L->w_depth * fabs(d);
-        g[3] = inv * m * L->w_depth * sgn(d);
+        g[3] += inv * m * L->w_depth * sgn(d);
     }
     if (L->w_unc != 0) { val += inv * L->w_unc * fabs(o->unc); g[5] = inv * L->w_unc * sgn(o->unc); }
     if (L->w_nu != 0) { val += inv * L->w_nu * o->nu; g[6] = inv * L->w_nu; }
@@ -462,7 +471,7 @@ int orc_loss_value(const orc_scene *sc, const orc_cam *cam, const double *Tcw, c
                 int p = py * W + px;
                 int m = collect(G, sc->n, &rl, px, py, buf);
                 pixout o;
-                double g[7];
+                double g[8];
                 blend_pixel(sc, G, buf, m, px, py, L->target_depth ? L->target_depth[p] : 0,
                             L->target_depth != NULL, &o, NULL);
                 acc += pixel_loss(L, &o, p, HW, g);
@@ -645,7 +654,7 @@ int orc_grad(const orc_scene *sc, const orc_cam *cam, const double *Tcw, const o
                 int m = collect(G, n, &rl, px, py, buf);
                 double Dp = L->target_depth ? L->target_depth[p] : 0;
                 pixout o;
-                double gch[7];
+                double gch[8];
                 blend_pixel(sc, G, buf, m, px, py, Dp, L->target_depth != NULL, &o, cb);
                 row_loss[py] += pixel_loss(L, &o, p, HW, gch);
                 double S[7] = {0, 0, 0, 0, 0, 0, 0};
@@ -663,6 +672,7 @@ int orc_grad(const orc_scene *sc, const orc_cam *cam, const double *Tcw, const o
                     for (int ch = 0; ch < 3; ++ch) a[A_R + ch] += w * gch[ch];
                     a[A_NU] += w * gch[6];
                     a[A_Z] += w * (gch[3] + 2.0 * gch[5] * (g->p[2] - Dp));
+                    if (e == o.med) a[A_Z] += gch[7];  /* D_median = z of this entry (Eq. 7) */
                     if (!c->clamped) {
                         double dpow = dal * g->opac * c->G;
                         a[A_OP] += dal * c->G;

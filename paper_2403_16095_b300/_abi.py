@@ -64,16 +64,16 @@ class gs_tiles(C.Structure):
 
 class gs_image(C.Structure):
     _fields_ = [("color", _vp), ("depth", _vp), ("alpha", _vp), ("unc", _vp), ("nu_map", _vp),
-                ("median", _vp), ("T_final", _vp), ("n_last", _vp), ("n_contrib", _vp)]
+                ("median", _vp), ("T_final", _vp), ("n_last", _vp), ("n_contrib", _vp), ("median_pos", _vp)]
 
 
 class gs_image_grad(C.Structure):
-    _fields_ = [("color", _vp), ("depth", _vp), ("alpha", _vp), ("unc", _vp), ("nu_map", _vp)]
+    _fields_ = [("color", _vp), ("depth", _vp), ("alpha", _vp), ("unc", _vp), ("nu_map", _vp), ("median", _vp)]
 
 
 class gs_loss(C.Structure):
     _fields_ = [("w_color", C.c_float), ("w_depth", C.c_float), ("w_unc", C.c_float), ("w_nu", C.c_float),
-                ("unc_tau", C.c_float), ("target_color", _vp), ("target_depth", _vp)]
+                ("unc_tau", C.c_float), ("target_color", _vp), ("target_depth", _vp), ("w_align", C.c_float)]
 
 
 class gs_grads(C.Structure):
@@ -237,9 +237,10 @@ def gs_bin_tiles_noalloc(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tenso
 
 
 def _image(img: dict) -> gs_image:
-    return gs_image(*(_ptr(img.get(k), torch.int32 if k in ("n_last", "n_contrib") else torch.float32, k)
+    ints = ("n_last", "n_contrib", "median_pos")
+    return gs_image(*(_ptr(img.get(k), torch.int32 if k in ints else torch.float32, k)
                       for k in ("color", "depth", "alpha", "unc", "nu_map", "median", "T_final", "n_last",
-                                "n_contrib")))
+                                "n_contrib", "median_pos")))
 
 
 def gs_render_fwd(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tensor, values: torch.Tensor,
@@ -277,11 +278,12 @@ def gs_render_bwd(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tensor, pose
         gl = gs_loss(float(loss.get("w_color", 0.0)), float(loss.get("w_depth", 0.0)), float(loss.get("w_unc", 0.0)),
                      float(loss.get("w_nu", 0.0)), float(loss.get("unc_tau", 0.0)),
                      _ptr(loss.get("target_color"), torch.float32, "target_color"),
-                     _ptr(loss.get("target_depth"), torch.float32, "target_depth"))
+                     _ptr(loss.get("target_depth"), torch.float32, "target_depth"),
+                     float(loss.get("w_align", 0.0)))
     gd = None
     if dL is not None:
         gd = gs_image_grad(*(_ptr(dL.get(k), torch.float32, "dL." + k)
-                             for k in ("color", "depth", "alpha", "unc", "nu_map")))
+                             for k in ("color", "depth", "alpha", "unc", "nu_map", "median")))
     gg = None
     if grads is not None:
         gg = gs_grads(*(_ptr(grads.get(k), torch.float32, "grads." + k)

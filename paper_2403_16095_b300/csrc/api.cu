@@ -173,7 +173,7 @@ gs_status gs_render_fwd(const gs_projected *proj, const gs_tiles *tiles, int n_f
     if (!out || !out->color || !out->T_final || !out->n_last) return fail(GS_ERR_INVALID_ARG, "image color/T_final/n_last required");
     if (!status) return fail(GS_ERR_INVALID_ARG, "status NULL");
     gs::ImagePtrs ip{out->color, out->depth, out->alpha, out->unc, out->nu_map, out->median, out->T_final, out->n_last,
-                     out->n_contrib};
+                     out->n_contrib, out->median_pos};
     return cuda_status(gs::launch_render_fwd(proj->rec, tiles->values, tiles->ranges, ft, obs_depth, ip, status, stream),
                        "gs_render_fwd");
 }
@@ -209,20 +209,24 @@ gs_status gs_render_bwd(const gs_projected *proj, const gs_tiles *tiles, int n_f
     if (loss) {
         lp.fused = 1;
         lp.w_color = loss->w_color; lp.w_depth = loss->w_depth; lp.w_unc = loss->w_unc;
-        lp.w_nu = loss->w_nu; lp.unc_tau = loss->unc_tau;
+        lp.w_nu = loss->w_nu; lp.unc_tau = loss->unc_tau; lp.w_align = loss->w_align;
         lp.target_color = loss->target_color; lp.target_depth = loss->target_depth;
         if (lp.w_color != 0.f && (!fwd->color || !lp.target_color)) return fail(GS_ERR_INVALID_ARG, "colour loss needs fwd.color and target_color");
         if (lp.w_depth != 0.f && (!fwd->depth || !lp.target_depth)) return fail(GS_ERR_INVALID_ARG, "depth loss needs fwd.depth and target_depth");
         if (lp.w_unc != 0.f && (!fwd->unc || !obs_depth)) return fail(GS_ERR_INVALID_ARG, "|U| loss needs fwd.unc and obs_depth");
         if (lp.unc_tau > 0.f && !fwd->nu_map) return fail(GS_ERR_INVALID_ARG, "unc_tau weighting needs fwd.nu_map");
+        if (lp.w_align != 0.f && (!fwd->depth || !fwd->median || !fwd->median_pos))
+            return fail(GS_ERR_INVALID_ARG, "L_align needs fwd.depth, fwd.median and fwd.median_pos");
     } else if (dL) {
         lp.g_color = dL->color; lp.g_depth = dL->depth; lp.g_alpha = dL->alpha; lp.g_unc = dL->unc; lp.g_nu = dL->nu_map;
+        lp.g_median = dL->median;
         if (lp.g_unc && !obs_depth) return fail(GS_ERR_INVALID_ARG, "a gradient on U needs obs_depth");
+        if (lp.g_median && !fwd->median_pos) return fail(GS_ERR_INVALID_ARG, "a median-depth gradient needs fwd.median_pos");
     } else {
         return fail(GS_ERR_INVALID_ARG, "either dL or loss is required");
     }
     gs::ImagePtrs ip{fwd->color, fwd->depth, fwd->alpha, fwd->unc, fwd->nu_map, fwd->median, fwd->T_final, fwd->n_last,
-                     fwd->n_contrib};
+                     fwd->n_contrib, fwd->median_pos};
     const int N = proj->n_gaussians;
     const int M = N * n_frames;
     const int per_frame = gs_pose_partials_per_frame(mode, N, n_frames, cams, opts->tile);

@@ -44,14 +44,14 @@ struct GaussPtrs {
 
 struct ImagePtrs {
     float *color, *depth, *alpha, *unc, *nu_map, *median, *T_final;
-    int32_t *n_last, *n_contrib;
+    int32_t *n_last, *n_contrib, *median_pos;
 };
 
 struct LossParams {
     int fused;  // 1: compute dL from the loss spec, 0: read upstream maps
-    float w_color, w_depth, w_unc, w_nu, unc_tau;
+    float w_color, w_depth, w_unc, w_nu, unc_tau, w_align;
     const float *target_color, *target_depth;
-    const float *g_color, *g_depth, *g_alpha, *g_unc, *g_nu;
+    const float *g_color, *g_depth, *g_alpha, *g_unc, *g_nu, *g_median;
 };
 
 // frame of a global tile id (frames are few: linear scan of a uniform table)

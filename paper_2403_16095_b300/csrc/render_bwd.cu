@@ -86,9 +86,10 @@ __global__ void __launch_bounds__(TILE *TILE)
     const uint2 range = ranges[gtile];
 
     // ---- per-pixel loss gradient w.r.t. the blended channels
-    float gc0 = 0.f, gc1 = 0.f, gc2 = 0.f, gD = 0.f, gO = 0.f, gU = 0.f, gN = 0.f;
+    float gc0 = 0.f, gc1 = 0.f, gc2 = 0.f, gD = 0.f, gO = 0.f, gU = 0.f, gN = 0.f, gM = 0.f;
     float T = 1.f, Dp = 0.f;
     uint32_t my_last = range.x;
+    int my_med = -1;  // tile-list position of the median entry (receives gM on its depth)
     if (inside) {
         T = fwd.T_final[pix];
         my_last = min(max((uint32_t)fwd.n_last[pix], range.x), range.y);  // stay inside this tile's list
@@ -106,6 +107,11 @@ __global__ void __launch_bounds__(TILE *TILE)
             if (lp.w_depth != 0.f) gD = kd * sgnf(fwd.depth[pix] - lp.target_depth[pix]);
             if (lp.w_unc != 0.f) gU = inv_hw * lp.w_unc * sgnf(fwd.unc[pix]);
             gN = inv_hw * lp.w_nu;
+            if (lp.w_align != 0.f) {  // Eq. 12: |D_alpha - D_median|
+                const float ga = inv_hw * lp.w_align * sgnf(fwd.depth[pix] - fwd.median[pix]);
+                gD += ga;
+                gM = -ga;
+            }
         } else {
             if (lp.g_color) {
                 gc0 = lp.g_color[cbase];
@@ -116,12 +122,16 @@ __global__ void __launch_bounds__(TILE *TILE)
             if (lp.g_alpha) gO = lp.g_alpha[pix];
             if (lp.g_unc) gU = lp.g_unc[pix];
             if (lp.g_nu) gN = lp.g_nu[pix];
+            if (lp.g_median) gM = lp.g_median[pix];
         }
+        if (gM != 0.f) my_med = fwd.median_pos[pix];
     }
     if (CD) {  // the launcher picked this variant because these are zero
         gO = 0.f;
         gU = 0.f;
         gN = 0.f;
+        gM = 0.f;
+        my_med = -1;
     }
     // ---- extent of the walk: block max and warp max of the last blended entry
     const uint32_t warp_last = __reduce_max_sync(0xffffffffu, my_last);
@@ -189,6 +199,7 @@ __global__ void __launch_bounds__(TILE *TILE)
                 v[G_CB] = -dpow * dx * dy;
                 v[G_CC] = -0.5f * dpow * dy * dy;
                 v[G_Z] = w * (gD + 2.f * gU * dz);
+                if (!CD && j == my_med) v[G_Z] += gM;  // D_median = z of the median entry (Eq. 7)
                 if (!POSE) {
                     v[G_OP] = clamped ? 0.f : dal * G;
                     v[G_NU] = w * gN;
@@ -273,7 +284,8 @@ cudaError_t launch_tile(int mode, const float4 *rec, const float4 *jac, const ui
                         const FrameTable &ft, const float *obs_depth, const ImagePtrs &fwd, const LossParams &lp,
                         float *grad2d, float *pp, int per_frame, double *pg, unsigned *cnt, const int32_t *status,
                         cudaStream_t s) {
-    const bool cd = lp.fused ? (lp.w_unc == 0.f && lp.w_nu == 0.f) : (!lp.g_alpha && !lp.g_unc && !lp.g_nu);
+    const bool cd = lp.fused ? (lp.w_unc == 0.f && lp.w_nu == 0.f && lp.w_align == 0.f)
+                             : (!lp.g_alpha && !lp.g_unc && !lp.g_nu && !lp.g_median);
 #define GS_BWD_ARGS rec, jac, values, ranges, ft, obs_depth, fwd, lp, grad2d, pp, per_frame, pg, cnt, status, s
     if (mode == GS_MODE_POSE)
         return cd ? launch_variant<TILE, GS_MODE_POSE, true>(GS_BWD_ARGS)

@@ -45,6 +45,7 @@ __global__ void __launch_bounds__(TILE *TILE, 1024 / (TILE * TILE))
     float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, dep = 0.f, opa = 0.f, unc = 0.f, nus = 0.f, med = 0.f;
     uint32_t last = range.x;
     int n_blend = 0;
+    int med_pos = -1;  // tile-list position of the median entry
     bool done = !inside;
 
     for (uint32_t base = range.x; base < range.y; base += BATCH) {
@@ -87,7 +88,10 @@ __global__ void __launch_bounds__(TILE *TILE, 1024 / (TILE * TILE))
                     const float dz = __fsub_rn(b.z, Dp);
                     unc = fmaf(w, __fmul_rn(dz, dz), unc);
                     nus = fmaf(w, b.w, nus);
-                    if (T >= 0.5f && Tn < 0.5f) med = b.z;
+                    if (T >= 0.5f && Tn < 0.5f) {
+                        med = b.z;
+                        med_pos = (int)(base + k);
+                    }
                     T = Tn;
                     last = base + k + 1;
                     ++n_blend;
@@ -110,6 +114,7 @@ __global__ void __launch_bounds__(TILE *TILE, 1024 / (TILE * TILE))
     out.T_final[pix] = T;
     out.n_last[pix] = (int32_t)last;
     if (out.n_contrib) out.n_contrib[pix] = n_blend;
+    if (out.median_pos) out.median_pos[pix] = med_pos;
 }
 
 }  // namespace

@@ -15,7 +15,7 @@ import torch
 from . import _abi as A
 from ._abi import Gaussians
 
-CHANNELS = ("color", "depth", "alpha", "unc", "nu_map", "median", "T_final", "n_last", "n_contrib")
+CHANNELS = ("color", "depth", "alpha", "unc", "nu_map", "median", "T_final", "n_last", "n_contrib", "median_pos")
 
 
 def _pix(cams) -> int:
@@ -60,6 +60,7 @@ class Rasterizer:
             "T_final": torch.empty(P, dtype=torch.float32, device=dev),
             "n_last": torch.empty(P, dtype=torch.int32, device=dev),
             "n_contrib": torch.empty(P, dtype=torch.int32, device=dev),
+            "median_pos": torch.empty(P, dtype=torch.int32, device=dev),
         }
         self.keep_keys = keep_keys
         self.values = self.keys = self.bin_ws = None
@@ -160,7 +161,6 @@ class GaussianRasterize(torch.autograd.Function):
         ctx.rast, ctx.g, ctx.T_cw, ctx.obs_depth = rast, g, T_cw, obs_depth
         im = rast.img
         outs = tuple(im[k].clone() for k in ("color", "depth", "alpha", "unc", "nu_map", "median"))
-        ctx.mark_non_differentiable(outs[5])
         return outs
 
     @staticmethod
@@ -168,7 +168,8 @@ class GaussianRasterize(torch.autograd.Function):
         rast: Rasterizer = ctx.rast
         g: Gaussians = ctx.g
         dL = {}
-        for k, v in (("color", g_color), ("depth", g_depth), ("alpha", g_alpha), ("unc", g_unc), ("nu_map", g_nu)):
+        for k, v in (("color", g_color), ("depth", g_depth), ("alpha", g_alpha), ("unc", g_unc), ("nu_map", g_nu),
+                     ("median", g_median)):
             if v is not None:
                 dL[k] = v.contiguous()
         if "unc" in dL and ctx.obs_depth is None:

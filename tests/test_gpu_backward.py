@@ -31,8 +31,13 @@ def _setup(mode, sc, cam, T, tile=16):
 
 def _loss_dict(tc, td, w=(1.0, 1.0, 1.0, 1.0, 0.0)):
     return dict(w_color=w[0], w_depth=w[1], w_unc=w[2], w_nu=w[3], unc_tau=w[4],
+                w_align=w[5] if len(w) > 5 else 0.0,
                 target_color=torch.from_numpy(np.ascontiguousarray(tc)).cuda().reshape(-1),
                 target_depth=torch.from_numpy(np.ascontiguousarray(td)).cuda().reshape(-1))
+
+
+def _spec(w, tc, td):
+    return oracle.LossSpec(*w[:5], target_color=tc, target_depth=td, w_align=w[5] if len(w) > 5 else 0.0)
 
 
 def _run(mode, sc, cam, T, tc, td, w, tile=16):
@@ -65,6 +70,7 @@ def _case(posed=True):
 
 W_ALL = (1.0, 1.0, 1.0, 1.0, 0.0)       # colour + depth + |U| + nu: every parameter gets a gradient
 W_TRACK = (0.2, 1.0, 0.0, 0.0, 0.025)   # tracking: lambda = {0.2, 1.0}, uncertainty weighting
+W_ALIGN = (0.7, 0.25, 0.0, 0.0, 0.0, 0.25)  # mapping-style weights incl. L_align (Eq. 12, Sec. 4)
 
 
 def _rel_check(name, got, want, elem=1e-4, norm=1e-5):
@@ -77,12 +83,12 @@ def _rel_check(name, got, want, elem=1e-4, norm=1e-5):
     assert e_max < elem and e_norm < norm, (name, e_max, e_norm)
 
 
-@pytest.mark.parametrize("w", [W_ALL, W_TRACK])
+@pytest.mark.parametrize("w", [W_ALL, W_TRACK, W_ALIGN])
 def test_full_mode_gradients_match_oracle(w):
     from paper_2403_16095_b300 import _abi as A
     sc, cam, T, tc, td = _case()
     r, grads = _run(A.GS_MODE_FULL, sc, cam, T, tc, td, w)
-    L = oracle.LossSpec(*w, target_color=tc, target_depth=td)
+    L = _spec(w, tc, td)
     og = oracle.grad(f32_scene(sc), cam, T, L)
     for k in PARAMS:
         if k == "nu" and w[3] == 0:
