@@ -47,7 +47,8 @@ class _Loss(C.Structure):
 
 class _Image(C.Structure):
     _fields_ = [("color", _dp), ("depth", _dp), ("alpha", _dp), ("unc", _dp), ("nu_map", _dp),
-                ("median", _dp), ("T_final", _dp), ("n_contrib", _ip), ("margins", _dp)]
+                ("median", _dp), ("T_final", _dp), ("n_contrib", _ip), ("margins", _dp),
+                ("dominant", _ip), ("dom_weight", _dp), ("dom_margin", _dp)]
 
 
 class _Grads(C.Structure):
@@ -167,9 +168,11 @@ def _image_bufs(n_pix, H=None, W=None):
     shp = (n_pix,) if H is None else (H, W)
     o = dict(color=np.zeros((3, *shp)), depth=np.zeros(shp), alpha=np.zeros(shp), unc=np.zeros(shp),
              nu_map=np.zeros(shp), median=np.zeros(shp), T_final=np.zeros(shp),
-             n_contrib=np.zeros(shp, np.int32), margins=np.zeros((6, *shp)))
-    im = _Image(*(_p(o[k], _ip if k == "n_contrib" else _dp) for k in
-                  ("color", "depth", "alpha", "unc", "nu_map", "median", "T_final", "n_contrib", "margins")))
+             n_contrib=np.zeros(shp, np.int32), margins=np.zeros((6, *shp)),
+             dominant=np.zeros(shp, np.int32), dom_weight=np.zeros(shp), dom_margin=np.zeros(shp))
+    im = _Image(*(_p(o[k], _ip if k in ("n_contrib", "dominant") else _dp) for k in
+                  ("color", "depth", "alpha", "unc", "nu_map", "median", "T_final", "n_contrib", "margins",
+                   "dominant", "dom_weight", "dom_margin")))
     return o, im
 
 
@@ -177,7 +180,9 @@ def render(scene, cam, T, obs_depth=None, mode="rect", jclamp=1.3, nu_cull=0.0):
     """Full image, FP64. mode 'rect' (rect-scatter lists) or 'brute' (scan every
     Gaussian per pixel). Returns planar arrays: color [3,H,W], others [H,W];
     margins [6,H,W] are the per-pixel decision margins (q vs 9, alpha vs 1/255,
-    T' vs 1e-4, opacity*G vs 0.99, relative depth gap of neighbours, T' vs 0.5)."""
+    T' vs 1e-4, opacity*G vs 0.99, relative depth gap of neighbours, T' vs 0.5).
+    dominant [H,W] is the Gaussian with the largest blend weight (-1: none),
+    dom_weight that weight and dom_margin its relative lead over the runner-up."""
     k = _Keep(scene)
     Tc = _f64(T).reshape(3, 4)
     od = None if obs_depth is None else _f64(obs_depth)
@@ -233,6 +238,44 @@ def grad(scene, cam, T, L: LossSpec, jclamp=1.3, nu_cull=0.0):
     assert r == 0
     o["loss"] = v.value
     return o
+
+
+def nu_estimate(scene, cams, Ts, obs_depths, tau=0.0, low_opacity=0.01, jclamp=1.3, nu_cull=0.0):
+    """Per-Gaussian depth uncertainty of Eq. 13 over a keyframe window (Sec. 3.2).
+
+    In frame f, pixel p is a dominated pixel of the Gaussian i with the largest
+    blend weight w = alpha T on p (the first in blend order on ties); i receives
+    w (D_p - d_i)^2 with D_p the sensor depth and d_i its camera-space depth in
+    f. nu_i = (sum over the window) / (M_1 + ... + M_k), its dominated-pixel
+    count; a Gaussian with no dominated pixel keeps its nu. With tau > 0, every
+    Gaussian with nu_i > tau has its opacity lowered to ``low_opacity`` (its
+    logit becomes min(logit, logit(low_opacity))).
+
+    Returns num [N], cnt [N] (int64), nu [N], over [N] (bool), opacity_logit
+    [N] and the per-frame oracle images (with their dominant maps)."""
+    n = scene.n
+    num = np.zeros(n)
+    cnt = np.zeros(n, np.int64)
+    images = []
+    for cam, T, D in zip(cams, Ts, obs_depths):
+        im = render(scene, cam, T, jclamp=jclamp, nu_cull=nu_cull)
+        d = project(scene, cam, T, jclamp=jclamp, nu_cull=nu_cull)["depth"]
+        dom = im["dominant"].reshape(-1)
+        w = im["dom_weight"].reshape(-1)
+        Dp = _f64(D).reshape(-1)
+        sel = dom >= 0
+        i = dom[sel]
+        np.add.at(num, i, w[sel] * (Dp[sel] - d[i]) ** 2)
+        np.add.at(cnt, i, 1)
+        images.append(im)
+    nu = _f64(scene.nu).copy()
+    has = cnt > 0
+    nu[has] = num[has] / cnt[has]
+    over = nu > tau if tau > 0 else np.zeros(n, bool)
+    logit = _f64(scene.opacity_logit).copy()
+    low = np.log(low_opacity / (1.0 - low_opacity))
+    logit[over] = np.minimum(logit[over], low)
+    return dict(num=num, cnt=cnt, nu=nu, over=over, opacity_logit=logit, images=images)
 
 
 def bin_tiles(rect, depth_f32, n_per_frame, tile, cams, capacity=None):

@@ -70,6 +70,9 @@ typedef struct { /* optional outputs; NULL members are skipped */
     double *color, *depth, *alpha, *unc, *nu_map, *median, *T_final; /* color [3][H][W] */
     int *n_contrib;
     double *margins; /* [6][H][W]: q-9, alpha-1/255, T'-1e-4, opacity*G-0.99, depth gap, T'-0.5 */
+    int *dominant;      /* Gaussian with the largest blend weight (Sec. 3.2), -1 if none */
+    double *dom_weight; /* that weight w = alpha T                                       */
+    double *dom_margin; /* (w_max - second largest w) / w_max; +inf with < 2 entries     */
 } orc_image;
 
 typedef struct { /* gradient outputs; NULL members are skipped */
@@ -249,6 +252,8 @@ typedef struct {
     double color[3], depth, alpha, unc, nu, median, T;
     int n;
     int med;  /* index (among the blended entries) of the median Gaussian, -1 if none */
+    int dom;  /* dominant Gaussian: largest w, the first one in blend order on ties; -1 if none */
+    double wmax, w2;  /* largest and second largest blend weight */
     double margin[6];
     uint64_t hash;
 } pixout;
@@ -263,6 +268,7 @@ static void blend_pixel(const orc_scene *sc, const gproj *G, const zent *list, i
                         double Dp, int has_D, pixout *o, contrib *cb) {
     memset(o, 0, sizeof(*o));
     o->med = -1;
+    o->dom = -1;
     for (int k = 0; k < 6; ++k) o->margin[k] = INFINITY;
     o->hash = 1469598103934665603ULL;
     double T = 1.0;
@@ -302,6 +308,8 @@ static void blend_pixel(const orc_scene *sc, const gproj *G, const zent *list, i
         if (has_D) o->unc += w * (g->p[2] - Dp) * (g->p[2] - Dp);
         o->nu += w * sc->nu[k];
         if (T >= 0.5 && Tn < 0.5) { o->median = g->p[2]; o->med = o->n; }
+        if (w > o->wmax) { o->w2 = o->wmax; o->wmax = w; o->dom = k; }
+        else if (w > o->w2) o->w2 = w;
         if (cb) {
             contrib *c = &cb[o->n];
             c->k = k; c->alpha = a; c->T = T; c->G = Gv; c->dx = dx; c->dy = dy; c->clamped = clamped;
@@ -342,6 +350,9 @@ static void store_pixel(orc_image *im, int HW, int p, const pixout *o) {
     if (im->T_final) im->T_final[p] = o->T;
     if (im->n_contrib) im->n_contrib[p] = o->n;
     if (im->margins) for (int k = 0; k < 6; ++k) im->margins[k * HW + p] = o->margin[k];
+    if (im->dominant) im->dominant[p] = o->dom;
+    if (im->dom_weight) im->dom_weight[p] = o->wmax;
+    if (im->dom_margin) im->dom_margin[p] = o->n >= 2 ? (o->wmax - o->w2) / o->wmax : INFINITY;
 }
 
 /* ---------------------------------------------------------------- loss */
