@@ -59,7 +59,7 @@ extern "C" {
 #endif
 
 #define GS_MAX_FRAMES 64
-#define GS_ABI_VERSION 1
+#define GS_ABI_VERSION 2
 
 typedef struct CUstream_st *gs_stream; /* a cudaStream_t; NULL = legacy default stream */
 
@@ -142,6 +142,10 @@ typedef struct {
     int32_t *n_contrib; /* number of blended entries per pixel, or NULL            */
     int32_t *median_pos; /* tile-list position of the median entry (-1: none), or
                             NULL; needed by a backward with a median-depth gradient */
+    int32_t *dom_pos;    /* tile-list position of the pixel's dominant entry, the one
+                            with the largest blend weight w = alpha T (the first in
+                            blend order on ties; -1: none), or NULL (Sec. 3.2)    */
+    float *dom_weight;   /* that weight (0: none); set iff dom_pos is set          */
 } gs_image;
 
 /* Upstream gradients dL/d(channel) per pixel (same layouts); NULL = zero. A
@@ -197,8 +201,8 @@ gs_status gs_project(const gs_gaussians *g, int n_frames, const gs_camera *cams,
 
 /* Sec. 3.1 pre-sort. Emits one (key, record) pair per tile overlapped by each
  * record's tile rect, key = (global tile id << 32) | float bits of z, sorts the
- * pairs by key with a stable LSD radix sort (ties keep record order) and writes
- * each tile's [start, end). The result is bit-exact and independent of the
+ * pairs by key, ties in record order (a counting pass by tile, then a radix sort
+ * of (z bits, record) inside each tile), and writes each tile's [start, end). The result is bit-exact and independent of the
  * launch configuration. If the pairs exceed tiles->capacity, status[0] is set to
  * GS_ERR_CAPACITY and status[1] to the pairs needed; later kernels then no-op.
  *   status: device int32[4]; ws: device scratch of
@@ -258,6 +262,33 @@ gs_status gs_render_bwd(const gs_projected *proj, const gs_tiles *tiles, int n_f
                         const gs_loss *loss, const gs_opts *opts, gs_grads *grads,
                         float *pose_partials, double *pose_grad, const int32_t *status, void *ws,
                         size_t ws_bytes, gs_stream stream);
+
+/* Per-Gaussian depth uncertainty, Eq. 13 (Sec. 3.2), accumulation half. Each
+ * pixel of the n_frames images whose forward found a dominant entry
+ * (fwd->dom_pos >= 0) adds, for that entry's Gaussian i,
+ *     nu_num[i] += w (D_p - d_i)^2   (FP64; w = fwd->dom_weight, D_p = obs_depth,
+ *                                     d_i = the record's projected depth z)
+ *     nu_cnt[i] += 1                 (its dominated pixels M)
+ * Calls add to the caller's arrays: zero them, then accumulate every frame of the
+ * keyframe window (one batched call or several). The FP64 additions run in an
+ * unspecified order (atomics): nu_num is reproducible to FP64 rounding, nu_cnt
+ * exactly. dominant: NULL or int32 [.][H][W], set to the Gaussian index of each
+ * pixel's dominant entry (-1: none).
+ *   nu_num: device double [N]; nu_cnt: device uint32 [N].                     */
+gs_status gs_nu_accumulate(const gs_projected *proj, const gs_tiles *tiles, int n_frames,
+                           const gs_camera *cams, const float *obs_depth, const gs_image *fwd,
+                           double *nu_num, uint32_t *nu_cnt, int32_t *dominant,
+                           const int32_t *status, gs_stream stream);
+
+/* Eq. 13 finish and the tau rule of Sec. 3.2. For each of the n Gaussians with
+ * nu_cnt > 0: nu = nu_num / nu_cnt (FP64, stored as FP32); the others keep nu.
+ * If tau > 0 and opacity_logit is not NULL, every Gaussian whose FP64 nu
+ * exceeds tau gets opacity_logit = min(opacity_logit, low_opacity_logit) (the
+ * paper lowers uncertain primitives to a low opacity instead of deleting them)
+ * and, if n_over is not NULL, is counted into *n_over (device uint32, added). */
+gs_status gs_nu_finalize(int n, const double *nu_num, const uint32_t *nu_cnt, float *nu, float tau,
+                         float low_opacity_logit, float *opacity_logit, uint32_t *n_over,
+                         const int32_t *status, gs_stream stream);
 
 /* Deterministic pose-gradient reduction (Sec. 3.4): pose_grad[f][k] =
  * sum_j partials[f][j][k], summed as double-floats (FP32 hi/lo pairs with

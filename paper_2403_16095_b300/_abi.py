@@ -64,7 +64,8 @@ class gs_tiles(C.Structure):
 
 class gs_image(C.Structure):
     _fields_ = [("color", _vp), ("depth", _vp), ("alpha", _vp), ("unc", _vp), ("nu_map", _vp),
-                ("median", _vp), ("T_final", _vp), ("n_last", _vp), ("n_contrib", _vp), ("median_pos", _vp)]
+                ("median", _vp), ("T_final", _vp), ("n_last", _vp), ("n_contrib", _vp), ("median_pos", _vp),
+                ("dom_pos", _vp), ("dom_weight", _vp)]
 
 
 class gs_image_grad(C.Structure):
@@ -88,8 +89,9 @@ class gs_adam(C.Structure):
 
 EXPORTS = ("gs_abi_version", "gs_last_error", "gs_project", "gs_bin_tiles_workspace_size", "gs_bin_tiles",
            "gs_bin_tiles_noalloc", "gs_render_fwd", "gs_pose_partials_per_frame", "gs_render_bwd_workspace_size",
-           "gs_render_bwd", "gs_pose_grad_reduce", "gs_pose_adam_step")
+           "gs_render_bwd", "gs_nu_accumulate", "gs_nu_finalize", "gs_pose_grad_reduce", "gs_pose_adam_step")
 GS_NOALLOC_MAX_PAIRS = 1 << 19
+ABI_VERSION = 2  # GS_ABI_VERSION of the gs.h these structures mirror
 
 
 def _load():
@@ -97,6 +99,8 @@ def _load():
         raise ImportError(f"libgs.so not built at {LIB_PATH}; run `python -m paper_2403_16095_b300.build`")
     lib = C.CDLL(LIB_PATH)
     lib.gs_abi_version.restype = C.c_int
+    if lib.gs_abi_version() != ABI_VERSION:
+        raise ImportError(f"libgs.so has ABI {lib.gs_abi_version()}, this binding needs {ABI_VERSION}; rebuild it")
     lib.gs_last_error.restype = C.c_char_p
     lib.gs_project.argtypes = [C.POINTER(gs_gaussians), C.c_int, C.POINTER(gs_camera), _vp,
                                C.POINTER(gs_opts), C.POINTER(gs_projected), _vp, _vp]
@@ -117,10 +121,13 @@ def _load():
                                   _vp, C.POINTER(gs_gaussians), _vp, C.POINTER(gs_image),
                                   C.POINTER(gs_image_grad), C.POINTER(gs_loss), C.POINTER(gs_opts),
                                   C.POINTER(gs_grads), _vp, _vp, _vp, _vp, C.c_size_t, _vp]
+    lib.gs_nu_accumulate.argtypes = [C.POINTER(gs_projected), C.POINTER(gs_tiles), C.c_int, C.POINTER(gs_camera),
+                                     _vp, C.POINTER(gs_image), _vp, _vp, _vp, _vp, _vp]
+    lib.gs_nu_finalize.argtypes = [C.c_int, _vp, _vp, _vp, C.c_float, C.c_float, _vp, _vp, _vp, _vp]
     lib.gs_pose_grad_reduce.argtypes = [_vp, C.c_int, C.c_int, _vp, _vp, _vp]
     lib.gs_pose_adam_step.argtypes = [_vp, _vp, _vp, C.c_int, C.POINTER(gs_adam), _vp, _vp]
-    for name in ("gs_project", "gs_bin_tiles", "gs_render_fwd", "gs_render_bwd", "gs_pose_grad_reduce",
-                 "gs_pose_adam_step"):
+    for name in ("gs_project", "gs_bin_tiles", "gs_render_fwd", "gs_render_bwd", "gs_nu_accumulate",
+                 "gs_nu_finalize", "gs_pose_grad_reduce", "gs_pose_adam_step"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -237,10 +244,10 @@ def gs_bin_tiles_noalloc(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tenso
 
 
 def _image(img: dict) -> gs_image:
-    ints = ("n_last", "n_contrib", "median_pos")
+    ints = ("n_last", "n_contrib", "median_pos", "dom_pos")
     return gs_image(*(_ptr(img.get(k), torch.int32 if k in ints else torch.float32, k)
                       for k in ("color", "depth", "alpha", "unc", "nu_map", "median", "T_final", "n_last",
-                                "n_contrib", "median_pos")))
+                                "n_contrib", "median_pos", "dom_pos", "dom_weight")))
 
 
 def gs_render_fwd(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tensor, values: torch.Tensor,
@@ -297,6 +304,31 @@ def gs_render_bwd(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tensor, pose
                              _ptr(pose_grad, torch.float64, "pose_grad", 6 * F),
                              _ptr(status, torch.int32, "status", 4), _ptr(ws, torch.uint8, "ws"), ws.numel(),
                              _stream(stream)))
+
+
+def gs_nu_accumulate(n_gaussians: int, cams, rec: torch.Tensor, values: torch.Tensor, obs_depth: torch.Tensor,
+                     fwd: dict, nu_num: torch.Tensor, nu_cnt: torch.Tensor, dominant: Optional[torch.Tensor],
+                     status: torch.Tensor, stream=None) -> None:
+    F = len(cams)
+    proj = gs_projected(n_gaussians, F, _ptr(rec, torch.float32, "rec"), 1, None)
+    tiles = gs_tiles(values.numel(), 0, _ptr(values, torch.int32, "values"), None, None)
+    _check(lib.gs_nu_accumulate(C.byref(proj), C.byref(tiles), F, cameras(cams),
+                                _ptr(obs_depth, torch.float32, "obs_depth"), C.byref(_image(fwd)),
+                                _ptr(nu_num, torch.float64, "nu_num", n_gaussians),
+                                _ptr(nu_cnt, torch.int32, "nu_cnt", n_gaussians),
+                                _ptr(dominant, torch.int32, "dominant"), _ptr(status, torch.int32, "status", 4),
+                                _stream(stream)))
+
+
+def gs_nu_finalize(nu_num: torch.Tensor, nu_cnt: torch.Tensor, nu: torch.Tensor, tau: float,
+                   low_opacity_logit: float, opacity_logit: Optional[torch.Tensor], n_over: Optional[torch.Tensor],
+                   status: torch.Tensor, stream=None) -> None:
+    n = nu.numel()
+    _check(lib.gs_nu_finalize(n, _ptr(nu_num, torch.float64, "nu_num", n), _ptr(nu_cnt, torch.int32, "nu_cnt", n),
+                              _ptr(nu, torch.float32, "nu"), float(tau), float(low_opacity_logit),
+                              _ptr(opacity_logit, torch.float32, "opacity_logit", n),
+                              _ptr(n_over, torch.int32, "n_over", 1), _ptr(status, torch.int32, "status", 4),
+                              _stream(stream)))
 
 
 def gs_pose_grad_reduce(partials: torch.Tensor, n_frames: int, per_frame: int, pose_grad: torch.Tensor,

@@ -172,8 +172,10 @@ gs_status gs_render_fwd(const gs_projected *proj, const gs_tiles *tiles, int n_f
     GS_TRY(check_tiles(tiles, ft));
     if (!out || !out->color || !out->T_final || !out->n_last) return fail(GS_ERR_INVALID_ARG, "image color/T_final/n_last required");
     if (!status) return fail(GS_ERR_INVALID_ARG, "status NULL");
+    if ((out->dom_pos == nullptr) != (out->dom_weight == nullptr))
+        return fail(GS_ERR_INVALID_ARG, "dom_pos and dom_weight go together");
     gs::ImagePtrs ip{out->color, out->depth, out->alpha, out->unc, out->nu_map, out->median, out->T_final, out->n_last,
-                     out->n_contrib, out->median_pos};
+                     out->n_contrib, out->median_pos, out->dom_pos, out->dom_weight};
     return cuda_status(gs::launch_render_fwd(proj->rec, tiles->values, tiles->ranges, ft, obs_depth, ip, status, stream),
                        "gs_render_fwd");
 }
@@ -226,7 +228,7 @@ gs_status gs_render_bwd(const gs_projected *proj, const gs_tiles *tiles, int n_f
         return fail(GS_ERR_INVALID_ARG, "either dL or loss is required");
     }
     gs::ImagePtrs ip{fwd->color, fwd->depth, fwd->alpha, fwd->unc, fwd->nu_map, fwd->median, fwd->T_final, fwd->n_last,
-                     fwd->n_contrib, fwd->median_pos};
+                     fwd->n_contrib, fwd->median_pos, nullptr, nullptr};
     const int N = proj->n_gaussians;
     const int M = N * n_frames;
     const int per_frame = gs_pose_partials_per_frame(mode, N, n_frames, cams, opts->tile);
@@ -264,6 +266,35 @@ gs_status gs_render_bwd(const gs_projected *proj, const gs_tiles *tiles, int n_f
     return cuda_status(gs::launch_project_bwd(gauss_ptrs(g), N, ft, T_cw, opts->jclamp, proj->rec, grad2d, *grads,
                                               pose_partials, per_frame, pose_grad, counters, status, stream),
                        "gs_render_bwd (projection adjoint)");
+}
+
+gs_status gs_nu_accumulate(const gs_projected *proj, const gs_tiles *tiles, int n_frames, const gs_camera *cams,
+                           const float *obs_depth, const gs_image *fwd, double *nu_num, uint32_t *nu_cnt,
+                           int32_t *dominant, const int32_t *status, gs_stream stream) {
+    gs::FrameTable ft;
+    GS_TRY(make_frames(n_frames, cams, 16, ft));
+    GS_TRY(check_proj(proj, n_frames));
+    if (!tiles || !tiles->values) return fail(GS_ERR_INVALID_ARG, "tiles.values NULL");
+    if (!fwd || !fwd->dom_pos || !fwd->dom_weight)
+        return fail(GS_ERR_INVALID_ARG, "fwd.dom_pos and fwd.dom_weight (from gs_render_fwd) required");
+    if (!obs_depth) return fail(GS_ERR_INVALID_ARG, "obs_depth (sensor depth D of Eq. 13) required");
+    if (!nu_num || !nu_cnt || !status) return fail(GS_ERR_INVALID_ARG, "nu_num/nu_cnt/status NULL");
+    if (!aligned(nu_num, 8) || !aligned(nu_cnt, 4)) return fail(GS_ERR_INVALID_ARG, "nu_num/nu_cnt misaligned");
+    return cuda_status(gs::launch_nu_accumulate(proj->rec, tiles->values, ft, proj->n_gaussians, obs_depth, fwd->dom_pos,
+                                                fwd->dom_weight, nu_num, nu_cnt, dominant, status, stream),
+                       "gs_nu_accumulate");
+}
+
+gs_status gs_nu_finalize(int n, const double *nu_num, const uint32_t *nu_cnt, float *nu, float tau,
+                         float low_opacity_logit, float *opacity_logit, uint32_t *n_over, const int32_t *status,
+                         gs_stream stream) {
+    if (n < 0) return fail(GS_ERR_INVALID_ARG, "n < 0");
+    if (!status) return fail(GS_ERR_INVALID_ARG, "status NULL");
+    if (n > 0 && (!nu_num || !nu_cnt || !nu)) return fail(GS_ERR_INVALID_ARG, "nu_num/nu_cnt/nu NULL");
+    if (!(tau == tau) || !(low_opacity_logit == low_opacity_logit)) return fail(GS_ERR_INVALID_ARG, "tau/low_opacity_logit NaN");
+    return cuda_status(gs::launch_nu_finalize(n, nu_num, nu_cnt, nu, tau, low_opacity_logit, opacity_logit, n_over,
+                                              status, stream),
+                       "gs_nu_finalize");
 }
 
 gs_status gs_pose_grad_reduce(const float *partials, int n_frames, int per_frame, double *pose_grad,

@@ -44,7 +44,8 @@ struct GaussPtrs {
 
 struct ImagePtrs {
     float *color, *depth, *alpha, *unc, *nu_map, *median, *T_final;
-    int32_t *n_last, *n_contrib, *median_pos;
+    int32_t *n_last, *n_contrib, *median_pos, *dom_pos;
+    float *dom_weight;
 };
 
 struct LossParams {
@@ -87,6 +88,14 @@ cudaError_t launch_render_bwd(int mode, const float *rec, const float *jac, cons
                               const ImagePtrs &fwd, const LossParams &lp, float *grad2d, float *pose_partials,
                               int per_frame, double *pose_grad, unsigned *counters, const int32_t *status,
                               cudaStream_t s);
+// nu.cu
+cudaError_t launch_nu_accumulate(const float *rec, const uint32_t *values, const FrameTable &ft, int n_gaussians,
+                                 const float *obs_depth, const int32_t *dom_pos, const float *dom_weight,
+                                 double *nu_num, uint32_t *nu_cnt, int32_t *dominant, const int32_t *status,
+                                 cudaStream_t s);
+cudaError_t launch_nu_finalize(int n, const double *nu_num, const uint32_t *nu_cnt, float *nu, float tau,
+                               float low_logit, float *opacity_logit, uint32_t *n_over, const int32_t *status,
+                               cudaStream_t s);
 // pose.cu
 cudaError_t launch_pose_reduce(const float *partials, int n_frames, int per_frame, double *out,
                                const int32_t *status, cudaStream_t s);

@@ -10,13 +10,17 @@
 // The per-pixel arithmetic (q, G, alpha, T) is the same function as in the
 // backward pass, written with explicitly rounded operations, so both passes take
 // identical accept/stop decisions and the result does not depend on TILE.
+//
+// The DOM variant also tracks each pixel's dominant entry (largest w = alpha T,
+// the first on ties; Sec. 3.2) for the per-Gaussian uncertainty of Eq. 13; it
+// is a separate instantiation so that tracking pays nothing for it.
 #include "gs_internal.cuh"
 #include "blend_common.cuh"
 
 namespace gs {
 namespace {
 
-template <int TILE>
+template <int TILE, bool DOM>
 __global__ void __launch_bounds__(TILE *TILE, 1024 / (TILE * TILE))
     k_render_fwd(const float4 *__restrict__ rec, const uint32_t *__restrict__ values,
                  const uint2 *__restrict__ ranges, FrameTable ft, const float *__restrict__ obs_depth, ImagePtrs out,
@@ -46,6 +50,8 @@ __global__ void __launch_bounds__(TILE *TILE, 1024 / (TILE * TILE))
     uint32_t last = range.x;
     int n_blend = 0;
     int med_pos = -1;  // tile-list position of the median entry
+    float wmax = 0.f;  // DOM: largest blend weight so far and its position
+    int dom_pos = -1;
     bool done = !inside;
 
     for (uint32_t base = range.x; base < range.y; base += BATCH) {
@@ -92,6 +98,10 @@ __global__ void __launch_bounds__(TILE *TILE, 1024 / (TILE * TILE))
                         med = b.z;
                         med_pos = (int)(base + k);
                     }
+                    if (DOM && w > wmax) {
+                        wmax = w;
+                        dom_pos = (int)(base + k);
+                    }
                     T = Tn;
                     last = base + k + 1;
                     ++n_blend;
@@ -115,6 +125,20 @@ __global__ void __launch_bounds__(TILE *TILE, 1024 / (TILE * TILE))
     out.n_last[pix] = (int32_t)last;
     if (out.n_contrib) out.n_contrib[pix] = n_blend;
     if (out.median_pos) out.median_pos[pix] = med_pos;
+    if (DOM) {
+        out.dom_pos[pix] = dom_pos;
+        out.dom_weight[pix] = wmax;
+    }
+}
+
+template <int TILE>
+cudaError_t launch_tile(const float4 *r4, const uint32_t *values, const uint2 *rg, const FrameTable &ft,
+                        const float *obs_depth, const ImagePtrs &out, const int32_t *status, cudaStream_t s) {
+    if (out.dom_pos)
+        k_render_fwd<TILE, true><<<ft.total_tiles, TILE * TILE, 0, s>>>(r4, values, rg, ft, obs_depth, out, status);
+    else
+        k_render_fwd<TILE, false><<<ft.total_tiles, TILE * TILE, 0, s>>>(r4, values, rg, ft, obs_depth, out, status);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -125,12 +149,11 @@ cudaError_t launch_render_fwd(const float *rec, const uint32_t *values, const ui
     const float4 *r4 = reinterpret_cast<const float4 *>(rec);
     const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
     switch (ft.tile) {
-        case 8: k_render_fwd<8><<<ft.total_tiles, 64, 0, s>>>(r4, values, rg, ft, obs_depth, out, status); break;
-        case 16: k_render_fwd<16><<<ft.total_tiles, 256, 0, s>>>(r4, values, rg, ft, obs_depth, out, status); break;
-        case 32: k_render_fwd<32><<<ft.total_tiles, 1024, 0, s>>>(r4, values, rg, ft, obs_depth, out, status); break;
+        case 8: return launch_tile<8>(r4, values, rg, ft, obs_depth, out, status, s);
+        case 16: return launch_tile<16>(r4, values, rg, ft, obs_depth, out, status, s);
+        case 32: return launch_tile<32>(r4, values, rg, ft, obs_depth, out, status, s);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 }  // namespace gs

@@ -31,7 +31,7 @@ class Rasterizer:
 
     def __init__(self, cams: Sequence, n_gaussians: int, tile: int = 16, mode: int = A.GS_MODE_POSE,
                  capacity: Optional[int] = None, jclamp: float = 1.3, nu_cull: float = 0.0,
-                 keep_keys: bool = False, device=None):
+                 keep_keys: bool = False, dominant: bool = False, device=None):
         self.cams = list(cams)
         self.F = len(self.cams)
         self.N = int(n_gaussians)
@@ -62,6 +62,9 @@ class Rasterizer:
             "n_contrib": torch.empty(P, dtype=torch.int32, device=dev),
             "median_pos": torch.empty(P, dtype=torch.int32, device=dev),
         }
+        if dominant:  # dominated pixels for the uncertainty of Eq. 13
+            self.img["dom_pos"] = torch.empty(P, dtype=torch.int32, device=dev)
+            self.img["dom_weight"] = torch.empty(P, dtype=torch.float32, device=dev)
         self.keep_keys = keep_keys
         self.values = self.keys = self.bin_ws = None
         self.set_capacity(capacity if capacity is not None else max(4096, 2 * self.M))
@@ -109,6 +112,35 @@ class Rasterizer:
                         obs_depth, self.img, dL, loss, grads, self.pose_partials,
                         self.pose_grad if fused_pose else None, self.status, self.bwd_ws, stream)
 
+    def nu_accumulate(self, obs_depth: torch.Tensor, nu_num: torch.Tensor, nu_cnt: torch.Tensor,
+                      dominant: Optional[torch.Tensor] = None, stream=None) -> None:
+        """Eq. 13: add every dominated pixel of this batch's frames to nu_num
+        (float64 [N]) and nu_cnt (int32 [N], used as uint32); needs a forward of a
+        Rasterizer built with dominant=True."""
+        if "dom_pos" not in self.img:
+            raise ValueError("Rasterizer was built without dominant=True")
+        A.gs_nu_accumulate(self.N, self.cams, self.rec, self.values, obs_depth, self.img, nu_num, nu_cnt, dominant,
+                           self.status, stream)
+
+    def estimate_nu(self, g: Gaussians, T_cw: torch.Tensor, obs_depth: torch.Tensor, tau: float = 0.025,
+                    low_opacity: float = 0.01, dominant: Optional[torch.Tensor] = None) -> int:
+        """Per-Gaussian uncertainty over this batch's keyframe window (Sec. 3.2):
+        render, accumulate Eq. 13, set g.nu in place and lower the opacity of every
+        Gaussian with nu > tau to ``low_opacity`` (tau <= 0: no opacity change).
+        Returns how many Gaussians exceeded tau (synchronises)."""
+        self.render(g, T_cw, obs_depth)
+        num = torch.zeros(self.N, dtype=torch.float64, device=self.device)
+        cnt = torch.zeros(self.N, dtype=torch.int32, device=self.device)
+        n_over = torch.zeros(1, dtype=torch.int32, device=self.device)
+        self.nu_accumulate(obs_depth, num, cnt, dominant)
+        low = math.log(low_opacity / (1.0 - low_opacity))
+        A.gs_nu_finalize(num, cnt, g.nu, tau, low, g.opacity_logit if tau > 0 else None, n_over, self.status)
+        self.last_nu = (num, cnt)
+        code, _ = self.read_status()
+        if code != 0:
+            raise A.GsError(code, "device status")
+        return int(n_over.item())
+
     def reduce_pose(self, stream=None) -> None:
         A.gs_pose_grad_reduce(self.pose_partials, self.F, self.per_frame, self.pose_grad, self.status, stream)
 
@@ -135,7 +167,7 @@ class Rasterizer:
         H, W = int(c.height), int(c.width)
         off = sum(int(x.width) * int(x.height) for x in self.cams[:f])
         out = {"color": self.img["color"][3 * off: 3 * off + 3 * H * W].view(3, H, W)}
-        for k in CHANNELS[1:]:
+        for k in CHANNELS[1:] + tuple(k for k in ("dom_pos", "dom_weight") if k in self.img):
             out[k] = self.img[k][off: off + H * W].view(H, W)
         return out
 
