@@ -59,7 +59,7 @@ extern "C" {
 #endif
 
 #define GS_MAX_FRAMES 64
-#define GS_ABI_VERSION 2
+#define GS_ABI_VERSION 3
 
 typedef struct CUstream_st *gs_stream; /* a cudaStream_t; NULL = legacy default stream */
 
@@ -167,6 +167,21 @@ typedef struct {
     float w_align;              /* L_align of Eq. 12                          */
 } gs_loss;
 
+/* 16-bit storage of the Gaussians (tracking and rendering; mapping keeps FP32).
+ * Gaussian i is the 32-byte record packed[i] of 16 16-bit values
+ *   (q x, y, z: uint16 fixed-point mean; then BF16 log-scale x, y, z,
+ *    quat w, x, y, z, opacity logit, r, g, b, nu, 0)
+ * and chunk c = i / GS_BF16_CHUNK has the FP32 box anchors[c] =
+ *   (lo x, lo y, lo z, step x, step y, step z, 0, 0);
+ * mean = lo + step * q per axis (FP32 multiply, then add). Written by
+ * gs_pack_bf16.                                                            */
+#define GS_BF16_CHUNK 256
+typedef struct {
+    int n;
+    const float *anchors;    /* [ceil(n / GS_BF16_CHUNK)][8], 16-byte aligned */
+    const uint16_t *packed;  /* [n][16], 16-byte aligned                     */
+} gs_gaussians_bf16;
+
 /* Parameter gradients (FULL mode), device, same layouts as gs_gaussians,
  * summed over frames; overwritten (not accumulated). NULL member = skipped. */
 typedef struct {
@@ -198,6 +213,33 @@ const char *gs_last_error(void);
  *   cams: host [n_frames]; T_cw: device [n_frames][3][4].                    */
 gs_status gs_project(const gs_gaussians *g, int n_frames, const gs_camera *cams, const float *T_cw,
                      const gs_opts *opts, gs_projected *out, const int32_t *status, gs_stream stream);
+
+/* gs_project with BF16 storage (same outputs; FWD and POSE modes; FULL mode,
+ * which differentiates the stored parameters, returns GS_ERR_UNSUPPORTED). */
+gs_status gs_project_bf16(const gs_gaussians_bf16 *g, int n_frames, const gs_camera *cams, const float *T_cw,
+                          const gs_opts *opts, gs_projected *out, const int32_t *status, gs_stream stream);
+
+/* Spatial order for BF16 packing (no counterpart in the paper; it makes the
+ * chunks of GS_BF16_CHUNK Gaussians compact). perm[j] = index of the j-th
+ * Gaussian in the order of the 30-bit Morton code of its mean, quantised to
+ * 1024 steps per axis over the bounding box of all means:
+ *   q = min(1023, floor((m - lo) * (1024 / (hi - lo))))  in FP32 (round to
+ *   nearest; q = 0 on an axis with hi == lo), bits interleaved x, y, z from
+ *   the lowest up; ties in index order. Deterministic.
+ *   means: device [n][3]; perm: device uint32 [n]; ws: 256-byte aligned.    */
+size_t gs_spatial_order_workspace_size(int n);
+gs_status gs_spatial_order(const float *means, int n, uint32_t *perm, void *ws, size_t ws_bytes,
+                           const int32_t *status, gs_stream stream);
+
+/* Packs FP32 Gaussians (in the order perm, or as they are if perm is NULL) into
+ * the 16-bit layout above. Per chunk, from its means' bounding box [lo, hi]:
+ * step = (hi - lo) / 65535 and q = rint((m - lo) / step) clamped to [0, 65535]
+ * (FP32, round to nearest even; q = 0 where step = 0), so a stored mean is
+ * within step/2 (plus FP32 rounding) of the original. The other values are
+ * rounded to the nearest BF16 (ties to even).
+ *   anchors: device float [ceil(n/GS_BF16_CHUNK)][8]; packed: device [n][16].  */
+gs_status gs_pack_bf16(const gs_gaussians *src, const uint32_t *perm, float *anchors, uint16_t *packed,
+                       const int32_t *status, gs_stream stream);
 
 /* Sec. 3.1 pre-sort. Emits one (key, record) pair per tile overlapped by each
  * record's tile rect, key = (global tile id << 32) | float bits of z, sorts the

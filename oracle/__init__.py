@@ -278,6 +278,95 @@ def nu_estimate(scene, cams, Ts, obs_depths, tau=0.0, low_opacity=0.01, jclamp=1
     return dict(num=num, cnt=cnt, nu=nu, over=over, opacity_logit=logit, images=images)
 
 
+# ------------------------------------------------------- BF16 storage
+BF16_CHUNK = 256
+
+
+def bf16_bits(x):
+    """Round FP32 values to BF16 (nearest, ties to even), as uint16 bit patterns:
+    the upper 16 bits of the FP32 pattern after adding half an ulp of BF16
+    (0x7fff) plus the lowest kept bit, so that a tie rounds to the even neighbour."""
+    u = np.ascontiguousarray(np.asarray(x, np.float32)).view(np.uint32).astype(np.uint64)
+    keep = (u >> 16) & 1
+    return ((u + 0x7FFF + keep) >> 16).astype(np.uint16)
+
+
+def bf16_value(bits):
+    """BF16 bit patterns -> FP32 (exact: the bits become the upper half)."""
+    return (np.asarray(bits, np.uint32) << 16).view(np.float32)
+
+
+def _spread3(v):
+    out = np.zeros_like(v, dtype=np.uint64)
+    for b in range(10):
+        out |= ((v >> b) & 1) << (3 * b)
+    return out
+
+
+def spatial_order(means):
+    """Permutation of the Gaussians in 30-bit Morton order of their FP32 means:
+    per axis q = min(1023, floor((m - lo) * (1024 / (hi - lo)))) in FP32 (0 on a
+    flat axis), code bits x, y, z interleaved from the lowest up; stable (ties by
+    index)."""
+    m = np.asarray(means, np.float32).reshape(-1, 3)
+    if m.shape[0] == 0:
+        return np.zeros(0, np.int64)
+    lo, hi = m.min(axis=0), m.max(axis=0)
+    code = np.zeros(m.shape[0], np.uint64)
+    for k in range(3):
+        ext = np.float32(hi[k] - lo[k])
+        if ext > 0:
+            sc = np.float32(np.float32(1024.0) / ext)
+            q = np.float32(m[:, k] - lo[k]) * sc
+            q = np.minimum(np.floor(q), 1023).astype(np.uint64)
+        else:
+            q = np.zeros(m.shape[0], np.uint64)
+        code |= _spread3(q) << k
+    return np.argsort(code, kind="stable")
+
+
+def pack_bf16(scene, perm=None):
+    """16-bit storage of FP32 Gaussians in the order perm. Per chunk of 256, from
+    the bounding box [lo, hi] of its means: step = (hi - lo) / 65535 and
+    q = rint((m - lo) / step) clamped to [0, 65535] in FP32 (q = 0 where step = 0);
+    the other values rounded to BF16. Returns anchors float32 [C, 8] = (lo xyz,
+    step xyz, 0, 0) and packed uint16 [N, 16] = (q xyz, log-scale, quaternion,
+    opacity logit, RGB, nu, 0)."""
+    n = scene.n
+    order = np.arange(n) if perm is None else np.asarray(perm)
+    f32 = {k: np.asarray(getattr(scene, k), np.float32)[order] for k in
+           ("means", "log_scales", "quats", "opacity_logit", "colors", "nu")}
+    C = (n + BF16_CHUNK - 1) // BF16_CHUNK
+    anchors = np.zeros((C, 8), np.float32)
+    q = np.zeros((n, 3), np.uint16)
+    for c in range(C):
+        sl = slice(c * BF16_CHUNK, (c + 1) * BF16_CHUNK)
+        m = f32["means"][sl]
+        lo, hi = m.min(axis=0), m.max(axis=0)
+        step = (hi - lo) / np.float32(65535.0)
+        anchors[c, 0:3], anchors[c, 3:6] = lo, step
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t = (m - lo) / step
+        t = np.where(step > 0, np.rint(t), 0.0)
+        q[sl] = np.clip(t, 0, 65535).astype(np.uint16)
+    vals = np.concatenate([f32["log_scales"], f32["quats"], f32["opacity_logit"][:, None], f32["colors"],
+                           f32["nu"][:, None], np.zeros((n, 1), np.float32)], axis=1)
+    return anchors, np.concatenate([q, bf16_bits(vals)], axis=1)
+
+
+def unpack_bf16(anchors, packed):
+    """The FP32 Gaussians that 16-bit storage represents (mean = lo + step * q,
+    FP32 product then FP32 sum), as a synth.Scene of FP64 arrays."""
+    import synth
+    packed = np.asarray(packed, np.uint16)
+    n = packed.shape[0]
+    box = np.asarray(anchors, np.float32)[np.arange(n) // BF16_CHUNK]
+    means = box[:, 0:3] + box[:, 3:6] * packed[:, 0:3].astype(np.float32)
+    v = bf16_value(packed[:, 3:])
+    return synth.Scene(*(np.asarray(x, np.float64) for x in
+                         (means, v[:, 0:3], v[:, 3:7], v[:, 7], v[:, 8:11], v[:, 11])))
+
+
 def bin_tiles(rect, depth_f32, n_per_frame, tile, cams, capacity=None):
     """Brute-force tile lists: (keys u64 [P], values u32 [P], ranges u32 [n_tiles,2])."""
     rect = np.ascontiguousarray(rect, dtype=np.int32)

@@ -12,7 +12,7 @@ not, so the build step never depends on an earlier build.
 import importlib
 
 _EXPORTS = {
-    "GsError": "_abi", "Gaussians": "_abi",
+    "GsError": "_abi", "Gaussians": "_abi", "PackedGaussians": "_abi", "pack_bf16": "_abi",
     "GaussianRasterize": "raster", "Rasterizer": "raster", "Tracker": "raster", "rasterize": "raster",
 }
 

@@ -77,6 +77,13 @@ class gs_loss(C.Structure):
                 ("unc_tau", C.c_float), ("target_color", _vp), ("target_depth", _vp), ("w_align", C.c_float)]
 
 
+class gs_gaussians_bf16(C.Structure):
+    _fields_ = [("n", C.c_int), ("anchors", _vp), ("packed", _vp)]
+
+
+GS_BF16_CHUNK = 256
+
+
 class gs_grads(C.Structure):
     _fields_ = [("means", _vp), ("log_scales", _vp), ("quats", _vp), ("opacity_logit", _vp),
                 ("colors", _vp), ("nu", _vp)]
@@ -89,9 +96,10 @@ class gs_adam(C.Structure):
 
 EXPORTS = ("gs_abi_version", "gs_last_error", "gs_project", "gs_bin_tiles_workspace_size", "gs_bin_tiles",
            "gs_bin_tiles_noalloc", "gs_render_fwd", "gs_pose_partials_per_frame", "gs_render_bwd_workspace_size",
-           "gs_render_bwd", "gs_nu_accumulate", "gs_nu_finalize", "gs_pose_grad_reduce", "gs_pose_adam_step")
+           "gs_render_bwd", "gs_project_bf16", "gs_spatial_order_workspace_size", "gs_spatial_order",
+           "gs_pack_bf16", "gs_nu_accumulate", "gs_nu_finalize", "gs_pose_grad_reduce", "gs_pose_adam_step")
 GS_NOALLOC_MAX_PAIRS = 1 << 19
-ABI_VERSION = 2  # GS_ABI_VERSION of the gs.h these structures mirror
+ABI_VERSION = 3  # GS_ABI_VERSION of the gs.h these structures mirror
 
 
 def _load():
@@ -104,6 +112,12 @@ def _load():
     lib.gs_last_error.restype = C.c_char_p
     lib.gs_project.argtypes = [C.POINTER(gs_gaussians), C.c_int, C.POINTER(gs_camera), _vp,
                                C.POINTER(gs_opts), C.POINTER(gs_projected), _vp, _vp]
+    lib.gs_project_bf16.argtypes = [C.POINTER(gs_gaussians_bf16), C.c_int, C.POINTER(gs_camera), _vp,
+                                    C.POINTER(gs_opts), C.POINTER(gs_projected), _vp, _vp]
+    lib.gs_spatial_order_workspace_size.argtypes = [C.c_int]
+    lib.gs_spatial_order_workspace_size.restype = C.c_size_t
+    lib.gs_spatial_order.argtypes = [_vp, C.c_int, _vp, _vp, C.c_size_t, _vp, _vp]
+    lib.gs_pack_bf16.argtypes = [C.POINTER(gs_gaussians), _vp, _vp, _vp, _vp, _vp]
     lib.gs_bin_tiles_workspace_size.argtypes = [C.c_int, C.c_int]
     lib.gs_bin_tiles_workspace_size.restype = C.c_size_t
     lib.gs_bin_tiles.argtypes = [C.POINTER(gs_projected), C.c_int, C.POINTER(gs_camera), C.POINTER(gs_opts),
@@ -126,7 +140,7 @@ def _load():
     lib.gs_nu_finalize.argtypes = [C.c_int, _vp, _vp, _vp, C.c_float, C.c_float, _vp, _vp, _vp, _vp]
     lib.gs_pose_grad_reduce.argtypes = [_vp, C.c_int, C.c_int, _vp, _vp, _vp]
     lib.gs_pose_adam_step.argtypes = [_vp, _vp, _vp, C.c_int, C.POINTER(gs_adam), _vp, _vp]
-    for name in ("gs_project", "gs_bin_tiles", "gs_render_fwd", "gs_render_bwd", "gs_nu_accumulate",
+    for name in ("gs_project", "gs_project_bf16", "gs_spatial_order", "gs_pack_bf16", "gs_bin_tiles", "gs_render_fwd", "gs_render_bwd", "gs_nu_accumulate",
                  "gs_nu_finalize", "gs_pose_grad_reduce", "gs_pose_adam_step"):
         getattr(lib, name).restype = C.c_int
     return lib
@@ -207,6 +221,76 @@ def gs_project(g: Gaussians, cams, T_cw: torch.Tensor, opts: gs_opts, rec: torch
                         _ptr(pose_jac, torch.float32, "pose_jac", M * GS_JAC_FLOATS))
     _check(lib.gs_project(C.byref(g.struct()), F, cameras(cams), _ptr(T_cw, torch.float32, "T_cw", 12 * F),
                           C.byref(opts), C.byref(proj), _ptr(status, torch.int32, "status", 4), _stream(stream)))
+
+
+@dataclass
+class PackedGaussians:
+    """16-bit storage (gs_gaussians_bf16): FP32 chunk boxes [ceil(N/256), 8] (lo
+    xyz, step xyz, 0, 0), packed records [N, 16] (int16 tensor holding the bits:
+    uint16 fixed-point mean, BF16 attributes) and the permutation (int32 [N])
+    from packed order to the FP32 source order, or None."""
+    anchors: torch.Tensor
+    packed: torch.Tensor
+    perm: Optional[torch.Tensor] = None
+
+    @property
+    def n(self) -> int:
+        return int(self.packed.shape[0])
+
+    def struct(self) -> gs_gaussians_bf16:
+        n = self.n
+        return gs_gaussians_bf16(n, _ptr(self.anchors, torch.float32, "anchors",
+                                         8 * ((n + GS_BF16_CHUNK - 1) // GS_BF16_CHUNK)),
+                                 _ptr(self.packed, torch.int16, "packed", 16 * n))
+
+
+def gs_project_bf16(g: PackedGaussians, cams, T_cw: torch.Tensor, opts: gs_opts, rec: torch.Tensor,
+                    tiles_touched: torch.Tensor, pose_jac: Optional[torch.Tensor], status: torch.Tensor,
+                    stream=None) -> None:
+    F = len(cams)
+    M = F * g.n
+    proj = gs_projected(g.n, F, _ptr(rec, torch.float32, "rec", M * GS_REC_FLOATS),
+                        _ptr(tiles_touched, torch.int32, "tiles_touched", M),
+                        _ptr(pose_jac, torch.float32, "pose_jac", M * GS_JAC_FLOATS))
+    _check(lib.gs_project_bf16(C.byref(g.struct()), F, cameras(cams), _ptr(T_cw, torch.float32, "T_cw", 12 * F),
+                               C.byref(opts), C.byref(proj), _ptr(status, torch.int32, "status", 4),
+                               _stream(stream)))
+
+
+def gs_spatial_order_workspace_size(n: int) -> int:
+    return int(lib.gs_spatial_order_workspace_size(n))
+
+
+def gs_spatial_order(means: torch.Tensor, perm: torch.Tensor, ws: torch.Tensor, status: torch.Tensor,
+                     stream=None) -> None:
+    n = means.shape[0]
+    _check(lib.gs_spatial_order(_ptr(means, torch.float32, "means", 3 * n), n, _ptr(perm, torch.int32, "perm", n),
+                                _ptr(ws, torch.uint8, "ws"), ws.numel(), _ptr(status, torch.int32, "status", 4),
+                                _stream(stream)))
+
+
+def gs_pack_bf16(src: Gaussians, perm: Optional[torch.Tensor], anchors: torch.Tensor, packed: torch.Tensor,
+                 status: torch.Tensor, stream=None) -> None:
+    n = src.n
+    _check(lib.gs_pack_bf16(C.byref(src.struct()), _ptr(perm, torch.int32, "perm", n),
+                            _ptr(anchors, torch.float32, "anchors", 8 * ((n + GS_BF16_CHUNK - 1) // GS_BF16_CHUNK)),
+                            _ptr(packed, torch.int16, "packed", 16 * n), _ptr(status, torch.int32, "status", 4),
+                            _stream(stream)))
+
+
+def pack_bf16(src: Gaussians, spatial: bool = True) -> PackedGaussians:
+    """Spatially orders (optional) and packs FP32 Gaussians into 16-bit storage."""
+    n, dev = src.n, src.means.device
+    status = torch.zeros(4, dtype=torch.int32, device=dev)
+    perm = None
+    if spatial:
+        perm = torch.empty(n, dtype=torch.int32, device=dev)
+        ws = torch.empty(max(1, gs_spatial_order_workspace_size(n)), dtype=torch.uint8, device=dev)
+        gs_spatial_order(src.means, perm, ws, status)
+    anchors = torch.empty((n + GS_BF16_CHUNK - 1) // GS_BF16_CHUNK, 8, dtype=torch.float32, device=dev)
+    packed = torch.empty(n, 16, dtype=torch.int16, device=dev)
+    gs_pack_bf16(src, perm, anchors, packed, status)
+    return PackedGaussians(anchors, packed, perm)
 
 
 def gs_bin_tiles_workspace_size(n_records: int, capacity: int) -> int:

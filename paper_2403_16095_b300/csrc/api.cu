@@ -139,6 +139,49 @@ gs_status gs_project(const gs_gaussians *g, int n_frames, const gs_camera *cams,
                        "gs_project");
 }
 
+gs_status gs_project_bf16(const gs_gaussians_bf16 *g, int n_frames, const gs_camera *cams, const float *T_cw,
+                          const gs_opts *opts, gs_projected *out, const int32_t *status, gs_stream stream) {
+    if (!g) return fail(GS_ERR_INVALID_ARG, "gaussians is NULL");
+    if (g->n < 0) return fail(GS_ERR_INVALID_ARG, "n < 0");
+    if (g->n > 0 && (!g->anchors || !g->packed)) return fail(GS_ERR_INVALID_ARG, "anchors/packed NULL");
+    if (!aligned(g->anchors, 16) || !aligned(g->packed, 16)) return fail(GS_ERR_INVALID_ARG, "anchors/packed must be 16-byte aligned");
+    GS_TRY(check_opts(opts));
+    if (opts->mode == GS_MODE_FULL) return fail(GS_ERR_UNSUPPORTED, "FULL mode needs FP32 parameters (gs_project)");
+    gs::FrameTable ft;
+    GS_TRY(make_frames(n_frames, cams, opts->tile, ft));
+    GS_TRY(check_proj(out, n_frames));
+    if (out->n_gaussians != g->n) return fail(GS_ERR_INVALID_ARG, "projected.n_gaussians != gaussians.n");
+    if (!T_cw || !status) return fail(GS_ERR_INVALID_ARG, "T_cw/status NULL");
+    if (opts->mode == GS_MODE_POSE && (!out->pose_jac || !aligned(out->pose_jac, 16)))
+        return fail(GS_ERR_INVALID_ARG, "POSE mode needs a 16-byte aligned pose_jac");
+    return cuda_status(gs::launch_project_bf16(g->anchors, g->packed, g->n, ft, T_cw, opts->jclamp, opts->nu_cull,
+                                               opts->mode, out->rec, out->tiles_touched, out->pose_jac, status, stream),
+                       "gs_project_bf16");
+}
+
+size_t gs_spatial_order_workspace_size(int n) { return n < 0 ? 0 : gs::spatial_order_workspace_bytes(n); }
+
+gs_status gs_spatial_order(const float *means, int n, uint32_t *perm, void *ws, size_t ws_bytes,
+                           const int32_t *status, gs_stream stream) {
+    if (n < 0) return fail(GS_ERR_INVALID_ARG, "n < 0");
+    if (!status) return fail(GS_ERR_INVALID_ARG, "status NULL");
+    if (n > 0 && (!means || !perm)) return fail(GS_ERR_INVALID_ARG, "means/perm NULL");
+    const size_t need = gs::spatial_order_workspace_bytes(n);
+    if (n > 0 && (!ws || ws_bytes < need)) return fail(GS_ERR_INVALID_ARG, "workspace %zu bytes < %zu needed", ws_bytes, need);
+    if (!aligned(ws, 256)) return fail(GS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    return cuda_status(gs::launch_spatial_order(means, n, perm, ws, status, stream), "gs_spatial_order");
+}
+
+gs_status gs_pack_bf16(const gs_gaussians *src, const uint32_t *perm, float *anchors, uint16_t *packed,
+                       const int32_t *status, gs_stream stream) {
+    GS_TRY(check_gauss(src));
+    if (!status) return fail(GS_ERR_INVALID_ARG, "status NULL");
+    if (src->n > 0 && (!anchors || !packed)) return fail(GS_ERR_INVALID_ARG, "anchors/packed NULL");
+    if (!aligned(anchors, 16) || !aligned(packed, 16)) return fail(GS_ERR_INVALID_ARG, "anchors/packed must be 16-byte aligned");
+    return cuda_status(gs::launch_pack_bf16(gauss_ptrs(src), src->n, perm, anchors, packed, status, stream),
+                       "gs_pack_bf16");
+}
+
 size_t gs_bin_tiles_workspace_size(int n_records, int capacity) {
     if (n_records < 0 || capacity < 1) return 0;
     return gs::bin_workspace_bytes(n_records, capacity);

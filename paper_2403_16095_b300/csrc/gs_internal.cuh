@@ -70,6 +70,9 @@ void set_error_message(const char *msg);
 cudaError_t launch_project(const GaussPtrs &g, int n, const FrameTable &ft, const float *T_cw, float jclamp,
                            float nu_cull, int mode, float *rec, int *touched, float *jac, const int32_t *status,
                            cudaStream_t s);
+cudaError_t launch_project_bf16(const float *anchors, const uint16_t *packed, int n, const FrameTable &ft,
+                                const float *T_cw, float jclamp, float nu_cull, int mode, float *rec, int *touched,
+                                float *jac, const int32_t *status, cudaStream_t s);
 cudaError_t launch_project_bwd(const GaussPtrs &g, int n, const FrameTable &ft, const float *T_cw, float jclamp,
                                const float *rec, const float *grad2d, gs_grads grads, float *pose_partials,
                                int per_frame, double *pose_grad, unsigned *counters, const int32_t *status,
@@ -88,6 +91,12 @@ cudaError_t launch_render_bwd(int mode, const float *rec, const float *jac, cons
                               const ImagePtrs &fwd, const LossParams &lp, float *grad2d, float *pose_partials,
                               int per_frame, double *pose_grad, unsigned *counters, const int32_t *status,
                               cudaStream_t s);
+// pack.cu
+size_t spatial_order_workspace_bytes(int n);
+cudaError_t launch_spatial_order(const float *means, int n, uint32_t *perm, void *ws, const int32_t *status,
+                                 cudaStream_t s);
+cudaError_t launch_pack_bf16(const GaussPtrs &g, int n, const uint32_t *perm, float *anchors, uint16_t *packed,
+                             const int32_t *status, cudaStream_t s);
 // nu.cu
 cudaError_t launch_nu_accumulate(const float *rec, const uint32_t *values, const FrameTable &ft, int n_gaussians,
                                  const float *obs_depth, const int32_t *dom_pos, const float *dom_weight,

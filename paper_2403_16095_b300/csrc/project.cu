@@ -17,6 +17,70 @@ namespace {
 
 constexpr int kProjThreads = 256;
 
+// Parameter sources. Each has a per-Gaussian handle (`Rec`) and accessors that
+// the projection calls in the same order for both storages.
+//   F32Src   the FP32 arrays of gs_gaussians; the handle is the index and every
+//            accessor loads lazily, so a culled Gaussian costs only its mean,
+//            quaternion (and nu when culling on it).
+//   BF16Src  the packed 32-byte record of gs_gaussians_bf16, fetched whole (one
+//            sector), plus its chunk's FP32 box: mean = lo + step * q (FP32
+//            multiply, then add, each rounded); BF16 -> FP32 is exact (the bits
+//            shifted up).
+struct F32Src {
+    GaussPtrs g;
+    struct Rec {
+        int i;
+    };
+    __device__ __forceinline__ Rec fetch(int i) const { return Rec{i}; }
+    __device__ __forceinline__ float4 quat(const Rec &r) const {
+        return __ldg(reinterpret_cast<const float4 *>(g.quats) + r.i);
+    }
+    __device__ __forceinline__ float mean(const Rec &r, int k) const { return __ldg(g.means + 3 * r.i + k); }
+    __device__ __forceinline__ float log_scale(const Rec &r, int k) const { return __ldg(g.log_scales + 3 * r.i + k); }
+    __device__ __forceinline__ float opacity_logit(const Rec &r) const { return __ldg(g.opacity_logit + r.i); }
+    __device__ __forceinline__ float color(const Rec &r, int k) const { return __ldg(g.colors + 3 * r.i + k); }
+    __device__ __forceinline__ float nu(const Rec &r) const { return __ldg(g.nu + r.i); }
+};
+
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+struct BF16Src {
+    const float4 *anchors;  // [ceil(n / GS_BF16_CHUNK)][2]: (lo xyz, step x), (step y, z, 0, 0)
+    const uint4 *packed;    // [n][2]; h[16] = q xyz (uint16), then BF16 log-scale xyz, quat
+                            // wxyz, logit, rgb, nu, 0; word k of the record holds h[2k]
+                            // (low half) and h[2k+1] (high half)
+    struct Rec {
+        float4 box0, box1;
+        uint4 a, b;
+    };
+    __device__ __forceinline__ Rec fetch(int i) const {
+        Rec r;
+        r.box0 = __ldg(anchors + 2 * (i / GS_BF16_CHUNK));
+        r.box1 = __ldg(anchors + 2 * (i / GS_BF16_CHUNK) + 1);
+        r.a = __ldg(packed + 2 * (size_t)i);
+        r.b = __ldg(packed + 2 * (size_t)i + 1);
+        return r;
+    }
+    __device__ __forceinline__ float4 quat(const Rec &r) const {
+        return make_float4(bf_lo(r.a.w), bf_hi(r.a.w), bf_lo(r.b.x), bf_hi(r.b.x));
+    }
+    __device__ __forceinline__ float mean(const Rec &r, int k) const {
+        const uint32_t q = k == 0 ? (r.a.x & 0xffffu) : (k == 1 ? (r.a.x >> 16) : (r.a.y & 0xffffu));
+        const float lo = k == 0 ? r.box0.x : (k == 1 ? r.box0.y : r.box0.z);
+        const float st = k == 0 ? r.box0.w : (k == 1 ? r.box1.x : r.box1.y);
+        return __fadd_rn(lo, __fmul_rn(st, (float)q));
+    }
+    __device__ __forceinline__ float log_scale(const Rec &r, int k) const {
+        return k == 0 ? bf_hi(r.a.y) : (k == 1 ? bf_lo(r.a.z) : bf_hi(r.a.z));
+    }
+    __device__ __forceinline__ float opacity_logit(const Rec &r) const { return bf_lo(r.b.y); }
+    __device__ __forceinline__ float color(const Rec &r, int k) const {
+        return k == 0 ? bf_hi(r.b.y) : (k == 1 ? bf_lo(r.b.z) : bf_hi(r.b.z));
+    }
+    __device__ __forceinline__ float nu(const Rec &r) const { return bf_lo(r.b.w); }
+};
+
 // Camera-space quantities of one Gaussian that both directions need.
 struct Geo {
     float R[3][3];   // rotation of the normalised quaternion
@@ -47,16 +111,17 @@ __device__ __forceinline__ void load_pose(const float *__restrict__ T, float W[3
 
 // Returns false if the Gaussian is culled before the 2D covariance step
 // (zero quaternion, behind the near plane, nu cull, non-positive determinant).
-__device__ __forceinline__ bool geometry(const GaussPtrs &g, int i, const FrameDesc &fd, const float W[3][3],
-                                         const float t[3], float jclamp, float nu_cull, Geo &o) {
-    const float4 q = __ldg(reinterpret_cast<const float4 *>(g.quats) + i);
+template <class Src>
+__device__ __forceinline__ bool geometry(const Src &src, const typename Src::Rec &G, const FrameDesc &fd,
+                                         const float W[3][3], const float t[3], float jclamp, float nu_cull, Geo &o) {
+    const float4 q = src.quat(G);
     const float n2 = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
-    const float mx = __ldg(g.means + 3 * i), my = __ldg(g.means + 3 * i + 1), mz = __ldg(g.means + 3 * i + 2);
+    const float mx = src.mean(G, 0), my = src.mean(G, 1), mz = src.mean(G, 2);
 #pragma unroll
     for (int r = 0; r < 3; ++r) o.p[r] = fmaf(W[r][0], mx, fmaf(W[r][1], my, fmaf(W[r][2], mz, t[r])));
     if (!(n2 > 0.f)) return false;
     if (!(o.p[2] > fd.znear)) return false;
-    if (nu_cull > 0.f && __ldg(g.nu + i) > nu_cull) return false;
+    if (nu_cull > 0.f && src.nu(G) > nu_cull) return false;
 
     o.qinv = rsqrtf(n2);
     const float w = q.x * o.qinv, x = q.y * o.qinv, y = q.z * o.qinv, z = q.w * o.qinv;
@@ -65,7 +130,7 @@ __device__ __forceinline__ bool geometry(const GaussPtrs &g, int i, const FrameD
     o.R[1][0] = 2.f * (x * y + w * z); o.R[1][1] = 1.f - 2.f * (x * x + z * z); o.R[1][2] = 2.f * (y * z - w * x);
     o.R[2][0] = 2.f * (x * z - w * y); o.R[2][1] = 2.f * (y * z + w * x); o.R[2][2] = 1.f - 2.f * (x * x + y * y);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) o.s[k] = expf(__ldg(g.log_scales + 3 * i + k));
+    for (int k = 0; k < 3; ++k) o.s[k] = expf(src.log_scale(G, k));
     // WM = W R diag(s); V = WM WM^T is symmetric by construction
 #pragma unroll
     for (int r = 0; r < 3; ++r)
@@ -122,9 +187,9 @@ __device__ __forceinline__ void write_culled(float *rec, int *touched, size_t r)
     touched[r] = 0;
 }
 
-template <bool JAC>
+template <bool JAC, class Src>
 __global__ void __launch_bounds__(kProjThreads)
-    k_project(GaussPtrs g, int n, FrameTable ft, const float *__restrict__ T_cw, float jclamp, float nu_cull,
+    k_project(Src src, int n, FrameTable ft, const float *__restrict__ T_cw, float jclamp, float nu_cull,
               float *__restrict__ rec, int *__restrict__ touched, float *__restrict__ jac,
               const int32_t *__restrict__ status) {
     if (status[0] != 0) return;
@@ -136,7 +201,8 @@ __global__ void __launch_bounds__(kProjThreads)
     float W[3][3], t[3];
     load_pose(T_cw + 12 * f, W, t);
     Geo o;
-    if (!geometry(g, i, fd, W, t, jclamp, nu_cull, o)) { write_culled(rec, touched, r); return; }
+    const typename Src::Rec G = src.fetch(i);
+    if (!geometry(src, G, fd, W, t, jclamp, nu_cull, o)) { write_culled(rec, touched, r); return; }
 
     const float mx = fmaf(fd.fx, o.u, fd.cx), my = fmaf(fd.fy, o.v, fd.cy);
     const float half = 0.5f * (o.a - o.c);
@@ -149,11 +215,11 @@ __global__ void __launch_bounds__(kProjThreads)
     const int ts = ft.tile;
     touched[r] = (ix1 / ts - ix0 / ts + 1) * (iy1 / ts - iy0 / ts + 1);
 
-    const float opac = 1.f / (1.f + expf(-__ldg(g.opacity_logit + i)));
+    const float opac = 1.f / (1.f + expf(-src.opacity_logit(G)));
     float4 *out = reinterpret_cast<float4 *>(rec + r * kRecFloats);
     out[0] = make_float4(mx, my, o.A, o.B);
-    out[1] = make_float4(o.C, opac, o.p[2], __ldg(g.nu + i));
-    out[2] = make_float4(__ldg(g.colors + 3 * i), __ldg(g.colors + 3 * i + 1), __ldg(g.colors + 3 * i + 2), rad);
+    out[1] = make_float4(o.C, opac, o.p[2], src.nu(G));
+    out[2] = make_float4(src.color(G, 0), src.color(G, 1), src.color(G, 2), rad);
     reinterpret_cast<int4 *>(out)[3] = make_int4(ix0, iy0, ix1, iy1);
 
     if (JAC) {
@@ -255,7 +321,8 @@ __global__ void __launch_bounds__(kProjThreads)
             float W[3][3], t[3];
             load_pose(T_cw + 12 * f, W, t);
             Geo o;
-            geometry(g, i, fd, W, t, jclamp, -1.f, o);  // same arithmetic as the forward
+            const F32Src src{g};
+            geometry(src, src.fetch(i), fd, W, t, jclamp, -1.f, o);  // same arithmetic as the forward
             const float *ga = grad2d + r * kGrad2d;
             const float gmx = ga[G_MX], gmy = ga[G_MY], gA = ga[G_CA], gB = ga[G_CB], gC = ga[G_CC];
             const float gz_dir = ga[G_Z];
@@ -368,16 +435,29 @@ __global__ void __launch_bounds__(kProjThreads)
 
 }  // namespace
 
-cudaError_t launch_project(const GaussPtrs &g, int n, const FrameTable &ft, const float *T_cw, float jclamp,
-                           float nu_cull, int mode, float *rec, int *touched, float *jac, const int32_t *status,
-                           cudaStream_t s) {
+template <class Src>
+cudaError_t launch_src(const Src &src, int n, const FrameTable &ft, const float *T_cw, float jclamp, float nu_cull,
+                       int mode, float *rec, int *touched, float *jac, const int32_t *status, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     dim3 grid((n + kProjThreads - 1) / kProjThreads, ft.n);
     if (mode == GS_MODE_POSE)
-        k_project<true><<<grid, kProjThreads, 0, s>>>(g, n, ft, T_cw, jclamp, nu_cull, rec, touched, jac, status);
+        k_project<true><<<grid, kProjThreads, 0, s>>>(src, n, ft, T_cw, jclamp, nu_cull, rec, touched, jac, status);
     else
-        k_project<false><<<grid, kProjThreads, 0, s>>>(g, n, ft, T_cw, jclamp, nu_cull, rec, touched, jac, status);
+        k_project<false><<<grid, kProjThreads, 0, s>>>(src, n, ft, T_cw, jclamp, nu_cull, rec, touched, jac, status);
     return cudaGetLastError();
+}
+
+cudaError_t launch_project(const GaussPtrs &g, int n, const FrameTable &ft, const float *T_cw, float jclamp,
+                           float nu_cull, int mode, float *rec, int *touched, float *jac, const int32_t *status,
+                           cudaStream_t s) {
+    return launch_src(F32Src{g}, n, ft, T_cw, jclamp, nu_cull, mode, rec, touched, jac, status, s);
+}
+
+cudaError_t launch_project_bf16(const float *anchors, const uint16_t *packed, int n, const FrameTable &ft,
+                                const float *T_cw, float jclamp, float nu_cull, int mode, float *rec, int *touched,
+                                float *jac, const int32_t *status, cudaStream_t s) {
+    const BF16Src src{reinterpret_cast<const float4 *>(anchors), reinterpret_cast<const uint4 *>(packed)};
+    return launch_src(src, n, ft, T_cw, jclamp, nu_cull, mode, rec, touched, jac, status, s);
 }
 
 cudaError_t launch_project_bwd(const GaussPtrs &g, int n, const FrameTable &ft, const float *T_cw, float jclamp,

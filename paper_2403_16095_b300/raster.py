@@ -13,7 +13,7 @@ from typing import Optional, Sequence
 import torch
 
 from . import _abi as A
-from ._abi import Gaussians
+from ._abi import Gaussians, PackedGaussians
 
 CHANNELS = ("color", "depth", "alpha", "unc", "nu_map", "median", "T_final", "n_last", "n_contrib", "median_pos")
 
@@ -92,8 +92,12 @@ class Rasterizer:
         return int(s[0]), int(s[1])
 
     # --------------------------------------------------------------- stages
-    def project(self, g: Gaussians, T_cw: torch.Tensor, stream=None) -> None:
-        A.gs_project(g, self.cams, T_cw, self.opts, self.rec, self.touched, self.jac, self.status, stream)
+    def project(self, g, T_cw: torch.Tensor, stream=None) -> None:
+        """g: Gaussians (FP32) or PackedGaussians (BF16 storage; FWD/POSE modes)."""
+        if isinstance(g, PackedGaussians):
+            A.gs_project_bf16(g, self.cams, T_cw, self.opts, self.rec, self.touched, self.jac, self.status, stream)
+        else:
+            A.gs_project(g, self.cams, T_cw, self.opts, self.rec, self.touched, self.jac, self.status, stream)
 
     def bin(self, stream=None) -> None:
         A.gs_bin_tiles(self.N, self.cams, self.opts, self.rec, self.touched, self.values, self.keys, self.ranges,
@@ -251,7 +255,7 @@ class Tracker:
     step on the pose, all on the device. With ``graph=True`` one iteration is
     captured once in a CUDA graph and replayed."""
 
-    def __init__(self, g: Gaussians, cam, tile: int = 16, iters: int = 30, lam=(0.2, 1.0), unc_tau: float = 0.025,
+    def __init__(self, g, cam, tile: int = 16, iters: int = 30, lam=(0.2, 1.0), unc_tau: float = 0.025,
                  lr_rot: float = 0.0015, lr_trans: float = 0.00215, jclamp: float = 1.3, graph: bool = True,
                  capacity: Optional[int] = None, timing: bool = False):
         self.g = g
@@ -264,7 +268,7 @@ class Tracker:
         self.bwd_events = ([(torch.cuda.Event(enable_timing=True, external=True),
                              torch.cuda.Event(enable_timing=True, external=True)) for _ in range(iters)]
                            if timing else None)
-        dev = g.means.device
+        dev = (g.packed if isinstance(g, PackedGaussians) else g.means).device
         self.rast = Rasterizer([cam], g.n, tile=tile, mode=A.GS_MODE_POSE, capacity=capacity, jclamp=jclamp)
         H, W = int(cam.height), int(cam.width)
         self.target_color = torch.zeros(3 * H * W, dtype=torch.float32, device=dev)
