@@ -15,6 +15,16 @@ buffer outside the timed region; within a frame the iterations run back to back
 as tracking does.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload track|mapping|uneven|precision]
+
+The default workload is the tracking one above. The others print their own
+line (same keys): ``mapping`` = one mapping iteration over a window of 8
+640x480 keyframes of a 1M-Gaussian room (forward + FULL backward to every
+parameter and the 8 poses, fused colour/depth/alignment/variance loss);
+``uneven`` = 16 frames of mixed resolution (6x 320x240, 6x 640x480, 4x
+1200x680) over a 2M-Gaussian two-room scene in one batch, tile size chosen by
+the autotuner; ``precision`` = tracking at 1200x680 on 5M Gaussians held in
+16-bit storage.
 
 With --gpus N > 1 (under torchrun) every rank tracks its own frames
 (independent replicas, no data collective); timing uses a barrier and the max
@@ -43,6 +53,10 @@ WORKLOAD = "track-640x480-300k-room"
 # product for colour + depth (7), dL/dalpha and the running suffix sum (5),
 # gradients of mean2d, conic and depth (21), 6x6 pose-Jacobian contraction (72).
 BWD_FLOP_PER_CONTRIB = 122
+# FULL mode per blended entry: recompute (13), transmittance recovery (4),
+# channel dot product (9 with opacity, U and the median), dL/dalpha and suffix
+# sum (5), gradients of mean2d, conic, opacity, depth and colour (21).
+BWD_FULL_FLOP_PER_CONTRIB = 52
 FP32_LANES_PER_SM = 128
 N_SM = 148
 
@@ -54,6 +68,7 @@ def _args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
     p.add_argument("--tile", type=int, default=16)
+    p.add_argument("--workload", choices=("track", "mapping", "uneven", "precision"), default="track")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-iters", type=int, default=0, help="oracle iterations for the CPU baseline (0 = auto)")
@@ -333,10 +348,184 @@ def run_ours(a):
         torch.distributed.destroy_process_group()
 
 
+# ---------------------------------------------------------------- batches
+def run_batch(a):
+    """Mapping window (8 keyframes) or uneven batch (16 mixed frames): one step =
+    project + bin + forward + FULL backward (fused loss) over the whole batch."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2403_16095_b300 import Gaussians, Rasterizer, autotune_tile
+    from paper_2403_16095_b300 import _abi as A
+    from paper_2403_16095_b300.build import build
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build()
+    w = synth.workload(a.workload)
+    sc, cams, poses = w["scene"], w["cams"], w["poses"]
+    F = len(cams)
+    names = ("means", "log_scales", "quats", "opacity_logit", "colors", "nu")
+    g_true = Gaussians(*(torch.from_numpy(np.ascontiguousarray(getattr(sc, k), np.float32)).to(dev) for k in names))
+    Tt = torch.from_numpy(np.ascontiguousarray(np.asarray(poses, np.float32))).to(dev).reshape(-1)
+    # targets: the true scene at the true poses; the optimised field is perturbed
+    r0 = Rasterizer(cams, g_true.n, tile=16, mode=A.GS_MODE_FWD)
+    r0.render(g_true, Tt)
+    tcol, tdep = r0.img["color"].clone(), r0.img["depth"].clone()
+    del r0
+    rng = np.random.default_rng(1000 + (3 if a.workload == "mapping" else 4))
+    pert = {k: np.asarray(getattr(sc, k), np.float32).copy() for k in names}
+    pert["means"] += rng.normal(0, 0.01, pert["means"].shape).astype(np.float32)
+    pert["colors"] = np.clip(pert["colors"] + rng.normal(0, 0.05, pert["colors"].shape), 0, 1).astype(np.float32)
+    g = Gaussians(*(torch.from_numpy(pert[k]).to(dev) for k in names))
+    loss = dict(w_color=0.7, w_depth=0.25, w_unc=0.05, w_align=0.25, target_color=tcol, target_depth=tdep)
+    tile, tune = a.tile, None
+    if a.workload == "uneven":
+        tile, tune = autotune_tile(cams, g, Tt, tdep, mode=A.GS_MODE_FULL, loss=loss)
+    r = Rasterizer(cams, g.n, tile=tile, mode=A.GS_MODE_FULL)
+    r.render(g, Tt, tdep)
+    r.set_capacity(int(r.read_status()[1] * 1.25) + 4096)
+    grads = {k: torch.empty_like(getattr(g, k)) for k in names}
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stages = ("project", "bin", "forward", "backward")
+
+    def step():
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev[0].record()
+        r.project(g, Tt)
+        ev[1].record()
+        r.bin()
+        ev[2].record()
+        r.forward(tdep)
+        ev[3].record()
+        r.backward(obs_depth=tdep, loss=loss, g=g, T_cw=Tt, grads=grads)
+        ev[4].record()
+        return ev
+
+    for _ in range(a.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    assert r.read_status()[0] == 0
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    clocks.start()
+    per = {s_: [] for s_ in stages}
+    tot = []
+    contrib = []
+    for _ in range(a.steps):
+        flush.zero_()
+        ev = step()
+        ev[4].synchronize()
+        for i, s_ in enumerate(stages):
+            per[s_].append(ev[i].elapsed_time(ev[i + 1]))
+        tot.append(ev[0].elapsed_time(ev[4]))
+        contrib.append(int(r.img["n_contrib"].sum()))
+    clk = clocks.stop()
+    if r.read_status()[0] != 0:
+        raise RuntimeError("device status set during the timed region")
+    total_ms = sum(tot)
+    value = F * a.steps / (total_ms / 1e3)
+    peaks = _peaks()
+    mhz = peaks.get("sm_max_mhz", 2032.0)
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    bwd_ms = statistics.mean(per["backward"])
+    E = statistics.mean(contrib)
+    achieved = E * BWD_FULL_FLOP_PER_CONTRIB / (bwd_ms * 1e-3) / 1e12
+    n_pix = sum(int(c.width) * int(c.height) for c in cams)
+    metric = {"mapping": "mapping keyframe-iterations/sec (fwd+FULL bwd), 8x640x480 window, 1M Gaussians",
+              "uneven": "frames/sec (fwd+FULL bwd), 16 mixed-resolution frames in one batch, 2M Gaussians"}[a.workload]
+    line = {"metric": metric, "value": value, "unit": "frames/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{a.workload}-{F}frames-{g.n // 1000}k", "frames": F, "pixels": n_pix,
+                       "gaussians": int(g.n), "tile": tile, "autotune_ms": tune,
+                       "l2": "flushed between steps (512 MB write, untimed)",
+                       "stage_ms": {s_: statistics.mean(v) for s_, v in per.items()},
+                       "pairs": int(r.read_status()[1]), "contributions": E},
+            "roofline": {"kernel": f"k_render_bwd<{tile},FULL> + k_project_bwd", "bound": "alu",
+                         "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                         "traffic": None, "flop_per_contribution": BWD_FULL_FLOP_PER_CONTRIB,
+                         "avg_launch_ms": bwd_ms},
+            "cpu_baseline": None, "gpu_launches": 8 * a.steps, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
+def run_precision(a):
+    """Tracking at 1200x680 on 5M Gaussians in 16-bit storage (BF16 attributes,
+    per-chunk fixed-point means), 30 iterations per frame in a CUDA graph."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2403_16095_b300 import Gaussians, Rasterizer, Tracker, pack_bf16
+    from paper_2403_16095_b300 import _abi as A
+    from paper_2403_16095_b300.build import build
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build()
+    w = synth.workload("precision")
+    sc, cam, poses = w["scene"], w["cams"][0], w["poses"]
+    names = ("means", "log_scales", "quats", "opacity_logit", "colors", "nu")
+    g32 = Gaussians(*(torch.from_numpy(np.ascontiguousarray(getattr(sc, k), np.float32)).to(dev) for k in names))
+    pk = pack_bf16(g32, spatial=True)
+    frames = list(range(a.warmup + a.steps))
+    r0 = Rasterizer([cam], g32.n, tile=a.tile, mode=A.GS_MODE_FWD)
+    tcol, tdep = {}, {}
+    for f in frames:
+        r0.render(g32, torch.from_numpy(np.asarray(poses[f % len(poses)], np.float32)).to(dev).reshape(-1))
+        tcol[f], tdep[f] = r0.img["color"].clone(), r0.img["depth"].clone()
+    del r0, g32
+    starts = {f: torch.from_numpy(synth.jitter_pose(poses[f % len(poses)], seed=1005 * 100 + f)).to(dev)
+              for f in frames}
+    tr = Tracker(pk, cam, tile=a.tile, iters=ITERS, graph=True, timing=True)
+    tr.prepare(tcol[0], tdep[0], starts[0], headroom=1.6)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    for f in frames[:a.warmup]:
+        flush.zero_()
+        tr.set_frame(tcol[f], tdep[f], starts[f])
+        tr.run()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    tot, bwd = [], []
+    for f in frames[a.warmup:]:
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        tr.set_frame(tcol[f], tdep[f], starts[f])
+        tr.run()
+        e1.record()
+        e1.synchronize()
+        tot.append(e0.elapsed_time(e1))
+        bwd.extend(tr.backward_ms())
+    clk = clocks.stop()
+    if tr.rast.read_status()[0] != 0:
+        raise RuntimeError("device status set during the timed region")
+    total_ms = sum(tot)
+    line = {"metric": "tracking iters/sec (fwd+pose-bwd) at 1200x680/5M Gaussians, 16-bit storage",
+            "value": ITERS * a.steps / (total_ms / 1e3), "unit": "iters/s", "n_gpus": 1, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16 storage, f32 compute", "data": "synthetic",
+            "config": {"workload": "precision-1200x680-5M-room", "gaussians": int(pk.n), "tile": a.tile,
+                       "iters_per_frame": ITERS, "l2": "flushed between steps (512 MB write, untimed)",
+                       "bwd_ms_avg": statistics.mean(bwd), "ms_per_iteration": total_ms / (a.steps * ITERS),
+                       "pairs_per_iteration": int(tr.rast.read_status()[1])},
+            "cpu_baseline": None, "gpu_launches": tr.kernel_launches_per_iteration() * ITERS * a.steps,
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload in ("mapping", "uneven"):
+        run_batch(a)
+    elif a.workload == "precision":
+        run_precision(a)
     else:
         run_ours(a)
 

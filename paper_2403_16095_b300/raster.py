@@ -181,6 +181,55 @@ class Rasterizer:
         return self.values[:P], self.ranges.view(-1, 2)
 
 
+# ===================================================================== autotuner
+_TILE_CACHE: dict = {}
+
+
+def autotune_tile(cams: Sequence, g, T_cw: torch.Tensor, obs_depth=None, mode: int = A.GS_MODE_FULL,
+                  loss: Optional[dict] = None, candidates=(8, 16, 32), reps: int = 3, jclamp: float = 1.3,
+                  nu_cull: float = 0.0):
+    """Picks the tile size (8, 16 or 32 pixels) of a frame batch by timing one
+    whole iteration (project, bin, forward and, unless mode is FWD, the backward
+    with the fused ``loss``) with CUDA events, ``reps`` times per candidate after
+    one untimed run. The rendered images and gradients do not depend on the tile
+    size (same per-pixel lists and arithmetic), so the choice changes speed only.
+    Results are cached per (resolutions, N, mode). Returns (best tile, {tile: ms})."""
+    key = (tuple((int(c.width), int(c.height)) for c in cams), int(g.n), int(mode))
+    if key in _TILE_CACHE:
+        return _TILE_CACHE[key]
+    full = mode == A.GS_MODE_FULL
+    grads = {k: torch.empty_like(getattr(g, k)) for k in
+             ("means", "log_scales", "quats", "opacity_logit", "colors", "nu")} if full else None
+    times = {}
+    for t in candidates:
+        r = Rasterizer(cams, g.n, tile=t, mode=mode, jclamp=jclamp, nu_cull=nu_cull)
+        r.render(g, T_cw, obs_depth)
+        r.set_capacity(int(r.read_status()[1] * 1.25) + 4096)
+
+        def one():
+            r.project(g, T_cw)
+            r.bin()
+            r.forward(obs_depth)
+            if mode != A.GS_MODE_FWD:
+                r.backward(obs_depth=obs_depth, loss=loss, g=g if full else None, T_cw=T_cw if full else None,
+                           grads=grads)
+
+        one()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            one()
+        e1.record()
+        e1.synchronize()
+        if r.read_status()[0] != 0:
+            raise A.GsError(r.read_status()[0], f"autotune tile {t}")
+        times[t] = e0.elapsed_time(e1) / reps
+        del r
+    best = min(times, key=times.get)
+    _TILE_CACHE[key] = (best, times)
+    return best, times
+
+
 # ===================================================================== autograd
 class GaussianRasterize(torch.autograd.Function):
     """Renders colour, depth, opacity, U, nu map and median depth of F frames at

@@ -182,3 +182,41 @@ def test_gpu_gradient_matches_oracle_central_differences():
                 assert abs(gpu[idx] - fd) <= 2e-3 * scale, (field, i, c, gpu[idx], fd)
                 checked += 1
     assert checked >= 100
+
+
+def test_autotuned_uneven_batch_is_tile_invariant():
+    """Config-4 machinery on a small uneven batch (3 resolutions, 5 frames): the
+    autotuner's pick is the fastest of its own timings, and every tile size gives
+    bit-identical images and the same FULL-mode gradients (up to the order of the
+    FP32 atomic sums)."""
+    from paper_2403_16095_b300 import Rasterizer, autotune_tile
+    from paper_2403_16095_b300 import _abi as A
+    sc = synth.room_scene(40_000, seed=1006)
+    cams = [synth.Camera(96, 64, 90.0, 90.0, 48.0, 32.0), synth.Camera(160, 120, 150.0, 150.0, 80.0, 60.0),
+            synth.Camera(200, 113, 187.5, 187.5, 100.0, 56.5)] + [synth.Camera(160, 120, 150.0, 150.0, 80.0, 60.0)] * 2
+    Ts = np.stack([np.asarray(T, np.float32) for T in synth.circle_poses(5, seed=1006)])
+    g = to_gpu_gaussians(sc)
+    Tt = poses_gpu(Ts)
+    tg = [synth.random_targets(c, 1006 + 10 + f, depth_range=(0.5, 4.0)) for f, c in enumerate(cams)]
+    tc = torch.from_numpy(np.concatenate([t[0].reshape(-1) for t in tg])).cuda()
+    td = torch.from_numpy(np.concatenate([t[1].reshape(-1) for t in tg])).cuda()
+    loss = dict(w_color=0.7, w_depth=0.25, w_unc=0.05, w_align=0.25, target_color=tc, target_depth=td)
+    best, times = autotune_tile(cams, g, Tt, td, mode=A.GS_MODE_FULL, loss=loss)
+    assert best == min(times, key=times.get) and set(times) == {8, 16, 32}
+    imgs, grads = {}, {}
+    for t in (8, 16, 32):
+        r = Rasterizer(cams, sc.n, tile=t, mode=A.GS_MODE_FULL)
+        r.render(g, Tt, td)
+        gr = {k: torch.empty_like(getattr(g, k)) for k in PARAMS}
+        r.backward(obs_depth=td, loss=loss, g=g, T_cw=Tt, grads=gr)
+        torch.cuda.synchronize()
+        assert r.read_status()[0] == 0
+        imgs[t] = {k: v.clone() for k, v in r.img.items()}
+        grads[t] = {k: v.cpu().numpy() for k, v in gr.items()}
+        grads[t]["pose"] = r.pose_grad.cpu().numpy()
+    for t in (8, 32):
+        for k in ("color", "depth", "alpha", "unc", "median", "T_final", "n_contrib"):
+            assert torch.equal(imgs[t][k], imgs[16][k]), (t, k)
+        for k in list(PARAMS[:-1]) + ["pose"]:
+            a, b = grads[t][k], grads[16][k]
+            assert np.abs(a - b).max() <= 1e-5 * np.abs(b).max(), (t, k)
