@@ -59,7 +59,7 @@ extern "C" {
 #endif
 
 #define GS_MAX_FRAMES 64
-#define GS_ABI_VERSION 3
+#define GS_ABI_VERSION 4
 
 typedef struct CUstream_st *gs_stream; /* a cudaStream_t; NULL = legacy default stream */
 
@@ -126,6 +126,11 @@ typedef struct {
     uint64_t *keys;       /* [capacity] sorted keys (tile << 32 | depth bits), or NULL */
     uint32_t *ranges;     /* [n_tiles][2] [start, end) of each tile's pairs;
                              an empty tile has start == end                    */
+    uint32_t *order;      /* NULL, or [n_tiles]: every tile id once, longest
+                             list first (lengths bucketed by 4, order within a
+                             bucket unspecified). gs_bin_tiles writes it;
+                             gs_render_fwd / gs_render_bwd then start the
+                             heaviest tiles first. Results do not depend on it. */
 } gs_tiles;
 
 /* Rendered channels (Eq. 3-10), device, FP32 except n_last. A NULL member is not

@@ -59,7 +59,8 @@ class gs_projected(C.Structure):
 
 
 class gs_tiles(C.Structure):
-    _fields_ = [("capacity", C.c_int), ("n_tiles", C.c_int), ("values", _vp), ("keys", _vp), ("ranges", _vp)]
+    _fields_ = [("capacity", C.c_int), ("n_tiles", C.c_int), ("values", _vp), ("keys", _vp), ("ranges", _vp),
+                ("order", _vp)]
 
 
 class gs_image(C.Structure):
@@ -99,7 +100,7 @@ EXPORTS = ("gs_abi_version", "gs_last_error", "gs_project", "gs_bin_tiles_worksp
            "gs_render_bwd", "gs_project_bf16", "gs_spatial_order_workspace_size", "gs_spatial_order",
            "gs_pack_bf16", "gs_nu_accumulate", "gs_nu_finalize", "gs_pose_grad_reduce", "gs_pose_adam_step")
 GS_NOALLOC_MAX_PAIRS = 1 << 19
-ABI_VERSION = 3  # GS_ABI_VERSION of the gs.h these structures mirror
+ABI_VERSION = 4  # GS_ABI_VERSION of the gs.h these structures mirror
 
 
 def _load():
@@ -299,14 +300,15 @@ def gs_bin_tiles_workspace_size(n_records: int, capacity: int) -> int:
 
 def gs_bin_tiles(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tensor, tiles_touched: torch.Tensor,
                  values: torch.Tensor, keys: Optional[torch.Tensor], ranges: torch.Tensor, status: torch.Tensor,
-                 ws: torch.Tensor, stream=None) -> None:
+                 ws: torch.Tensor, stream=None, order: Optional[torch.Tensor] = None) -> None:
     F = len(cams)
     proj = gs_projected(n_gaussians, F, _ptr(rec, torch.float32, "rec"), _ptr(tiles_touched, torch.int32), None)
     cap = values.numel()
     if keys is not None and keys.numel() < cap:
         raise ValueError("keys must hold as many entries as values")
     tiles = gs_tiles(cap, ranges.numel() // 2, _ptr(values, torch.int32, "values"),
-                     _ptr(keys, torch.int64, "keys"), _ptr(ranges, torch.int32, "ranges"))
+                     _ptr(keys, torch.int64, "keys"), _ptr(ranges, torch.int32, "ranges"),
+                     _ptr(order, torch.int32, "order", ranges.numel() // 2))
     _check(lib.gs_bin_tiles(C.byref(proj), F, cameras(cams), C.byref(opts), C.byref(tiles),
                             _ptr(status, torch.int32, "status", 4), _ptr(ws, torch.uint8, "ws"), ws.numel(),
                             _stream(stream)))
@@ -314,7 +316,7 @@ def gs_bin_tiles(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tensor, tiles
 
 def gs_bin_tiles_noalloc(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tensor, tiles_touched: torch.Tensor,
                          values: torch.Tensor, keys: Optional[torch.Tensor], ranges: torch.Tensor,
-                         status: torch.Tensor, stream=None) -> None:
+                         status: torch.Tensor, stream=None, order: Optional[torch.Tensor] = None) -> None:
     """gs_bin_tiles without a caller workspace (static device scratch; see gs.h)."""
     F = len(cams)
     proj = gs_projected(n_gaussians, F, _ptr(rec, torch.float32, "rec"), _ptr(tiles_touched, torch.int32), None)
@@ -322,7 +324,8 @@ def gs_bin_tiles_noalloc(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tenso
     if keys is not None and keys.numel() < cap:
         raise ValueError("keys must hold as many entries as values")
     tiles = gs_tiles(cap, ranges.numel() // 2, _ptr(values, torch.int32, "values"),
-                     _ptr(keys, torch.int64, "keys"), _ptr(ranges, torch.int32, "ranges"))
+                     _ptr(keys, torch.int64, "keys"), _ptr(ranges, torch.int32, "ranges"),
+                     _ptr(order, torch.int32, "order", ranges.numel() // 2))
     _check(lib.gs_bin_tiles_noalloc(C.byref(proj), F, cameras(cams), C.byref(opts), C.byref(tiles),
                                     _ptr(status, torch.int32, "status", 4), _stream(stream)))
 
@@ -336,11 +339,11 @@ def _image(img: dict) -> gs_image:
 
 def gs_render_fwd(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tensor, values: torch.Tensor,
                   ranges: torch.Tensor, obs_depth: Optional[torch.Tensor], out: dict, status: torch.Tensor,
-                  stream=None) -> None:
+                  stream=None, order: Optional[torch.Tensor] = None) -> None:
     F = len(cams)
     proj = gs_projected(n_gaussians, F, _ptr(rec, torch.float32, "rec"), 1, None)  # touched unused
     tiles = gs_tiles(values.numel(), ranges.numel() // 2, _ptr(values, torch.int32), None,
-                     _ptr(ranges, torch.int32))
+                     _ptr(ranges, torch.int32), _ptr(order, torch.int32, "order", ranges.numel() // 2))
     _check(lib.gs_render_fwd(C.byref(proj), C.byref(tiles), F, cameras(cams),
                              _ptr(obs_depth, torch.float32, "obs_depth"), C.byref(opts), C.byref(_image(out)),
                              _ptr(status, torch.int32, "status", 4), _stream(stream)))
@@ -358,12 +361,12 @@ def gs_render_bwd(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tensor, pose
                   values: torch.Tensor, ranges: torch.Tensor, T_cw: Optional[torch.Tensor], g: Optional[Gaussians],
                   obs_depth: Optional[torch.Tensor], fwd: dict, dL: Optional[dict], loss: Optional[dict],
                   grads: Optional[dict], pose_partials: torch.Tensor, pose_grad: Optional[torch.Tensor],
-                  status: torch.Tensor, ws: torch.Tensor, stream=None) -> None:
+                  status: torch.Tensor, ws: torch.Tensor, stream=None, order: Optional[torch.Tensor] = None) -> None:
     F = len(cams)
     proj = gs_projected(n_gaussians, F, _ptr(rec, torch.float32, "rec"), 1,
                         _ptr(pose_jac, torch.float32, "pose_jac"))
     tiles = gs_tiles(values.numel(), ranges.numel() // 2, _ptr(values, torch.int32), None,
-                     _ptr(ranges, torch.int32))
+                     _ptr(ranges, torch.int32), _ptr(order, torch.int32, "order", ranges.numel() // 2))
     gl = None
     if loss is not None:
         gl = gs_loss(float(loss.get("w_color", 0.0)), float(loss.get("w_depth", 0.0)), float(loss.get("w_unc", 0.0)),

@@ -201,7 +201,7 @@ gs_status gs_bin_tiles(const gs_projected *proj, int n_frames, const gs_camera *
     if (!aligned(ws, 256)) return fail(GS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
     const int npf = proj->n_gaussians > 0 ? proj->n_gaussians : 1;
     return cuda_status(gs::launch_bin_tiles(proj->rec, proj->tiles_touched, M, npf, ft, tiles->capacity, tiles->values,
-                                            tiles->keys, tiles->ranges, status, ws, stream),
+                                            tiles->keys, tiles->ranges, tiles->order, status, ws, stream),
                        "gs_bin_tiles");
 }
 
@@ -219,7 +219,8 @@ gs_status gs_render_fwd(const gs_projected *proj, const gs_tiles *tiles, int n_f
         return fail(GS_ERR_INVALID_ARG, "dom_pos and dom_weight go together");
     gs::ImagePtrs ip{out->color, out->depth, out->alpha, out->unc, out->nu_map, out->median, out->T_final, out->n_last,
                      out->n_contrib, out->median_pos, out->dom_pos, out->dom_weight};
-    return cuda_status(gs::launch_render_fwd(proj->rec, tiles->values, tiles->ranges, ft, obs_depth, ip, status, stream),
+    return cuda_status(gs::launch_render_fwd(proj->rec, tiles->values, tiles->ranges, tiles->order, ft, obs_depth, ip,
+                                             status, stream),
                        "gs_render_fwd");
 }
 
@@ -292,7 +293,8 @@ gs_status gs_render_bwd(const gs_projected *proj, const gs_tiles *tiles, int n_f
                 if (e != cudaSuccess) return cuda_status(e, "gs_render_bwd memset");
             }
         }
-        return cuda_status(gs::launch_render_bwd(mode, proj->rec, proj->pose_jac, tiles->values, tiles->ranges, ft,
+        return cuda_status(gs::launch_render_bwd(mode, proj->rec, proj->pose_jac, tiles->values, tiles->ranges,
+                                                 tiles->order, ft,
                                                  obs_depth, ip, lp, nullptr, pose_partials, per_frame, pose_grad,
                                                  counters, status, stream),
                            "gs_render_bwd");
@@ -303,7 +305,8 @@ gs_status gs_render_bwd(const gs_projected *proj, const gs_tiles *tiles, int n_f
     float *grad2d = static_cast<float *>(ws);
     if ((e = cudaMemsetAsync(grad2d, 0, sizeof(float) * gs::kGrad2d * (size_t)M, stream)) != cudaSuccess)
         return cuda_status(e, "gs_render_bwd memset");
-    if ((e = gs::launch_render_bwd(mode, proj->rec, nullptr, tiles->values, tiles->ranges, ft, obs_depth, ip, lp,
+    if ((e = gs::launch_render_bwd(mode, proj->rec, nullptr, tiles->values, tiles->ranges, tiles->order, ft, obs_depth,
+                                   ip, lp,
                                    grad2d, pose_partials, per_frame, nullptr, nullptr, status, stream)) != cudaSuccess)
         return cuda_status(e, "gs_render_bwd");
     return cuda_status(gs::launch_project_bwd(gauss_ptrs(g), N, ft, T_cw, opts->jclamp, proj->rec, grad2d, *grads,

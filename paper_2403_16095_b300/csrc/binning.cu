@@ -8,7 +8,10 @@
 //                 `ranges` buffer doubles as the counters); pairs are spread
 //                 over the lanes of a warp so large footprints do not serialise.
 //   k_tile_scan   exclusive scan of the counters -> each tile's [start, start)
-//                 cursor, total pair count P and the capacity check.
+//                 cursor, total pair count P and the capacity check; optionally
+//                 the launch order of the blend kernels: tiles by descending
+//                 list length (a counting sort on lengths / 4), so that the
+//                 longest tiles, which bound the blend kernels, start first.
 //   k_tile_fill   each pair claims a slot in its tile's bucket and stores the
 //                 low key (depth bits << 32 | record); after this pass every
 //                 tile's cursor equals its end, so `ranges` is final.
@@ -124,16 +127,28 @@ __global__ void __launch_bounds__(kThreads)
 
 // One CTA: exclusive scan of the per-tile counts (ranges[2t+1]) into
 // ranges[2t] = ranges[2t+1] = start (the fill then advances ranges[2t+1] to end).
+constexpr int kOrderBuckets = kScanThreads;  // list length / 4, clipped
+
+__device__ __forceinline__ int order_bucket(uint32_t len) { return (int)min(len >> 2, (uint32_t)kOrderBuckets - 1); }
+
 __global__ void __launch_bounds__(kScanThreads)
     k_tile_scan(uint32_t *__restrict__ ranges, int n_tiles, int capacity, int32_t *__restrict__ status,
-                int *__restrict__ misc) {
+                int *__restrict__ misc, uint32_t *__restrict__ order) {
     __shared__ long long s_w[kScanThreads / 32];
+    __shared__ uint32_t s_hist[kOrderBuckets];
+    __shared__ uint32_t s_bw[kScanThreads / 32];
     if (!status_ok(status)) return;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (order) s_hist[t] = 0;
+    __syncthreads();
     const int per = (n_tiles + kScanThreads - 1) / kScanThreads;
     const int lo = min(n_tiles, t * per), hi = min(n_tiles, lo + per);
     long long local = 0;
-    for (int k = lo; k < hi; ++k) local += ranges[2 * (size_t)k + 1];
+    for (int k = lo; k < hi; ++k) {
+        const uint32_t c = ranges[2 * (size_t)k + 1];
+        local += c;
+        if (order) atomicAdd(&s_hist[order_bucket(c)], 1u);
+    }
     long long x = local;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -147,12 +162,31 @@ __global__ void __launch_bounds__(kScanThreads)
         run += (w < warp) ? s_w[w] : 0;
         total += s_w[w];
     }
+    if (order) {
+        // descending bucket order: thread t owns bucket B = last - t; its first
+        // slot is the number of tiles in heavier buckets (CTA exclusive scan)
+        __syncthreads();
+        const uint32_t h = s_hist[kOrderBuckets - 1 - t];
+        uint32_t xs = h;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, xs, off);
+            if (lane >= off) xs += y;
+        }
+        if (lane == 31) s_bw[warp] = xs;
+        __syncthreads();
+        uint32_t pre = 0;
+        for (int w = 0; w < warp; ++w) pre += s_bw[w];
+        s_hist[kOrderBuckets - 1 - t] = pre + xs - h;  // cursor of that bucket
+        __syncthreads();
+    }
     for (int k = lo; k < hi; ++k) {
         const uint32_t c = ranges[2 * (size_t)k + 1];
         const uint32_t start = (uint32_t)(run > UINT_MAX ? UINT_MAX : run);
         ranges[2 * (size_t)k] = start;
         ranges[2 * (size_t)k + 1] = start;
         run += c;
+        if (order) order[atomicAdd(&s_hist[order_bucket(c)], 1u)] = (uint32_t)k;
     }
     if (t == 0) {
         status[1] = (int32_t)(total > INT_MAX ? INT_MAX : total);
@@ -338,7 +372,7 @@ size_t bin_workspace_bytes(int n_records, int capacity) {
 
 cudaError_t launch_bin_tiles(const float *rec, const int *touched, int n_records, int n_per_frame,
                              const FrameTable &ft, int capacity, uint32_t *values, uint64_t *keys_out,
-                             uint32_t *ranges, int32_t *status, void *ws, cudaStream_t s) {
+                             uint32_t *ranges, uint32_t *order, int32_t *status, void *ws, cudaStream_t s) {
     const WsLayout L = layout(capacity);
     char *w = static_cast<char *>(ws);
     uint64_t *low = reinterpret_cast<uint64_t *>(w + L.low);
@@ -353,7 +387,7 @@ cudaError_t launch_bin_tiles(const float *rec, const int *touched, int n_records
     if (ft.total_tiles == 0) return cudaSuccess;
     const int grid = n_records > 0 ? (n_records + kThreads - 1) / kThreads : 1;
     k_tile_count<<<grid, kThreads, 0, s>>>(rec, touched, n_records, n_per_frame, ft, ranges, status);
-    k_tile_scan<<<1, kScanThreads, 0, s>>>(ranges, ft.total_tiles, capacity, status, misc);
+    k_tile_scan<<<1, kScanThreads, 0, s>>>(ranges, ft.total_tiles, capacity, status, misc, order);
     k_tile_fill<<<grid, kThreads, 0, s>>>(rec, touched, n_records, n_per_frame, ft, ranges, low, capacity, status);
     k_tile_sort<<<ft.total_tiles, kThreads, 0, s>>>(low, tmp, ranges, values, keys_out, rec_bits, status);
     return cudaGetLastError();

@@ -81,13 +81,14 @@ cudaError_t launch_project_bwd(const GaussPtrs &g, int n, const FrameTable &ft, 
 size_t bin_workspace_bytes(int n_records, int capacity);
 cudaError_t launch_bin_tiles(const float *rec, const int *touched, int n_records, int n_per_frame,
                              const FrameTable &ft, int capacity, uint32_t *values, uint64_t *keys_out,
-                             uint32_t *ranges, int32_t *status, void *ws, cudaStream_t s);
+                             uint32_t *ranges, uint32_t *order, int32_t *status, void *ws, cudaStream_t s);
 // render_fwd.cu
-cudaError_t launch_render_fwd(const float *rec, const uint32_t *values, const uint32_t *ranges, const FrameTable &ft,
-                              const float *obs_depth, const ImagePtrs &out, const int32_t *status, cudaStream_t s);
+cudaError_t launch_render_fwd(const float *rec, const uint32_t *values, const uint32_t *ranges, const uint32_t *order,
+                              const FrameTable &ft, const float *obs_depth, const ImagePtrs &out,
+                              const int32_t *status, cudaStream_t s);
 // render_bwd.cu
 cudaError_t launch_render_bwd(int mode, const float *rec, const float *jac, const uint32_t *values,
-                              const uint32_t *ranges, const FrameTable &ft, const float *obs_depth,
+                              const uint32_t *ranges, const uint32_t *order, const FrameTable &ft, const float *obs_depth,
                               const ImagePtrs &fwd, const LossParams &lp, float *grad2d, float *pose_partials,
                               int per_frame, double *pose_grad, unsigned *counters, const int32_t *status,
                               cudaStream_t s);

@@ -48,7 +48,8 @@ struct BwdSmem {
 template <int TILE, int MODE, bool CD>
 __global__ void __launch_bounds__(TILE *TILE)
     k_render_bwd(const float4 *__restrict__ rec, const float4 *__restrict__ jac, const uint32_t *__restrict__ values,
-                 const uint2 *__restrict__ ranges, FrameTable ft, const float *__restrict__ obs_depth, ImagePtrs fwd,
+                 const uint2 *__restrict__ ranges, const uint32_t *__restrict__ order, FrameTable ft,
+                 const float *__restrict__ obs_depth, ImagePtrs fwd,
                  LossParams lp, float *__restrict__ grad2d, float *__restrict__ pose_partials, int per_frame,
                  double *__restrict__ pose_grad, unsigned *__restrict__ counters, const int32_t *__restrict__ status) {
     using SM = BwdSmem<TILE, MODE>;
@@ -69,7 +70,7 @@ __global__ void __launch_bounds__(TILE *TILE)
     __shared__ int s_flag;
     if (status[0] != 0) return;
 
-    const int gtile = blockIdx.x;
+    const int gtile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;  // heaviest tiles first
     const int f = frame_of_tile(ft, gtile);
     const FrameDesc &fd = ft.f[f];
     const int lt = gtile - fd.tile_off;
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(TILE *TILE)
 // device (a host-side attribute; the first call happens outside any capture).
 template <int TILE, int MODE, bool CD>
 cudaError_t launch_variant(const float4 *rec, const float4 *jac, const uint32_t *values, const uint2 *ranges,
-                           const FrameTable &ft, const float *obs_depth, const ImagePtrs &fwd, const LossParams &lp,
+                           const uint32_t *order, const FrameTable &ft, const float *obs_depth, const ImagePtrs &fwd, const LossParams &lp,
                            float *grad2d, float *pp, int per_frame, double *pg, unsigned *cnt, const int32_t *status,
                            cudaStream_t s) {
     // raise the dynamic shared-memory limit once per device (a host-side
@@ -274,19 +275,19 @@ cudaError_t launch_variant(const float4 *rec, const float4 *jac, const uint32_t 
         if (e != cudaSuccess) return e;
         if (dev < 64) done.fetch_or(1ull << dev);
     }
-    k_render_bwd<TILE, MODE, CD><<<ft.total_tiles, TILE * TILE, smem, s>>>(rec, jac, values, ranges, ft, obs_depth, fwd,
+    k_render_bwd<TILE, MODE, CD><<<ft.total_tiles, TILE * TILE, smem, s>>>(rec, jac, values, ranges, order, ft, obs_depth, fwd,
                                                                            lp, grad2d, pp, per_frame, pg, cnt, status);
     return cudaGetLastError();
 }
 
 template <int TILE>
 cudaError_t launch_tile(int mode, const float4 *rec, const float4 *jac, const uint32_t *values, const uint2 *ranges,
-                        const FrameTable &ft, const float *obs_depth, const ImagePtrs &fwd, const LossParams &lp,
+                        const uint32_t *order, const FrameTable &ft, const float *obs_depth, const ImagePtrs &fwd, const LossParams &lp,
                         float *grad2d, float *pp, int per_frame, double *pg, unsigned *cnt, const int32_t *status,
                         cudaStream_t s) {
     const bool cd = lp.fused ? (lp.w_unc == 0.f && lp.w_nu == 0.f && lp.w_align == 0.f)
                              : (!lp.g_alpha && !lp.g_unc && !lp.g_nu && !lp.g_median);
-#define GS_BWD_ARGS rec, jac, values, ranges, ft, obs_depth, fwd, lp, grad2d, pp, per_frame, pg, cnt, status, s
+#define GS_BWD_ARGS rec, jac, values, ranges, order, ft, obs_depth, fwd, lp, grad2d, pp, per_frame, pg, cnt, status, s
     if (mode == GS_MODE_POSE)
         return cd ? launch_variant<TILE, GS_MODE_POSE, true>(GS_BWD_ARGS)
                   : launch_variant<TILE, GS_MODE_POSE, false>(GS_BWD_ARGS);
@@ -298,7 +299,7 @@ cudaError_t launch_tile(int mode, const float4 *rec, const float4 *jac, const ui
 }  // namespace
 
 cudaError_t launch_render_bwd(int mode, const float *rec, const float *jac, const uint32_t *values,
-                              const uint32_t *ranges, const FrameTable &ft, const float *obs_depth,
+                              const uint32_t *ranges, const uint32_t *order, const FrameTable &ft, const float *obs_depth,
                               const ImagePtrs &fwd, const LossParams &lp, float *grad2d, float *pose_partials,
                               int per_frame, double *pose_grad, unsigned *counters, const int32_t *status,
                               cudaStream_t s) {
@@ -307,9 +308,9 @@ cudaError_t launch_render_bwd(int mode, const float *rec, const float *jac, cons
     const float4 *j4 = reinterpret_cast<const float4 *>(jac);
     const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
     switch (ft.tile) {
-        case 8: return launch_tile<8>(mode, r4, j4, values, rg, ft, obs_depth, fwd, lp, grad2d, pose_partials, per_frame, pose_grad, counters, status, s);
-        case 16: return launch_tile<16>(mode, r4, j4, values, rg, ft, obs_depth, fwd, lp, grad2d, pose_partials, per_frame, pose_grad, counters, status, s);
-        case 32: return launch_tile<32>(mode, r4, j4, values, rg, ft, obs_depth, fwd, lp, grad2d, pose_partials, per_frame, pose_grad, counters, status, s);
+        case 8: return launch_tile<8>(mode, r4, j4, values, rg, order, ft, obs_depth, fwd, lp, grad2d, pose_partials, per_frame, pose_grad, counters, status, s);
+        case 16: return launch_tile<16>(mode, r4, j4, values, rg, order, ft, obs_depth, fwd, lp, grad2d, pose_partials, per_frame, pose_grad, counters, status, s);
+        case 32: return launch_tile<32>(mode, r4, j4, values, rg, order, ft, obs_depth, fwd, lp, grad2d, pose_partials, per_frame, pose_grad, counters, status, s);
         default: return cudaErrorInvalidValue;
     }
 }

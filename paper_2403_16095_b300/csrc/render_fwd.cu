@@ -23,15 +23,15 @@ namespace {
 template <int TILE, bool DOM>
 __global__ void __launch_bounds__(TILE *TILE, 1024 / (TILE * TILE))
     k_render_fwd(const float4 *__restrict__ rec, const uint32_t *__restrict__ values,
-                 const uint2 *__restrict__ ranges, FrameTable ft, const float *__restrict__ obs_depth, ImagePtrs out,
-                 const int32_t *__restrict__ status) {
+                 const uint2 *__restrict__ ranges, const uint32_t *__restrict__ order, FrameTable ft,
+                 const float *__restrict__ obs_depth, ImagePtrs out, const int32_t *__restrict__ status) {
     constexpr int NT = TILE * TILE;
     constexpr int BATCH = NT < 256 ? NT : 256;
     __shared__ float4 s_a[BATCH], s_b[BATCH], s_c[BATCH];
     __shared__ int4 s_r[BATCH];
     if (status[0] != 0) return;
 
-    const int gtile = blockIdx.x;
+    const int gtile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;  // heaviest tiles first
     const int f = frame_of_tile(ft, gtile);
     const FrameDesc &fd = ft.f[f];
     const int lt = gtile - fd.tile_off;
@@ -132,26 +132,30 @@ __global__ void __launch_bounds__(TILE *TILE, 1024 / (TILE * TILE))
 }
 
 template <int TILE>
-cudaError_t launch_tile(const float4 *r4, const uint32_t *values, const uint2 *rg, const FrameTable &ft,
-                        const float *obs_depth, const ImagePtrs &out, const int32_t *status, cudaStream_t s) {
+cudaError_t launch_tile(const float4 *r4, const uint32_t *values, const uint2 *rg, const uint32_t *order,
+                        const FrameTable &ft, const float *obs_depth, const ImagePtrs &out, const int32_t *status,
+                        cudaStream_t s) {
     if (out.dom_pos)
-        k_render_fwd<TILE, true><<<ft.total_tiles, TILE * TILE, 0, s>>>(r4, values, rg, ft, obs_depth, out, status);
+        k_render_fwd<TILE, true><<<ft.total_tiles, TILE * TILE, 0, s>>>(r4, values, rg, order, ft, obs_depth, out,
+                                                                         status);
     else
-        k_render_fwd<TILE, false><<<ft.total_tiles, TILE * TILE, 0, s>>>(r4, values, rg, ft, obs_depth, out, status);
+        k_render_fwd<TILE, false><<<ft.total_tiles, TILE * TILE, 0, s>>>(r4, values, rg, order, ft, obs_depth, out,
+                                                                          status);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_render_fwd(const float *rec, const uint32_t *values, const uint32_t *ranges, const FrameTable &ft,
-                              const float *obs_depth, const ImagePtrs &out, const int32_t *status, cudaStream_t s) {
+cudaError_t launch_render_fwd(const float *rec, const uint32_t *values, const uint32_t *ranges, const uint32_t *order,
+                              const FrameTable &ft, const float *obs_depth, const ImagePtrs &out,
+                              const int32_t *status, cudaStream_t s) {
     if (ft.total_tiles == 0) return cudaSuccess;
     const float4 *r4 = reinterpret_cast<const float4 *>(rec);
     const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
     switch (ft.tile) {
-        case 8: return launch_tile<8>(r4, values, rg, ft, obs_depth, out, status, s);
-        case 16: return launch_tile<16>(r4, values, rg, ft, obs_depth, out, status, s);
-        case 32: return launch_tile<32>(r4, values, rg, ft, obs_depth, out, status, s);
+        case 8: return launch_tile<8>(r4, values, rg, order, ft, obs_depth, out, status, s);
+        case 16: return launch_tile<16>(r4, values, rg, order, ft, obs_depth, out, status, s);
+        case 32: return launch_tile<32>(r4, values, rg, order, ft, obs_depth, out, status, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -48,6 +48,7 @@ class Rasterizer:
         self.status = torch.zeros(4, dtype=torch.int32, device=dev)
         self.n_tiles = _tiles(self.cams, tile)
         self.ranges = torch.empty(2 * self.n_tiles, dtype=torch.int32, device=dev)
+        self.order = torch.empty(self.n_tiles, dtype=torch.int32, device=dev)  # heaviest tiles first
         self.pix_total = _pix(self.cams)
         P = self.pix_total
         self.img = {
@@ -101,11 +102,11 @@ class Rasterizer:
 
     def bin(self, stream=None) -> None:
         A.gs_bin_tiles(self.N, self.cams, self.opts, self.rec, self.touched, self.values, self.keys, self.ranges,
-                       self.status, self.bin_ws, stream)
+                       self.status, self.bin_ws, stream, order=self.order)
 
     def forward(self, obs_depth: Optional[torch.Tensor] = None, stream=None) -> None:
         A.gs_render_fwd(self.N, self.cams, self.opts, self.rec, self.values, self.ranges, obs_depth, self.img,
-                        self.status, stream)
+                        self.status, stream, order=self.order)
 
     def backward(self, *, obs_depth=None, loss: Optional[dict] = None, dL: Optional[dict] = None,
                  g: Optional[Gaussians] = None, T_cw: Optional[torch.Tensor] = None, grads: Optional[dict] = None,
@@ -114,7 +115,7 @@ class Rasterizer:
         ``pose_grad`` (otherwise call reduce_pose())."""
         A.gs_render_bwd(self.N, self.cams, self.opts, self.rec, self.jac, self.values, self.ranges, T_cw, g,
                         obs_depth, self.img, dL, loss, grads, self.pose_partials,
-                        self.pose_grad if fused_pose else None, self.status, self.bwd_ws, stream)
+                        self.pose_grad if fused_pose else None, self.status, self.bwd_ws, stream, order=self.order)
 
     def nu_accumulate(self, obs_depth: torch.Tensor, nu_num: torch.Tensor, nu_cnt: torch.Tensor,
                       dominant: Optional[torch.Tensor] = None, stream=None) -> None:

@@ -147,6 +147,12 @@ def test_bin_tiles_bit_exact(cams, tile, ties):
     full = ranges[:, 1] > ranges[:, 0]
     assert np.array_equal(got[full], ranges[full])          # non-empty tiles: exact [start, end)
     assert np.all(got[~full, 0] == got[~full, 1])            # empty tiles: any start == end
+    # launch order: every tile once, list lengths (bucketed by 4) non-increasing
+    order = r.order.cpu().numpy()
+    assert np.array_equal(np.sort(order), np.arange(len(ranges)))
+    lens = (ranges[:, 1] - ranges[:, 0]).astype(np.int64)
+    b = np.minimum(lens[order] >> 2, 1023)
+    assert np.all(np.diff(b) <= 0)
 
 
 def test_bin_tiles_capacity_overflow_sets_status():

@@ -150,3 +150,33 @@ def test_near_plane_and_nu_cull():
     torch.cuda.synchronize()
     ora = oracle.render(f32_scene(sc2), cam, T, nu_cull=0.025)
     _compare(r, 0, ora)
+
+
+def test_launch_order_changes_nothing():
+    """The heaviest-first launch order written by the binning only reorders CTAs:
+    forward images and the POSE-mode pose gradient are bit-identical to a launch
+    in plain tile order."""
+    from paper_2403_16095_b300 import Rasterizer
+    from paper_2403_16095_b300 import _abi as A
+    sc = synth.room_scene(60_000, seed=1007)
+    cam = synth.Camera(320, 240, 300.0, 300.0, 160.0, 120.0)
+    T = np.asarray(synth.room_track_poses(3, seed=1007)[1], np.float32)
+    tc, td = synth.random_targets(cam, 1007 + 1, depth_range=(0.5, 4.0))
+    obs = torch.from_numpy(td).cuda().reshape(-1)
+    loss = dict(w_color=0.2, w_depth=1.0, unc_tau=0.025, target_color=torch.from_numpy(tc).cuda().reshape(-1),
+                target_depth=obs)
+    r = Rasterizer([cam], sc.n, tile=16, mode=A.GS_MODE_POSE)
+    r.render(to_gpu_gaussians(sc), poses_gpu(T), obs)
+    r.backward(obs_depth=obs, loss=loss)
+    torch.cuda.synchronize()
+    assert not torch.equal(r.order.cpu(), torch.arange(r.n_tiles, dtype=torch.int32))
+    img_o = {k: v.clone() for k, v in r.img.items()}
+    pg_o = r.pose_grad.clone()
+    A.gs_render_fwd(r.N, r.cams, r.opts, r.rec, r.values, r.ranges, obs, r.img, r.status, order=None)
+    A.gs_render_bwd(r.N, r.cams, r.opts, r.rec, r.jac, r.values, r.ranges, None, None, obs, r.img, None, loss,
+                    None, r.pose_partials, r.pose_grad, r.status, r.bwd_ws, order=None)
+    torch.cuda.synchronize()
+    assert r.read_status()[0] == 0
+    for k, v in img_o.items():
+        assert torch.equal(v, r.img[k]), k
+    assert torch.equal(pg_o, r.pose_grad)
