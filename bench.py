@@ -249,6 +249,7 @@ def run_ours(a):
     torch.cuda.synchronize()
     assert tr.rast.read_status()[0] == 0, "warm-up failed (pair capacity?)"
 
+    r_cnt = Rasterizer([cam], g.n, tile=a.tile, mode=A.GS_MODE_FWD)
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
@@ -260,7 +261,11 @@ def run_ours(a):
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
         bwd_ms.extend(tr.backward_ms())
-        contrib.append(int(tr.rast.img["n_contrib"].sum()))
+        # blended entries (the roofline's work unit) of a full-channel forward at the
+        # frame's final pose, outside the timed region (the tracker renders only
+        # the channels its loss reads)
+        r_cnt.render(g, tr.T_cw)
+        contrib.append(int(r_cnt.img["n_contrib"].sum()))
         code, _ = tr.rast.read_status()
         if code:
             raise RuntimeError(f"device status {code} during the timed region")

@@ -4,7 +4,7 @@
 //                the frame's pose partials (the same routine the backward
 //                kernels run in their last CTA, so results are bit-identical),
 //                final value in FP64.
-// k_pose_adam    one thread per frame: converts the left se(3) gradient
+// k_pose_adam    one warp per frame: converts the left se(3) gradient
 //                (rho, phi) into the {so(3) | T} form the paper optimises
 //                (g_t = g_rho, g_R = g_phi - t x g_rho), updates the FP64 Adam
 //                moments, computes the step d = -lr mhat / (sqrt(vhat) + eps) in
@@ -50,46 +50,64 @@ __device__ void so3_exp(const double w[3], double R[3][3]) {
         }
 }
 
-__global__ void k_pose_adam(double *__restrict__ state, const double *__restrict__ grad, float *__restrict__ T_cw,
-                            int n_frames, gs_adam ad, const int32_t *__restrict__ status) {
+// One warp per frame: lane k < 6 updates moment k and its step; lanes 0-8 form
+// one entry each of Exp(d_R) and of the composed rotation; lanes 9-11 the
+// translation. Same arithmetic per entry as a scalar loop would do, spread over
+// lanes so that the FP64 dependency chain is short.
+__global__ void __launch_bounds__(32)
+    k_pose_adam(double *__restrict__ state, const double *__restrict__ grad, float *__restrict__ T_cw,
+                int n_frames, gs_adam ad, const int32_t *__restrict__ status) {
     if (status[0] != 0) return;
-    const int f = threadIdx.x;
+    const int f = blockIdx.x, lane = threadIdx.x;
     if (f >= n_frames) return;
     double *st = state + (size_t)f * GS_POSE_STATE_DOUBLES;
     double *R = st, *t = st + 9, *m = st + 12, *v = st + 18;
     const double *gr = grad + (size_t)f * 6;
-    st[24] += 1.0;                 // step count
-    st[25] *= (double)ad.beta1;    // beta1^step
-    st[26] *= (double)ad.beta2;    // beta2^step
-    const float c1 = (float)(1.0 - st[25]), c2 = (float)(1.0 - st[26]);
-    double g[6];
-    g[0] = gr[0];
-    g[1] = gr[1];
-    g[2] = gr[2];
-    g[3] = gr[3] - (t[1] * gr[2] - t[2] * gr[1]);
-    g[4] = gr[4] - (t[2] * gr[0] - t[0] * gr[2]);
-    g[5] = gr[5] - (t[0] * gr[1] - t[1] * gr[0]);
-    const double b1 = ad.beta1, b2 = ad.beta2;
-    double d[6];
-    for (int k = 0; k < 6; ++k) {
-        m[k] = b1 * m[k] + (1.0 - b1) * g[k];
-        v[k] = b2 * v[k] + (1.0 - b2) * g[k] * g[k];
-        const float lr = k < 3 ? ad.lr_trans : ad.lr_rot;
-        d[k] = (double)(-lr * ((float)m[k] / c1) / (sqrtf((float)v[k] / c2) + ad.eps));
+    const double p1 = st[25] * (double)ad.beta1, p2 = st[26] * (double)ad.beta2;  // beta^step
+    const float c1 = (float)(1.0 - p1), c2 = (float)(1.0 - p2);
+    const double Rold = lane < 9 ? R[lane] : 0.0;
+    double dk = 0.0;
+    if (lane < 6) {
+        double g;
+        switch (lane) {  // {so(3) | T}: g_t = g_rho, g_R = g_phi - t x g_rho
+            case 3: g = gr[3] - (t[1] * gr[2] - t[2] * gr[1]); break;
+            case 4: g = gr[4] - (t[2] * gr[0] - t[0] * gr[2]); break;
+            case 5: g = gr[5] - (t[0] * gr[1] - t[1] * gr[0]); break;
+            default: g = gr[lane];
+        }
+        const double b1 = ad.beta1, b2 = ad.beta2;
+        const double mk = b1 * m[lane] + (1.0 - b1) * g;
+        const double vk = b2 * v[lane] + (1.0 - b2) * g * g;
+        m[lane] = mk;
+        v[lane] = vk;
+        const float lr = lane < 3 ? ad.lr_trans : ad.lr_rot;
+        dk = (double)(-lr * ((float)mk / c1) / (sqrtf((float)vk / c2) + ad.eps));
     }
-    double dR[3][3], Rn[3][3];
+    double d[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) d[k] = __shfl_sync(0xffffffffu, dk, k);
+    double dR[3][3];
     so3_exp(d + 3, dR);
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) Rn[i][j] = dR[i][0] * R[j] + dR[i][1] * R[3 + j] + dR[i][2] * R[6 + j];
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) R[3 * i + j] = Rn[i][j];
-    for (int k = 0; k < 3; ++k) t[k] += d[k];
-    float *T = T_cw + (size_t)f * 12;
-    for (int i = 0; i < 3; ++i) {
-        T[4 * i + 0] = (float)R[3 * i + 0];
-        T[4 * i + 1] = (float)R[3 * i + 1];
-        T[4 * i + 2] = (float)R[3 * i + 2];
-        T[4 * i + 3] = (float)t[i];
+    // Rn[i][j] = sum_l dR[i][l] R[l][j]; lane i*3+j holds R[i][j] in Rold
+    double Rc[3][3];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) Rc[e / 3][e % 3] = __shfl_sync(0xffffffffu, Rold, e);
+    __syncwarp();
+    if (lane < 9) {
+        const int i = lane / 3, j = lane % 3;
+        const double rn = dR[i][0] * Rc[0][j] + dR[i][1] * Rc[1][j] + dR[i][2] * Rc[2][j];
+        R[lane] = rn;
+        T_cw[(size_t)f * 12 + 4 * i + j] = (float)rn;
+    } else if (lane < 12) {
+        const int k = lane - 9;
+        const double tn = t[k] + d[k];
+        t[k] = tn;
+        T_cw[(size_t)f * 12 + 4 * k + 3] = (float)tn;
+    }
+    if (lane == 0) {
+        st[24] += 1.0;  // step count
+        st[25] = p1;
+        st[26] = p2;
     }
 }
 
@@ -105,7 +123,7 @@ cudaError_t launch_pose_reduce(const float *partials, int n_frames, int per_fram
 cudaError_t launch_pose_adam(double *state, const double *grad, float *T_cw, int n_frames, gs_adam adam,
                              const int32_t *status, cudaStream_t s) {
     if (n_frames == 0) return cudaSuccess;
-    k_pose_adam<<<1, 64, 0, s>>>(state, grad, T_cw, n_frames, adam, status);
+    k_pose_adam<<<n_frames, 32, 0, s>>>(state, grad, T_cw, n_frames, adam, status);
     return cudaGetLastError();
 }
 

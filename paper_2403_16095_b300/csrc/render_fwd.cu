@@ -12,15 +12,17 @@
 // identical accept/stop decisions and the result does not depend on TILE.
 //
 // The DOM variant also tracks each pixel's dominant entry (largest w = alpha T,
-// the first on ties; Sec. 3.2) for the per-Gaussian uncertainty of Eq. 13; it
-// is a separate instantiation so that tracking pays nothing for it.
+// the first on ties; Sec. 3.2) for the per-Gaussian uncertainty of Eq. 13; the
+// LITE variant (taken when opacity, U, median and the contribution count are
+// not requested, as in tracking) accumulates only colour, depth and the nu map.
+// Separate instantiations, so each caller pays only for what it reads.
 #include "gs_internal.cuh"
 #include "blend_common.cuh"
 
 namespace gs {
 namespace {
 
-template <int TILE, bool DOM>
+template <int TILE, bool DOM, bool LITE>
 __global__ void __launch_bounds__(TILE *TILE, 1024 / (TILE * TILE))
     k_render_fwd(const float4 *__restrict__ rec, const uint32_t *__restrict__ values,
                  const uint2 *__restrict__ ranges, const uint32_t *__restrict__ order, FrameTable ft,
@@ -90,13 +92,16 @@ __global__ void __launch_bounds__(TILE *TILE, 1024 / (TILE * TILE))
                     c1 = fmaf(w, c.y, c1);
                     c2 = fmaf(w, c.z, c2);
                     dep = fmaf(w, b.z, dep);
-                    opa = __fadd_rn(opa, w);
-                    const float dz = __fsub_rn(b.z, Dp);
-                    unc = fmaf(w, __fmul_rn(dz, dz), unc);
                     nus = fmaf(w, b.w, nus);
-                    if (T >= 0.5f && Tn < 0.5f) {
-                        med = b.z;
-                        med_pos = (int)(base + k);
+                    if (!LITE) {
+                        opa = __fadd_rn(opa, w);
+                        const float dz = __fsub_rn(b.z, Dp);
+                        unc = fmaf(w, __fmul_rn(dz, dz), unc);
+                        if (T >= 0.5f && Tn < 0.5f) {
+                            med = b.z;
+                            med_pos = (int)(base + k);
+                        }
+                        ++n_blend;
                     }
                     if (DOM && w > wmax) {
                         wmax = w;
@@ -104,7 +109,6 @@ __global__ void __launch_bounds__(TILE *TILE, 1024 / (TILE * TILE))
                     }
                     T = Tn;
                     last = base + k + 1;
-                    ++n_blend;
                 }
                 if (__all_sync(0xffffffffu, done)) break;
             }
@@ -117,14 +121,16 @@ __global__ void __launch_bounds__(TILE *TILE, 1024 / (TILE * TILE))
     out.color[cbase + HW] = c1;
     out.color[cbase + 2 * (size_t)HW] = c2;
     if (out.depth) out.depth[pix] = dep;
-    if (out.alpha) out.alpha[pix] = opa;
-    if (out.unc && obs_depth) out.unc[pix] = unc;
     if (out.nu_map) out.nu_map[pix] = nus;
-    if (out.median) out.median[pix] = med;
     out.T_final[pix] = T;
     out.n_last[pix] = (int32_t)last;
-    if (out.n_contrib) out.n_contrib[pix] = n_blend;
-    if (out.median_pos) out.median_pos[pix] = med_pos;
+    if (!LITE) {
+        if (out.alpha) out.alpha[pix] = opa;
+        if (out.unc && obs_depth) out.unc[pix] = unc;
+        if (out.median) out.median[pix] = med;
+        if (out.n_contrib) out.n_contrib[pix] = n_blend;
+        if (out.median_pos) out.median_pos[pix] = med_pos;
+    }
     if (DOM) {
         out.dom_pos[pix] = dom_pos;
         out.dom_weight[pix] = wmax;
@@ -135,12 +141,16 @@ template <int TILE>
 cudaError_t launch_tile(const float4 *r4, const uint32_t *values, const uint2 *rg, const uint32_t *order,
                         const FrameTable &ft, const float *obs_depth, const ImagePtrs &out, const int32_t *status,
                         cudaStream_t s) {
+    const bool lite = !out.alpha && !out.unc && !out.median && !out.median_pos && !out.n_contrib;
     if (out.dom_pos)
-        k_render_fwd<TILE, true><<<ft.total_tiles, TILE * TILE, 0, s>>>(r4, values, rg, order, ft, obs_depth, out,
-                                                                         status);
+        k_render_fwd<TILE, true, false><<<ft.total_tiles, TILE * TILE, 0, s>>>(r4, values, rg, order, ft, obs_depth,
+                                                                                out, status);
+    else if (lite)
+        k_render_fwd<TILE, false, true><<<ft.total_tiles, TILE * TILE, 0, s>>>(r4, values, rg, order, ft, obs_depth,
+                                                                                out, status);
     else
-        k_render_fwd<TILE, false><<<ft.total_tiles, TILE * TILE, 0, s>>>(r4, values, rg, order, ft, obs_depth, out,
-                                                                          status);
+        k_render_fwd<TILE, false, false><<<ft.total_tiles, TILE * TILE, 0, s>>>(r4, values, rg, order, ft, obs_depth,
+                                                                                 out, status);
     return cudaGetLastError();
 }
 

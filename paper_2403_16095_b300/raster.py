@@ -31,7 +31,10 @@ class Rasterizer:
 
     def __init__(self, cams: Sequence, n_gaussians: int, tile: int = 16, mode: int = A.GS_MODE_POSE,
                  capacity: Optional[int] = None, jclamp: float = 1.3, nu_cull: float = 0.0,
-                 keep_keys: bool = False, dominant: bool = False, device=None):
+                 keep_keys: bool = False, dominant: bool = False, channels: str = "all", device=None):
+        """channels: "all" renders every channel; "track" only what the tracking
+        loss and its POSE backward read (colour, depth, nu map, T_final, n_last),
+        which selects the lighter forward kernel."""
         self.cams = list(cams)
         self.F = len(self.cams)
         self.N = int(n_gaussians)
@@ -63,6 +66,11 @@ class Rasterizer:
             "n_contrib": torch.empty(P, dtype=torch.int32, device=dev),
             "median_pos": torch.empty(P, dtype=torch.int32, device=dev),
         }
+        if channels == "track":
+            for k in ("alpha", "unc", "median", "n_contrib", "median_pos"):
+                del self.img[k]
+        elif channels != "all":
+            raise ValueError(f"channels={channels!r}")
         if dominant:  # dominated pixels for the uncertainty of Eq. 13
             self.img["dom_pos"] = torch.empty(P, dtype=torch.int32, device=dev)
             self.img["dom_weight"] = torch.empty(P, dtype=torch.float32, device=dev)
@@ -172,8 +180,9 @@ class Rasterizer:
         H, W = int(c.height), int(c.width)
         off = sum(int(x.width) * int(x.height) for x in self.cams[:f])
         out = {"color": self.img["color"][3 * off: 3 * off + 3 * H * W].view(3, H, W)}
-        for k in CHANNELS[1:] + tuple(k for k in ("dom_pos", "dom_weight") if k in self.img):
-            out[k] = self.img[k][off: off + H * W].view(H, W)
+        for k in CHANNELS[1:] + ("dom_pos", "dom_weight"):
+            if k in self.img:
+                out[k] = self.img[k][off: off + H * W].view(H, W)
         return out
 
     def tile_lists(self):
@@ -319,7 +328,8 @@ class Tracker:
                              torch.cuda.Event(enable_timing=True, external=True)) for _ in range(iters)]
                            if timing else None)
         dev = (g.packed if isinstance(g, PackedGaussians) else g.means).device
-        self.rast = Rasterizer([cam], g.n, tile=tile, mode=A.GS_MODE_POSE, capacity=capacity, jclamp=jclamp)
+        self.rast = Rasterizer([cam], g.n, tile=tile, mode=A.GS_MODE_POSE, capacity=capacity, jclamp=jclamp,
+                               channels="track")
         H, W = int(cam.height), int(cam.width)
         self.target_color = torch.zeros(3 * H * W, dtype=torch.float32, device=dev)
         self.target_depth = torch.zeros(H * W, dtype=torch.float32, device=dev)

@@ -180,3 +180,23 @@ def test_launch_order_changes_nothing():
     for k, v in img_o.items():
         assert torch.equal(v, r.img[k]), k
     assert torch.equal(pg_o, r.pose_grad)
+
+
+def test_tracking_channels_forward_equals_full_forward():
+    """The lighter forward taken when only the tracking channels are requested
+    renders colour, depth, nu map, T_final and n_last bit-identically."""
+    from paper_2403_16095_b300 import Rasterizer
+    from paper_2403_16095_b300 import _abi as A
+    sc = synth.room_scene(60_000, seed=1007)
+    cam = synth.Camera(320, 240, 300.0, 300.0, 160.0, 120.0)
+    T = np.asarray(synth.room_track_poses(3, seed=1007)[2], np.float32)
+    _, td = synth.random_targets(cam, 1007 + 2, depth_range=(0.5, 4.0))
+    obs = torch.from_numpy(td).cuda().reshape(-1)
+    imgs = []
+    for ch in ("all", "track"):
+        r = Rasterizer([cam], sc.n, tile=16, mode=A.GS_MODE_POSE, channels=ch)
+        r.render(to_gpu_gaussians(sc), poses_gpu(T), obs)
+        imgs.append(r.img)
+    assert "n_contrib" not in imgs[1]
+    for k in ("color", "depth", "nu_map", "T_final", "n_last"):
+        assert torch.equal(imgs[0][k], imgs[1][k]), k
