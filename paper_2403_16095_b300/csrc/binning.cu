@@ -275,33 +275,42 @@ __device__ bool cta_radix_pass(const uint64_t *src, uint64_t *dst, int n, int sh
 }
 
 // ---------------------------------------------------------------------------
-// k_tile_sort: one CTA per tile. Buckets of at most kSmemKeys keys are sorted
-// in shared memory by a bitonic network (padding = the all-ones key, which
-// sorts last; low keys are unique within a bucket, so the result is the same
-// as a stable radix sort). Larger buckets take a stable LSD radix sort that
-// ping-pongs in global memory.
-__global__ void __launch_bounds__(kThreads)
+// k_tile_sort: one CTA per tile, heaviest tiles first when the launch order is
+// given. Buckets of at most kSmemKeys keys are sorted in shared memory by a
+// bitonic network (padding = the all-ones key, which sorts last; low keys are
+// unique within a bucket, so the result is the same as a stable radix sort).
+// Warp w owns the contiguous segment [w S, (w + 1) S), S = padded size / 8, and
+// the pairs whose elements lie in it: a stage whose stride is below S stays
+// inside each segment and needs only a warp barrier, so a 256-key bucket takes
+// 9 CTA barriers instead of 36. Larger buckets take a stable LSD radix sort
+// that ping-pongs in global memory.
+__global__ void __launch_bounds__(kThreads, 8)
     k_tile_sort(uint64_t *low_keys, uint64_t *tmp, const uint32_t *__restrict__ ranges,
-                uint32_t *__restrict__ values, uint64_t *__restrict__ keys_out, int rec_bits,
-                const int32_t *__restrict__ status) {
+                const uint32_t *__restrict__ order, uint32_t *__restrict__ values, uint64_t *__restrict__ keys_out,
+                int rec_bits, const int32_t *__restrict__ status) {
     __shared__ uint64_t s_a[kSmemKeys];
     __shared__ uint32_t s_cnt[kRadix];
     __shared__ uint32_t s_wh[kWarps][kRadix];
     __shared__ uint32_t s_warp[kWarps];
     if (!status_ok(status)) return;
-    const int tile = blockIdx.x;
+    const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
     const uint32_t s = ranges[2 * (size_t)tile], e = ranges[2 * (size_t)tile + 1];
     const int n = (int)(e - s);
     if (n <= 0) return;
     const int tid = threadIdx.x;
     if (n <= kSmemKeys) {
-        int np = 2;
+        int np = 16;
         while (np < n) np <<= 1;
         for (int i = tid; i < np; i += kThreads) s_a[i] = i < n ? low_keys[s + i] : ~0ull;
         __syncthreads();
+        const int lane = tid & 31, warp = tid >> 5;
+        const int seg = np / kWarps;            // elements per warp segment (>= 2)
+        const int seg_pairs = seg >> 1;         // pairs per warp and stage
         for (int size = 2; size <= np; size <<= 1)
             for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int t = tid; t < (np >> 1); t += kThreads) {
+                const bool cross = stride >= seg;  // pairs span two warps' segments
+                for (int u = lane; u < seg_pairs; u += 32) {
+                    const int t = warp * seg_pairs + u;
                     const int i = ((t & ~(stride - 1)) << 1) | (t & (stride - 1));  // lower index of pair t
                     const int j = i + stride;
                     const uint64_t x = s_a[i], y = s_a[j];
@@ -311,8 +320,14 @@ __global__ void __launch_bounds__(kThreads)
                         s_a[j] = x;
                     }
                 }
-                __syncthreads();
+                // a CTA barrier where this stage or the next one crosses segments
+                const int next_stride = stride > 1 ? (stride >> 1) : size;
+                if (cross || next_stride >= seg)
+                    __syncthreads();
+                else
+                    __syncwarp();
             }
+        __syncthreads();
         for (int i = tid; i < n; i += kThreads) {
             const uint64_t k = s_a[i];
             values[s + i] = (uint32_t)k;
@@ -389,7 +404,7 @@ cudaError_t launch_bin_tiles(const float *rec, const int *touched, int n_records
     k_tile_count<<<grid, kThreads, 0, s>>>(rec, touched, n_records, n_per_frame, ft, ranges, status);
     k_tile_scan<<<1, kScanThreads, 0, s>>>(ranges, ft.total_tiles, capacity, status, misc, order);
     k_tile_fill<<<grid, kThreads, 0, s>>>(rec, touched, n_records, n_per_frame, ft, ranges, low, capacity, status);
-    k_tile_sort<<<ft.total_tiles, kThreads, 0, s>>>(low, tmp, ranges, values, keys_out, rec_bits, status);
+    k_tile_sort<<<ft.total_tiles, kThreads, 0, s>>>(low, tmp, ranges, order, values, keys_out, rec_bits, status);
     return cudaGetLastError();
 }
 
