@@ -57,6 +57,10 @@ BWD_FLOP_PER_CONTRIB = 122
 # channel dot product (9 with opacity, U and the median), dL/dalpha and suffix
 # sum (5), gradients of mean2d, conic, opacity, depth and colour (21).
 BWD_FULL_FLOP_PER_CONTRIB = 52
+# DRAM bytes (read + write) of one k_render_bwd<16,POSE> launch of this workload,
+# from one ncu capture of the current kernel (profiles/k_render_blend_track-640x480-300k.md,
+# cold cache); None once the kernel changes.
+BWD_DRAM_BYTES_PER_LAUNCH = 27.48928e6 + 768
 FP32_LANES_PER_SM = 128
 N_SM = 148
 
@@ -320,7 +324,9 @@ def run_ours(a):
     E = statistics.mean(contrib)
     achieved = E * BWD_FLOP_PER_CONTRIB / (bwd_avg_ms * 1e-3) / 1e12
     roof = {"kernel": "k_render_bwd<16,POSE>", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
-            "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+            "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+            "traffic": BWD_DRAM_BYTES_PER_LAUNCH if a.tile == 16 else None,
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch, cold cache",
             "peak_source": f"148 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (max SM clock)",
             "flop_per_contribution": BWD_FLOP_PER_CONTRIB, "contributions_per_launch": E,
             "avg_launch_ms": bwd_avg_ms, "launches": len(bwd_ms)}
