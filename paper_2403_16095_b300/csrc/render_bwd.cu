@@ -228,18 +228,29 @@ __global__ void __launch_bounds__(TILE *TILE)
                 }
             } else {
                 if (__any_sync(0xffffffffu, act)) {
+                    // warp sum of the 11 gradients by recursive halving: at each
+                    // step a lane keeps half of its values and adds its partner's
+                    // copy of them (16 shuffles instead of 11 x 5); lane pairs end
+                    // up holding one total each, and 11 lanes add them with one
+                    // warp-wide atomic instruction
+                    float h[16];
 #pragma unroll
-                    for (int m = 0; m < 11; ++m) {
-                        float s = v[m];
+                    for (int m = 0; m < 16; ++m) h[m] = m < 11 ? v[m] : 0.f;
 #pragma unroll
-                        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-                        v[m] = s;
+                    for (int n = 16, o = 16; n > 1; n >>= 1, o >>= 1) {
+                        const bool up = (lane & o) != 0;
+#pragma unroll
+                        for (int i = 0; i < n / 2; ++i) {
+                            const float send = up ? h[i] : h[i + n / 2];
+                            const float keep = up ? h[i + n / 2] : h[i];
+                            h[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                        }
                     }
-                    if (lane == 0) {
-                        float *gp = grad2d + (size_t)s_idx[k] * kGrad2d;
-#pragma unroll
-                        for (int m = 0; m < 11; ++m) atomicAdd(gp + m, v[m]);
-                    }
+                    h[0] += __shfl_xor_sync(0xffffffffu, h[0], 1);
+                    const int field = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 +
+                                      ((lane >> 1) & 1);
+                    if ((lane & 1) == 0 && field < 11)
+                        atomicAdd(grad2d + (size_t)s_idx[k] * kGrad2d + field, h[0]);
                 }
             }
           }
