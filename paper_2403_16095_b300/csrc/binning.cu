@@ -128,6 +128,7 @@ __global__ void __launch_bounds__(kThreads)
 // One CTA: exclusive scan of the per-tile counts (ranges[2t+1]) into
 // ranges[2t] = ranges[2t+1] = start (the fill then advances ranges[2t+1] to end).
 constexpr int kOrderBuckets = kScanThreads;  // list length / 4, clipped
+constexpr int kWarpSortKeys = 256;           // shorter lists are sorted by one warp
 
 __device__ __forceinline__ int order_bucket(uint32_t len) { return (int)min(len >> 2, (uint32_t)kOrderBuckets - 1); }
 
@@ -179,6 +180,8 @@ __global__ void __launch_bounds__(kScanThreads)
         for (int w = 0; w < warp; ++w) pre += s_bw[w];
         s_hist[kOrderBuckets - 1 - t] = pre + xs - h;  // cursor of that bucket
         __syncthreads();
+        // tiles of kWarpSortKeys or more entries: the first misc[1] of the order
+        if (t == 0) misc[1] = (int)s_hist[kWarpSortKeys / 4 - 1];
     }
     for (int k = lo; k < hi; ++k) {
         const uint32_t c = ranges[2 * (size_t)k + 1];
@@ -275,10 +278,12 @@ __device__ bool cta_radix_pass(const uint64_t *src, uint64_t *dst, int n, int sh
 }
 
 // ---------------------------------------------------------------------------
-// k_tile_sort: one CTA per tile, heaviest tiles first when the launch order is
-// given. Buckets of at most kSmemKeys keys are sorted in shared memory by a
-// bitonic network (padding = the all-ones key, which sorts last; low keys are
-// unique within a bucket, so the result is the same as a stable radix sort).
+// k_tile_sort: heaviest tiles first when the launch order is given. With the
+// order, tiles of fewer than kWarpSortKeys entries (most of them) are sorted one
+// per warp, 8 per CTA, with warp barriers only; the others take one CTA each.
+// Buckets of at most kSmemKeys keys are sorted in shared memory by a bitonic
+// network (padding = the all-ones key, which sorts last; low keys are unique
+// within a bucket, so the result is the same as a stable radix sort).
 // Warp w owns the contiguous segment [w S, (w + 1) S), S = padded size / 8, and
 // the pairs whose elements lie in it: a stage whose stride is below S stays
 // inside each segment and needs only a warp barrier, so a 256-key bucket takes
@@ -286,18 +291,55 @@ __device__ bool cta_radix_pass(const uint64_t *src, uint64_t *dst, int n, int sh
 // that ping-pongs in global memory.
 __global__ void __launch_bounds__(kThreads, 8)
     k_tile_sort(uint64_t *low_keys, uint64_t *tmp, const uint32_t *__restrict__ ranges,
-                const uint32_t *__restrict__ order, uint32_t *__restrict__ values, uint64_t *__restrict__ keys_out,
-                int rec_bits, const int32_t *__restrict__ status) {
+                const uint32_t *__restrict__ order, const int *__restrict__ misc, int n_tiles,
+                uint32_t *__restrict__ values, uint64_t *__restrict__ keys_out, int rec_bits,
+                const int32_t *__restrict__ status) {
     __shared__ uint64_t s_a[kSmemKeys];
     __shared__ uint32_t s_cnt[kRadix];
     __shared__ uint32_t s_wh[kWarps][kRadix];
     __shared__ uint32_t s_warp[kWarps];
+    static_assert(kWarps * kWarpSortKeys <= kSmemKeys, "warp buckets share s_a");
     if (!status_ok(status)) return;
+    const int tid = threadIdx.x;
+    const int n_large = order ? misc[1] : n_tiles;
+    if ((int)blockIdx.x >= n_large) {  // one short tile per warp
+        const int lane = tid & 31, warp = tid >> 5;
+        const int ti = n_large + ((int)blockIdx.x - n_large) * kWarps + warp;
+        if (ti >= n_tiles) return;
+        const int tile = (int)order[ti];
+        const uint32_t s = ranges[2 * (size_t)tile], e = ranges[2 * (size_t)tile + 1];
+        const int n = (int)(e - s);
+        if (n <= 0) return;
+        uint64_t *wa = s_a + warp * kWarpSortKeys;
+        int np = 2;
+        while (np < n) np <<= 1;
+        for (int i = lane; i < np; i += 32) wa[i] = i < n ? low_keys[s + i] : ~0ull;
+        __syncwarp();
+        for (int size = 2; size <= np; size <<= 1)
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int t = lane; t < (np >> 1); t += 32) {
+                    const int i = ((t & ~(stride - 1)) << 1) | (t & (stride - 1));
+                    const int j = i + stride;
+                    const uint64_t x = wa[i], y = wa[j];
+                    const bool up = (i & size) == 0;
+                    if ((x > y) == up) {
+                        wa[i] = y;
+                        wa[j] = x;
+                    }
+                }
+                __syncwarp();
+            }
+        for (int i = lane; i < n; i += 32) {
+            const uint64_t k = wa[i];
+            values[s + i] = (uint32_t)k;
+            if (keys_out) keys_out[s + i] = ((uint64_t)tile << 32) | (k >> 32);
+        }
+        return;
+    }
     const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
     const uint32_t s = ranges[2 * (size_t)tile], e = ranges[2 * (size_t)tile + 1];
     const int n = (int)(e - s);
     if (n <= 0) return;
-    const int tid = threadIdx.x;
     if (n <= kSmemKeys) {
         int np = 16;
         while (np < n) np <<= 1;
@@ -404,7 +446,8 @@ cudaError_t launch_bin_tiles(const float *rec, const int *touched, int n_records
     k_tile_count<<<grid, kThreads, 0, s>>>(rec, touched, n_records, n_per_frame, ft, ranges, status);
     k_tile_scan<<<1, kScanThreads, 0, s>>>(ranges, ft.total_tiles, capacity, status, misc, order);
     k_tile_fill<<<grid, kThreads, 0, s>>>(rec, touched, n_records, n_per_frame, ft, ranges, low, capacity, status);
-    k_tile_sort<<<ft.total_tiles, kThreads, 0, s>>>(low, tmp, ranges, order, values, keys_out, rec_bits, status);
+    k_tile_sort<<<ft.total_tiles, kThreads, 0, s>>>(low, tmp, ranges, order, misc, ft.total_tiles, values, keys_out,
+                                                    rec_bits, status);
     return cudaGetLastError();
 }
 
