@@ -61,6 +61,11 @@ BWD_FULL_FLOP_PER_CONTRIB = 52
 # from one ncu capture of the current kernel (profiles/k_render_blend_track-640x480-300k.md,
 # cold cache); None once the kernel changes.
 BWD_DRAM_BYTES_PER_LAUNCH = 27.48928e6 + 768
+# forward per blended entry: offsets (2), q (7), exponent argument (1), opacity x G
+# (1), clamp (1), 1 - alpha and T' (2), w (1), colour, depth and nu
+# accumulation (10), ex2 (1)
+FWD_FLOP_PER_CONTRIB = 26
+FUSED_DRAM_BYTES_PER_LAUNCH = None  # not yet captured for the fused kernel
 FP32_LANES_PER_SM = 128
 N_SM = 148
 
@@ -74,6 +79,7 @@ def _args():
     p.add_argument("--tile", type=int, default=16)
     p.add_argument("--workload", choices=("track", "mapping", "uneven", "precision"), default="track")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--unfused", action="store_true", help="forward and backward as two launches per iteration")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-iters", type=int, default=0, help="oracle iterations for the CPU baseline (0 = auto)")
     return p.parse_args()
@@ -230,7 +236,7 @@ def run_ours(a):
     del r0
     starts_t = [torch.from_numpy(np.asarray(T, np.float64)).to(dev) for T in starts]
 
-    tr = Tracker(g, cam, tile=a.tile, iters=ITERS, graph=True, timing=True)
+    tr = Tracker(g, cam, tile=a.tile, iters=ITERS, graph=True, timing=True, fused=not a.unfused)
     f0 = my_frames[0]
     tr.prepare(tcol[f0], tdep[f0], starts_t[f0], headroom=1.6)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
@@ -316,19 +322,25 @@ def run_ours(a):
             torch.distributed.destroy_process_group()
         return
 
-    # ---- roofline of the dominant kernel (the POSE-mode backward)
+    # ---- roofline of the dominant kernel: the fused forward + POSE backward
+    # launch (or, with --unfused, the POSE backward alone)
     peaks = _peaks()
     mhz = peaks.get("sm_max_mhz", 2032.0)
     fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12  # TFLOP/s
     bwd_avg_ms = statistics.mean(bwd_ms)
     E = statistics.mean(contrib)
-    achieved = E * BWD_FLOP_PER_CONTRIB / (bwd_avg_ms * 1e-3) / 1e12
-    roof = {"kernel": "k_render_bwd<16,POSE>", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
-            "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-            "traffic": BWD_DRAM_BYTES_PER_LAUNCH if a.tile == 16 else None,
+    if tr.fused:
+        kname, flop, traffic = f"k_render_fused_pose<{a.tile}>", FWD_FLOP_PER_CONTRIB + BWD_FLOP_PER_CONTRIB, \
+            (FUSED_DRAM_BYTES_PER_LAUNCH if a.tile == 16 else None)
+    else:
+        kname, flop, traffic = f"k_render_bwd<{a.tile},POSE>", BWD_FLOP_PER_CONTRIB, \
+            (BWD_DRAM_BYTES_PER_LAUNCH if a.tile == 16 else None)
+    achieved = E * flop / (bwd_avg_ms * 1e-3) / 1e12
+    roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+            "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch, cold cache",
             "peak_source": f"148 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (max SM clock)",
-            "flop_per_contribution": BWD_FLOP_PER_CONTRIB, "contributions_per_launch": E,
+            "flop_per_contribution": flop, "contributions_per_launch": E,
             "avg_launch_ms": bwd_avg_ms, "launches": len(bwd_ms)}
     bwd_share = sum(bwd_ms) / sum(step_ms)
 

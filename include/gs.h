@@ -59,7 +59,7 @@ extern "C" {
 #endif
 
 #define GS_MAX_FRAMES 64
-#define GS_ABI_VERSION 4
+#define GS_ABI_VERSION 5
 
 typedef struct CUstream_st *gs_stream; /* a cudaStream_t; NULL = legacy default stream */
 
@@ -309,6 +309,20 @@ gs_status gs_render_bwd(const gs_projected *proj, const gs_tiles *tiles, int n_f
                         const gs_loss *loss, const gs_opts *opts, gs_grads *grads,
                         float *pose_partials, double *pose_grad, const int32_t *status, void *ws,
                         size_t ws_bytes, gs_stream stream);
+
+/* Tracking pass: the forward blend (Eq. 3-10) and the POSE-mode backward of the
+ * fused tracking loss (Eq. 14, 16, 19: L1 colour and depth, optionally weighted
+ * by 1/(1 + nu_map/unc_tau)) in one pass per tile, with nothing written in
+ * between. Equal bit for bit to gs_render_fwd followed by gs_render_bwd (POSE)
+ * with the same loss. Only losses with w_unc = w_nu = w_align = 0
+ * (GS_ERR_UNSUPPORTED otherwise). `out` may be NULL, or name any of color,
+ * depth, nu_map, T_final and n_last to have them written as well (its other
+ * members are ignored). pose_partials, pose_grad and ws as for gs_render_bwd
+ * in POSE mode (ws: gs_render_bwd_workspace_size(records, GS_MODE_POSE)).    */
+gs_status gs_render_fwd_bwd_pose(const gs_projected *proj, const gs_tiles *tiles, int n_frames,
+                                 const gs_camera *cams, const gs_loss *loss, const gs_opts *opts,
+                                 gs_image *out, float *pose_partials, double *pose_grad,
+                                 const int32_t *status, void *ws, size_t ws_bytes, gs_stream stream);
 
 /* Per-Gaussian depth uncertainty, Eq. 13 (Sec. 3.2), accumulation half. Each
  * pixel of the n_frames images whose forward found a dominant entry

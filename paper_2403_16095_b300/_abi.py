@@ -97,10 +97,10 @@ class gs_adam(C.Structure):
 
 EXPORTS = ("gs_abi_version", "gs_last_error", "gs_project", "gs_bin_tiles_workspace_size", "gs_bin_tiles",
            "gs_bin_tiles_noalloc", "gs_render_fwd", "gs_pose_partials_per_frame", "gs_render_bwd_workspace_size",
-           "gs_render_bwd", "gs_project_bf16", "gs_spatial_order_workspace_size", "gs_spatial_order",
+           "gs_render_bwd", "gs_render_fwd_bwd_pose", "gs_project_bf16", "gs_spatial_order_workspace_size", "gs_spatial_order",
            "gs_pack_bf16", "gs_nu_accumulate", "gs_nu_finalize", "gs_pose_grad_reduce", "gs_pose_adam_step")
 GS_NOALLOC_MAX_PAIRS = 1 << 19
-ABI_VERSION = 4  # GS_ABI_VERSION of the gs.h these structures mirror
+ABI_VERSION = 5  # GS_ABI_VERSION of the gs.h these structures mirror
 
 
 def _load():
@@ -136,12 +136,15 @@ def _load():
                                   _vp, C.POINTER(gs_gaussians), _vp, C.POINTER(gs_image),
                                   C.POINTER(gs_image_grad), C.POINTER(gs_loss), C.POINTER(gs_opts),
                                   C.POINTER(gs_grads), _vp, _vp, _vp, _vp, C.c_size_t, _vp]
+    lib.gs_render_fwd_bwd_pose.argtypes = [C.POINTER(gs_projected), C.POINTER(gs_tiles), C.c_int,
+                                           C.POINTER(gs_camera), C.POINTER(gs_loss), C.POINTER(gs_opts),
+                                           C.POINTER(gs_image), _vp, _vp, _vp, _vp, C.c_size_t, _vp]
     lib.gs_nu_accumulate.argtypes = [C.POINTER(gs_projected), C.POINTER(gs_tiles), C.c_int, C.POINTER(gs_camera),
                                      _vp, C.POINTER(gs_image), _vp, _vp, _vp, _vp, _vp]
     lib.gs_nu_finalize.argtypes = [C.c_int, _vp, _vp, _vp, C.c_float, C.c_float, _vp, _vp, _vp, _vp]
     lib.gs_pose_grad_reduce.argtypes = [_vp, C.c_int, C.c_int, _vp, _vp, _vp]
     lib.gs_pose_adam_step.argtypes = [_vp, _vp, _vp, C.c_int, C.POINTER(gs_adam), _vp, _vp]
-    for name in ("gs_project", "gs_project_bf16", "gs_spatial_order", "gs_pack_bf16", "gs_bin_tiles", "gs_render_fwd", "gs_render_bwd", "gs_nu_accumulate",
+    for name in ("gs_project", "gs_project_bf16", "gs_render_fwd_bwd_pose", "gs_spatial_order", "gs_pack_bf16", "gs_bin_tiles", "gs_render_fwd", "gs_render_bwd", "gs_nu_accumulate",
                  "gs_nu_finalize", "gs_pose_grad_reduce", "gs_pose_adam_step"):
         getattr(lib, name).restype = C.c_int
     return lib
@@ -416,6 +419,34 @@ def gs_nu_finalize(nu_num: torch.Tensor, nu_cnt: torch.Tensor, nu: torch.Tensor,
                               _ptr(opacity_logit, torch.float32, "opacity_logit", n),
                               _ptr(n_over, torch.int32, "n_over", 1), _ptr(status, torch.int32, "status", 4),
                               _stream(stream)))
+
+
+def _loss(loss: dict) -> gs_loss:
+    return gs_loss(float(loss.get("w_color", 0.0)), float(loss.get("w_depth", 0.0)), float(loss.get("w_unc", 0.0)),
+                   float(loss.get("w_nu", 0.0)), float(loss.get("unc_tau", 0.0)),
+                   _ptr(loss.get("target_color"), torch.float32, "target_color"),
+                   _ptr(loss.get("target_depth"), torch.float32, "target_depth"),
+                   float(loss.get("w_align", 0.0)))
+
+
+def gs_render_fwd_bwd_pose(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tensor, pose_jac: torch.Tensor,
+                           values: torch.Tensor, ranges: torch.Tensor, loss: dict, out: Optional[dict],
+                           pose_partials: torch.Tensor, pose_grad: Optional[torch.Tensor], status: torch.Tensor,
+                           ws: torch.Tensor, stream=None, order: Optional[torch.Tensor] = None) -> None:
+    """Tracking pass: forward + POSE backward of the colour/depth loss in one launch."""
+    F = len(cams)
+    proj = gs_projected(n_gaussians, F, _ptr(rec, torch.float32, "rec"), 1,
+                        _ptr(pose_jac, torch.float32, "pose_jac"))
+    tiles = gs_tiles(values.numel(), ranges.numel() // 2, _ptr(values, torch.int32), None,
+                     _ptr(ranges, torch.int32), _ptr(order, torch.int32, "order", ranges.numel() // 2))
+    gl = _loss(loss)
+    img = _image(out) if out is not None else None
+    _check(lib.gs_render_fwd_bwd_pose(C.byref(proj), C.byref(tiles), F, cameras(cams), C.byref(gl), C.byref(opts),
+                                      C.byref(img) if img is not None else None,
+                                      _ptr(pose_partials, torch.float32, "pose_partials"),
+                                      _ptr(pose_grad, torch.float64, "pose_grad", 6 * F),
+                                      _ptr(status, torch.int32, "status", 4), _ptr(ws, torch.uint8, "ws"), ws.numel(),
+                                      _stream(stream)))
 
 
 def gs_pose_grad_reduce(partials: torch.Tensor, n_frames: int, per_frame: int, pose_grad: torch.Tensor,

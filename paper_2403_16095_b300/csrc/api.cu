@@ -314,6 +314,56 @@ gs_status gs_render_bwd(const gs_projected *proj, const gs_tiles *tiles, int n_f
                        "gs_render_bwd (projection adjoint)");
 }
 
+gs_status gs_render_fwd_bwd_pose(const gs_projected *proj, const gs_tiles *tiles, int n_frames, const gs_camera *cams,
+                                 const gs_loss *loss, const gs_opts *opts, gs_image *out, float *pose_partials,
+                                 double *pose_grad, const int32_t *status, void *ws, size_t ws_bytes,
+                                 gs_stream stream) {
+    GS_TRY(check_opts(opts));
+    if (opts->mode != GS_MODE_POSE) return fail(GS_ERR_INVALID_ARG, "the tracking pass needs POSE mode");
+    gs::FrameTable ft;
+    GS_TRY(make_frames(n_frames, cams, opts->tile, ft));
+    GS_TRY(check_proj(proj, n_frames));
+    GS_TRY(check_tiles(tiles, ft));
+    if (!status || !pose_partials) return fail(GS_ERR_INVALID_ARG, "status/pose_partials NULL");
+    if (!proj->pose_jac) return fail(GS_ERR_INVALID_ARG, "POSE mode needs projected.pose_jac");
+    if (!loss) return fail(GS_ERR_INVALID_ARG, "loss is NULL");
+    if (loss->w_unc != 0.f || loss->w_nu != 0.f || loss->w_align != 0.f)
+        return fail(GS_ERR_UNSUPPORTED, "the tracking pass supports colour and depth L1 terms only");
+    gs::LossParams lp{};
+    lp.fused = 1;
+    lp.w_color = loss->w_color; lp.w_depth = loss->w_depth; lp.unc_tau = loss->unc_tau;
+    lp.target_color = loss->target_color; lp.target_depth = loss->target_depth;
+    if (lp.w_color != 0.f && !lp.target_color) return fail(GS_ERR_INVALID_ARG, "colour loss needs target_color");
+    if (lp.w_depth != 0.f && !lp.target_depth) return fail(GS_ERR_INVALID_ARG, "depth loss needs target_depth");
+    gs::ImagePtrs ip{};
+    if (out) {
+        ip.color = out->color; ip.depth = out->depth; ip.nu_map = out->nu_map;
+        ip.T_final = out->T_final; ip.n_last = out->n_last;
+    }
+    const int N = proj->n_gaussians;
+    const int M = N * n_frames;
+    const int per_frame = gs_pose_partials_per_frame(GS_MODE_POSE, N, n_frames, cams, opts->tile);
+    const size_t need = bwd_ws_bytes(M, GS_MODE_POSE);
+    if (!ws || ws_bytes < need || !aligned(ws, 256))
+        return fail(GS_ERR_INVALID_ARG, "workspace %zu bytes < %zu needed (256-aligned)", ws_bytes, need);
+    unsigned *counters = reinterpret_cast<unsigned *>(static_cast<char *>(ws) + grad2d_bytes(M, GS_MODE_POSE));
+    cudaError_t e;
+    if (pose_grad && (e = cudaMemsetAsync(counters, 0, sizeof(unsigned) * n_frames, stream)) != cudaSuccess)
+        return cuda_status(e, "gs_render_fwd_bwd_pose memset");
+    for (int f = 0; f < n_frames; ++f) {
+        const int used = ft.f[f].tiles_x * ft.f[f].tiles_y;
+        if (used < per_frame) {
+            e = cudaMemsetAsync(pose_partials + ((size_t)f * per_frame + used) * 12, 0,
+                                sizeof(float) * 12 * (size_t)(per_frame - used), stream);
+            if (e != cudaSuccess) return cuda_status(e, "gs_render_fwd_bwd_pose memset");
+        }
+    }
+    return cuda_status(gs::launch_render_fused_pose(proj->rec, proj->pose_jac, tiles->values, tiles->ranges,
+                                                    tiles->order, ft, ip, lp, pose_partials, per_frame, pose_grad,
+                                                    counters, status, stream),
+                       "gs_render_fwd_bwd_pose");
+}
+
 gs_status gs_nu_accumulate(const gs_projected *proj, const gs_tiles *tiles, int n_frames, const gs_camera *cams,
                            const float *obs_depth, const gs_image *fwd, double *nu_num, uint32_t *nu_cnt,
                            int32_t *dominant, const int32_t *status, gs_stream stream) {

@@ -125,6 +125,15 @@ class Rasterizer:
                         obs_depth, self.img, dL, loss, grads, self.pose_partials,
                         self.pose_grad if fused_pose else None, self.status, self.bwd_ws, stream, order=self.order)
 
+    def fwd_bwd_pose(self, loss: dict, images: bool = False, fused_pose: bool = True, stream=None) -> None:
+        """Tracking pass (POSE mode): forward + backward of the colour/depth loss in
+        one launch per tile; with images=True the tracking channels are written
+        too (bit-identical to forward() + backward())."""
+        out = {k: self.img[k] for k in ("color", "depth", "nu_map", "T_final", "n_last")} if images else None
+        A.gs_render_fwd_bwd_pose(self.N, self.cams, self.opts, self.rec, self.jac, self.values, self.ranges, loss,
+                                 out, self.pose_partials, self.pose_grad if fused_pose else None, self.status,
+                                 self.bwd_ws, stream, order=self.order)
+
     def nu_accumulate(self, obs_depth: torch.Tensor, nu_num: torch.Tensor, nu_cnt: torch.Tensor,
                       dominant: Optional[torch.Tensor] = None, stream=None) -> None:
         """Eq. 13: add every dominated pixel of this batch's frames to nu_num
@@ -316,11 +325,14 @@ class Tracker:
 
     def __init__(self, g, cam, tile: int = 16, iters: int = 30, lam=(0.2, 1.0), unc_tau: float = 0.025,
                  lr_rot: float = 0.0015, lr_trans: float = 0.00215, jclamp: float = 1.3, graph: bool = True,
-                 capacity: Optional[int] = None, timing: bool = False):
+                 capacity: Optional[int] = None, timing: bool = False, fused: bool = True):
         self.g = g
         self.cam = cam
         self.iters = iters
         self.graph_enabled = graph
+        # fused: forward and backward in one launch per tile (gs_render_fwd_bwd_pose);
+        # otherwise gs_render_fwd then gs_render_bwd (same results, bit for bit)
+        self.fused = fused
         # optional per-iteration CUDA events around each backward launch (recorded
         # inside the captured graph as event nodes), for per-kernel timing
         self.timing = timing
@@ -346,19 +358,24 @@ class Tracker:
         r = self.rast
         r.project(self.g, self.T_cw, stream)
         r.bin(stream)
-        r.forward(self.target_depth, stream)
-        if self.bwd_events is not None:
-            self.bwd_events[it][0].record(stream)
-        r.backward(obs_depth=self.target_depth, loss=self.loss, stream=stream)  # + fused pose reduction
+        if self.fused:
+            if self.bwd_events is not None:
+                self.bwd_events[it][0].record(stream)
+            r.fwd_bwd_pose(self.loss, stream=stream)  # + fused pose reduction
+        else:
+            r.forward(self.target_depth, stream)
+            if self.bwd_events is not None:
+                self.bwd_events[it][0].record(stream)
+            r.backward(obs_depth=self.target_depth, loss=self.loss, stream=stream)  # + fused pose reduction
         if self.bwd_events is not None:
             self.bwd_events[it][1].record(stream)
         A.gs_pose_adam_step(self.state, r.pose_grad, self.T_cw, 1, self.adam, r.status, stream)
 
     def kernel_launches_per_iteration(self) -> int:
         """libgs kernels one iteration launches (memsets not counted): project;
-        tile count, scan, fill, per-tile sort; forward; backward (with the fused
-        pose reduction); Adam step."""
-        return 1 + 4 + 1 + 1 + 1
+        tile count, scan, fill, per-tile sort; forward + backward as one fused
+        launch, or as two (each with the fused pose reduction); Adam step."""
+        return 1 + 4 + (1 if self.fused else 2) + 1
 
     def _capture(self):
         """Capture all ``iters`` iterations of a frame in one CUDA graph."""
@@ -371,8 +388,9 @@ class Tracker:
                 self._iteration(self.stream, it)
 
     def backward_ms(self) -> list:
-        """Per-iteration duration of the backward kernel in the last frame (needs
-        timing=True and a completed frame)."""
+        """Per-iteration duration of the backward launch in the last frame (the
+        fused forward + backward launch when fused; needs timing=True and a
+        completed frame)."""
         return [a.elapsed_time(b) for a, b in self.bwd_events]
 
     def set_frame(self, target_color: torch.Tensor, target_depth: torch.Tensor, T_init: torch.Tensor) -> None:

@@ -122,3 +122,50 @@ def test_full_size_pose_gradient_matches_oracle(track_full):
     rel = np.abs(got - og["pose"]).max() / np.abs(og["pose"]).max()
     print("full-size pose gradient", got, og["pose"], rel)
     assert rel < 5e-5  # measured 5.3e-6 on a B300
+
+
+def test_fused_tracking_pass_equals_forward_then_backward(track_full):
+    """gs_render_fwd_bwd_pose (one launch per tile) reproduces gs_render_fwd +
+    gs_render_bwd (POSE, tracking loss) bit for bit: the tracking channels and
+    the FP64 pose gradient, at 640x480 / 300k in the benchmark's configuration."""
+    from paper_2403_16095_b300 import Rasterizer
+    from paper_2403_16095_b300 import _abi as A
+    sc, cam, T, tc, td = track_full
+    obs = torch.from_numpy(td).cuda().reshape(-1)
+    loss = dict(w_color=0.2, w_depth=1.0, unc_tau=0.025, target_color=torch.from_numpy(tc).cuda().reshape(-1),
+                target_depth=obs)
+    res = []
+    for fused in (False, True):
+        r = Rasterizer([cam], sc.n, tile=16, mode=A.GS_MODE_POSE, channels="track")
+        r.render(to_gpu_gaussians(sc), poses_gpu(T), obs)
+        for k in r.img:
+            r.img[k].fill_(-1 if r.img[k].dtype == torch.int32 else float("nan"))
+        r.pose_grad.zero_()
+        if fused:
+            r.fwd_bwd_pose(loss, images=True)
+        else:
+            r.forward(obs)
+            r.backward(obs_depth=obs, loss=loss)
+        torch.cuda.synchronize()
+        assert r.read_status()[0] == 0
+        res.append(({k: v.clone() for k, v in r.img.items()}, r.pose_grad.clone()))
+    for k in res[0][0]:
+        assert torch.equal(res[0][0][k], res[1][0][k]), k
+    assert torch.equal(res[0][1], res[1][1])
+    # losses beyond colour and depth are refused by the fused pass
+    with pytest.raises(A.GsError):
+        r.fwd_bwd_pose(dict(loss, w_align=0.1))
+
+
+def test_tracker_fused_equals_unfused(room_small):
+    from paper_2403_16095_b300 import Tracker
+    sc, cam, poses = room_small
+    g = to_gpu_gaussians(sc)
+    tcol, tdep = _targets(sc, cam, poses[0])
+    T0 = torch.from_numpy(synth.jitter_pose(poses[0], seed=6))
+    out = []
+    for fused in (False, True):
+        tr = Tracker(g, cam, iters=10, graph=True, fused=fused)
+        tr.prepare(tcol, tdep, T0)
+        out.append(tr.track(tcol, tdep, T0))
+    assert torch.equal(out[0], out[1])
