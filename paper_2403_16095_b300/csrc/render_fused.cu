@@ -78,16 +78,16 @@ __global__ void __launch_bounds__(TILE *TILE)
 
     // stages list entries [lo, hi) of the tile into shared memory
     auto stage = [&](int lo, int hi) {
-        if (tid < hi - lo) {
-            const uint32_t r = values[lo + tid];
+        for (int i = tid; i < hi - lo; i += NT) {
+            const uint32_t r = values[lo + i];
             const float4 *R = rec + (size_t)r * 4;
-            s_a[tid] = R[0];
-            s_b[tid] = R[1];
-            s_c[tid] = R[2];
-            s_r[tid] = reinterpret_cast<const int4 *>(R)[3];
+            s_a[i] = R[0];
+            s_b[i] = R[1];
+            s_c[i] = R[2];
+            s_r[i] = reinterpret_cast<const int4 *>(R)[3];
             const float4 *J = jac + (size_t)r * 9;
 #pragma unroll
-            for (int q = 0; q < 9; ++q) s_j[tid * 9 + q] = J[q];
+            for (int q = 0; q < 9; ++q) s_j[i * 9 + q] = J[q];
         }
     };
 
