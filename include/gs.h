@@ -59,7 +59,7 @@ extern "C" {
 #endif
 
 #define GS_MAX_FRAMES 64
-#define GS_ABI_VERSION 5
+#define GS_ABI_VERSION 6
 
 typedef struct CUstream_st *gs_stream; /* a cudaStream_t; NULL = legacy default stream */
 
@@ -318,10 +318,14 @@ gs_status gs_render_bwd(const gs_projected *proj, const gs_tiles *tiles, int n_f
  * (GS_ERR_UNSUPPORTED otherwise). `out` may be NULL, or name any of color,
  * depth, nu_map, T_final and n_last to have them written as well (its other
  * members are ignored). pose_partials, pose_grad and ws as for gs_render_bwd
- * in POSE mode (ws: gs_render_bwd_workspace_size(records, GS_MODE_POSE)).    */
+ * in POSE mode (ws: gs_render_bwd_workspace_size(records, GS_MODE_POSE)).
+ * If adam_state is not NULL (then pose_grad, adam and T_cw are required), the
+ * CTA that reduces frame f's pose gradient also applies gs_pose_adam_step to
+ * frame f (same arithmetic), rewriting T_cw for the next iteration.          */
 gs_status gs_render_fwd_bwd_pose(const gs_projected *proj, const gs_tiles *tiles, int n_frames,
                                  const gs_camera *cams, const gs_loss *loss, const gs_opts *opts,
                                  gs_image *out, float *pose_partials, double *pose_grad,
+                                 double *adam_state, const gs_adam *adam, float *T_cw,
                                  const int32_t *status, void *ws, size_t ws_bytes, gs_stream stream);
 
 /* Per-Gaussian depth uncertainty, Eq. 13 (Sec. 3.2), accumulation half. Each

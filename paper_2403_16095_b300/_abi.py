@@ -100,7 +100,7 @@ EXPORTS = ("gs_abi_version", "gs_last_error", "gs_project", "gs_bin_tiles_worksp
            "gs_render_bwd", "gs_render_fwd_bwd_pose", "gs_project_bf16", "gs_spatial_order_workspace_size", "gs_spatial_order",
            "gs_pack_bf16", "gs_nu_accumulate", "gs_nu_finalize", "gs_pose_grad_reduce", "gs_pose_adam_step")
 GS_NOALLOC_MAX_PAIRS = 1 << 19
-ABI_VERSION = 5  # GS_ABI_VERSION of the gs.h these structures mirror
+ABI_VERSION = 6  # GS_ABI_VERSION of the gs.h these structures mirror
 
 
 def _load():
@@ -138,7 +138,8 @@ def _load():
                                   C.POINTER(gs_grads), _vp, _vp, _vp, _vp, C.c_size_t, _vp]
     lib.gs_render_fwd_bwd_pose.argtypes = [C.POINTER(gs_projected), C.POINTER(gs_tiles), C.c_int,
                                            C.POINTER(gs_camera), C.POINTER(gs_loss), C.POINTER(gs_opts),
-                                           C.POINTER(gs_image), _vp, _vp, _vp, _vp, C.c_size_t, _vp]
+                                           C.POINTER(gs_image), _vp, _vp, _vp, C.POINTER(gs_adam), _vp, _vp, _vp,
+                                           C.c_size_t, _vp]
     lib.gs_nu_accumulate.argtypes = [C.POINTER(gs_projected), C.POINTER(gs_tiles), C.c_int, C.POINTER(gs_camera),
                                      _vp, C.POINTER(gs_image), _vp, _vp, _vp, _vp, _vp]
     lib.gs_nu_finalize.argtypes = [C.c_int, _vp, _vp, _vp, C.c_float, C.c_float, _vp, _vp, _vp, _vp]
@@ -432,8 +433,11 @@ def _loss(loss: dict) -> gs_loss:
 def gs_render_fwd_bwd_pose(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tensor, pose_jac: torch.Tensor,
                            values: torch.Tensor, ranges: torch.Tensor, loss: dict, out: Optional[dict],
                            pose_partials: torch.Tensor, pose_grad: Optional[torch.Tensor], status: torch.Tensor,
-                           ws: torch.Tensor, stream=None, order: Optional[torch.Tensor] = None) -> None:
-    """Tracking pass: forward + POSE backward of the colour/depth loss in one launch."""
+                           ws: torch.Tensor, stream=None, order: Optional[torch.Tensor] = None,
+                           adam_state: Optional[torch.Tensor] = None, adam: Optional[gs_adam] = None,
+                           T_cw: Optional[torch.Tensor] = None) -> None:
+    """Tracking pass: forward + POSE backward of the colour/depth loss in one launch,
+    optionally followed (in the same launch) by the Adam step on the pose."""
     F = len(cams)
     proj = gs_projected(n_gaussians, F, _ptr(rec, torch.float32, "rec"), 1,
                         _ptr(pose_jac, torch.float32, "pose_jac"))
@@ -445,6 +449,9 @@ def gs_render_fwd_bwd_pose(n_gaussians: int, cams, opts: gs_opts, rec: torch.Ten
                                       C.byref(img) if img is not None else None,
                                       _ptr(pose_partials, torch.float32, "pose_partials"),
                                       _ptr(pose_grad, torch.float64, "pose_grad", 6 * F),
+                                      _ptr(adam_state, torch.float64, "adam_state", GS_POSE_STATE_DOUBLES * F),
+                                      C.byref(adam) if adam is not None else None,
+                                      _ptr(T_cw, torch.float32, "T_cw", 12 * F),
                                       _ptr(status, torch.int32, "status", 4), _ptr(ws, torch.uint8, "ws"), ws.numel(),
                                       _stream(stream)))
 

@@ -316,8 +316,8 @@ gs_status gs_render_bwd(const gs_projected *proj, const gs_tiles *tiles, int n_f
 
 gs_status gs_render_fwd_bwd_pose(const gs_projected *proj, const gs_tiles *tiles, int n_frames, const gs_camera *cams,
                                  const gs_loss *loss, const gs_opts *opts, gs_image *out, float *pose_partials,
-                                 double *pose_grad, const int32_t *status, void *ws, size_t ws_bytes,
-                                 gs_stream stream) {
+                                 double *pose_grad, double *adam_state, const gs_adam *adam, float *T_cw,
+                                 const int32_t *status, void *ws, size_t ws_bytes, gs_stream stream) {
     GS_TRY(check_opts(opts));
     if (opts->mode != GS_MODE_POSE) return fail(GS_ERR_INVALID_ARG, "the tracking pass needs POSE mode");
     gs::FrameTable ft;
@@ -329,6 +329,8 @@ gs_status gs_render_fwd_bwd_pose(const gs_projected *proj, const gs_tiles *tiles
     if (!loss) return fail(GS_ERR_INVALID_ARG, "loss is NULL");
     if (loss->w_unc != 0.f || loss->w_nu != 0.f || loss->w_align != 0.f)
         return fail(GS_ERR_UNSUPPORTED, "the tracking pass supports colour and depth L1 terms only");
+    if (adam_state && (!pose_grad || !adam || !T_cw))
+        return fail(GS_ERR_INVALID_ARG, "the pose update needs pose_grad, adam and T_cw");
     gs::LossParams lp{};
     lp.fused = 1;
     lp.w_color = loss->w_color; lp.w_depth = loss->w_depth; lp.unc_tau = loss->unc_tau;
@@ -358,9 +360,10 @@ gs_status gs_render_fwd_bwd_pose(const gs_projected *proj, const gs_tiles *tiles
             if (e != cudaSuccess) return cuda_status(e, "gs_render_fwd_bwd_pose memset");
         }
     }
+    const gs_adam ad = adam ? *adam : gs_adam{};
     return cuda_status(gs::launch_render_fused_pose(proj->rec, proj->pose_jac, tiles->values, tiles->ranges,
                                                     tiles->order, ft, ip, lp, pose_partials, per_frame, pose_grad,
-                                                    counters, status, stream),
+                                                    counters, adam_state, ad, T_cw, status, stream),
                        "gs_render_fwd_bwd_pose");
 }
 

@@ -12,12 +12,16 @@
 //   - the second staging of the last batch: records and pose Jacobians staged
 //     for the forward stay in shared memory for the backward when the batch
 //     boundaries coincide, i.e. whenever the walk fits in one batch;
-//   - one launch and one tail of idle SMs.
+//   - one launch and one tail of idle SMs;
+//   - optionally the Adam launch: the CTA that reduces a frame's pose gradient
+//     also applies the pose update (the same warp routine as
+//     gs_pose_adam_step).
 // The per-pixel arithmetic is the same as in the two kernels (same helpers,
 // same order), so images and pose gradients are bit-identical to them.
 #include "gs_internal.cuh"
 #include "blend_common.cuh"
 #include "dfloat.cuh"
+#include "pose_adam.cuh"
 
 #include <atomic>
 
@@ -43,7 +47,8 @@ __global__ void __launch_bounds__(TILE *TILE)
                         const uint32_t *__restrict__ values, const uint2 *__restrict__ ranges,
                         const uint32_t *__restrict__ order, FrameTable ft, ImagePtrs out, LossParams lp,
                         float *__restrict__ pose_partials, int per_frame, double *__restrict__ pose_grad,
-                        unsigned *__restrict__ counters, const int32_t *__restrict__ status) {
+                        unsigned *__restrict__ counters, double *__restrict__ adam_state, gs_adam adam,
+                        float *__restrict__ T_cw, const int32_t *__restrict__ status) {
     using SM = FusedSmem<TILE>;
     constexpr int NT = SM::NT;
     constexpr int BATCH = SM::BATCH;
@@ -234,15 +239,23 @@ __global__ void __launch_bounds__(TILE *TILE)
     float *part_f = pose_partials + (size_t)f * per_frame * 12;
     __syncthreads();  // the tail may reuse the staging bytes
     cta_pose_partial(acc, part_f + (size_t)lt * 12, s_wdf);
-    if (pose_grad)
+    if (pose_grad) {
         last_cta_pose_reduce(part_f, per_frame, fd.tiles_x * fd.tiles_y, counters + f, pose_grad + 6 * f, s_red,
                              &s_flag);
+        if (adam_state && s_flag) {  // this CTA holds the frame's pose gradient
+            __syncthreads();
+            if (warp == 0)
+                pose_adam_warp(adam_state + (size_t)f * GS_POSE_STATE_DOUBLES, pose_grad + 6 * f, T_cw + 12 * f,
+                               adam);
+        }
+    }
 }
 
 template <int TILE>
 cudaError_t launch_tile(const float4 *rec, const float4 *jac, const uint32_t *values, const uint2 *ranges,
                         const uint32_t *order, const FrameTable &ft, const ImagePtrs &out, const LossParams &lp,
-                        float *pp, int per_frame, double *pg, unsigned *cnt, const int32_t *status, cudaStream_t s) {
+                        float *pp, int per_frame, double *pg, unsigned *cnt, double *adam_state, const gs_adam &adam,
+                        float *T_cw, const int32_t *status, cudaStream_t s) {
     // raise the dynamic shared-memory limit once per device (a host-side
     // attribute; the first call happens outside any stream capture)
     static std::atomic<uint64_t> done{0};
@@ -256,7 +269,8 @@ cudaError_t launch_tile(const float4 *rec, const float4 *jac, const uint32_t *va
         if (dev < 64) done.fetch_or(1ull << dev);
     }
     k_render_fused_pose<TILE><<<ft.total_tiles, TILE * TILE, smem, s>>>(rec, jac, values, ranges, order, ft, out, lp,
-                                                                        pp, per_frame, pg, cnt, status);
+                                                                        pp, per_frame, pg, cnt, adam_state, adam,
+                                                                        T_cw, status);
     return cudaGetLastError();
 }
 
@@ -265,15 +279,16 @@ cudaError_t launch_tile(const float4 *rec, const float4 *jac, const uint32_t *va
 cudaError_t launch_render_fused_pose(const float *rec, const float *jac, const uint32_t *values,
                                      const uint32_t *ranges, const uint32_t *order, const FrameTable &ft,
                                      const ImagePtrs &out, const LossParams &lp, float *pose_partials, int per_frame,
-                                     double *pose_grad, unsigned *counters, const int32_t *status, cudaStream_t s) {
+                                     double *pose_grad, unsigned *counters, double *adam_state, const gs_adam &adam,
+                                     float *T_cw, const int32_t *status, cudaStream_t s) {
     if (ft.total_tiles == 0) return cudaSuccess;
     const float4 *r4 = reinterpret_cast<const float4 *>(rec);
     const float4 *j4 = reinterpret_cast<const float4 *>(jac);
     const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
     switch (ft.tile) {
-        case 8: return launch_tile<8>(r4, j4, values, rg, order, ft, out, lp, pose_partials, per_frame, pose_grad, counters, status, s);
-        case 16: return launch_tile<16>(r4, j4, values, rg, order, ft, out, lp, pose_partials, per_frame, pose_grad, counters, status, s);
-        case 32: return launch_tile<32>(r4, j4, values, rg, order, ft, out, lp, pose_partials, per_frame, pose_grad, counters, status, s);
+        case 8: return launch_tile<8>(r4, j4, values, rg, order, ft, out, lp, pose_partials, per_frame, pose_grad, counters, adam_state, adam, T_cw, status, s);
+        case 16: return launch_tile<16>(r4, j4, values, rg, order, ft, out, lp, pose_partials, per_frame, pose_grad, counters, adam_state, adam, T_cw, status, s);
+        case 32: return launch_tile<32>(r4, j4, values, rg, order, ft, out, lp, pose_partials, per_frame, pose_grad, counters, adam_state, adam, T_cw, status, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -125,14 +125,17 @@ class Rasterizer:
                         obs_depth, self.img, dL, loss, grads, self.pose_partials,
                         self.pose_grad if fused_pose else None, self.status, self.bwd_ws, stream, order=self.order)
 
-    def fwd_bwd_pose(self, loss: dict, images: bool = False, fused_pose: bool = True, stream=None) -> None:
+    def fwd_bwd_pose(self, loss: dict, images: bool = False, fused_pose: bool = True, stream=None,
+                     adam_state=None, adam=None, T_cw=None) -> None:
         """Tracking pass (POSE mode): forward + backward of the colour/depth loss in
         one launch per tile; with images=True the tracking channels are written
-        too (bit-identical to forward() + backward())."""
+        too (bit-identical to forward() + backward()); with adam_state (and adam,
+        T_cw) the same launch also applies the pose Adam step."""
         out = {k: self.img[k] for k in ("color", "depth", "nu_map", "T_final", "n_last")} if images else None
         A.gs_render_fwd_bwd_pose(self.N, self.cams, self.opts, self.rec, self.jac, self.values, self.ranges, loss,
                                  out, self.pose_partials, self.pose_grad if fused_pose else None, self.status,
-                                 self.bwd_ws, stream, order=self.order)
+                                 self.bwd_ws, stream, order=self.order, adam_state=adam_state, adam=adam,
+                                 T_cw=T_cw)
 
     def nu_accumulate(self, obs_depth: torch.Tensor, nu_num: torch.Tensor, nu_cnt: torch.Tensor,
                       dominant: Optional[torch.Tensor] = None, stream=None) -> None:
@@ -358,24 +361,28 @@ class Tracker:
         r = self.rast
         r.project(self.g, self.T_cw, stream)
         r.bin(stream)
-        if self.fused:
-            if self.bwd_events is not None:
-                self.bwd_events[it][0].record(stream)
-            r.fwd_bwd_pose(self.loss, stream=stream)  # + fused pose reduction
+        ev = self.bwd_events[it] if self.bwd_events is not None else None
+        if self.fused:  # forward, backward, pose reduction and Adam step in one launch
+            if ev:
+                ev[0].record(stream)
+            r.fwd_bwd_pose(self.loss, stream=stream, adam_state=self.state, adam=self.adam, T_cw=self.T_cw)
+            if ev:
+                ev[1].record(stream)
         else:
             r.forward(self.target_depth, stream)
-            if self.bwd_events is not None:
-                self.bwd_events[it][0].record(stream)
+            if ev:
+                ev[0].record(stream)
             r.backward(obs_depth=self.target_depth, loss=self.loss, stream=stream)  # + fused pose reduction
-        if self.bwd_events is not None:
-            self.bwd_events[it][1].record(stream)
-        A.gs_pose_adam_step(self.state, r.pose_grad, self.T_cw, 1, self.adam, r.status, stream)
+            if ev:
+                ev[1].record(stream)
+            A.gs_pose_adam_step(self.state, r.pose_grad, self.T_cw, 1, self.adam, r.status, stream)
 
     def kernel_launches_per_iteration(self) -> int:
         """libgs kernels one iteration launches (memsets not counted): project;
-        tile count, scan, fill, per-tile sort; forward + backward as one fused
-        launch, or as two (each with the fused pose reduction); Adam step."""
-        return 1 + 4 + (1 if self.fused else 2) + 1
+        tile count, scan, fill, per-tile sort; then either the tracking pass
+        (forward, backward, pose reduction and Adam step in one launch) or the
+        forward, the backward (with the pose reduction) and the Adam step."""
+        return 1 + 4 + (1 if self.fused else 3)
 
     def _capture(self):
         """Capture all ``iters`` iterations of a frame in one CUDA graph."""
