@@ -105,7 +105,8 @@ typedef struct {
  * rec: GS_REC_FLOATS floats per record, 16-byte aligned:
  *   [0..1] mean2d (pixels)   [2..4] conic (A, B, C): q = A dx^2 + 2B dx dy + C dy^2
  *   [5] opacity  [6] depth z  [7] nu  [8..10] RGB  [11] radius (pixels)
- *   [12..15] int32 inclusive pixel rect x0, y0, x1, y1 (x0 > x1: culled).       */
+ *   [12..15] int32 inclusive pixel rect x0, y0, x1, y1 (x0 > x1: culled; the
+ *   other fields of a culled record are not written).                        */
 #define GS_REC_FLOATS 16
 #define GS_JAC_FLOATS 36
 typedef struct {

@@ -178,12 +178,10 @@ __device__ __forceinline__ bool geometry(const Src &src, const typename Src::Rec
     return true;
 }
 
+// A culled record gets only its empty rect (16 B of the 64): at 5M Gaussians
+// most records are culled, and nothing reads their other fields.
 __device__ __forceinline__ void write_culled(float *rec, int *touched, size_t r) {
-    float4 *o = reinterpret_cast<float4 *>(rec + r * kRecFloats);
-    o[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-    o[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-    o[2] = make_float4(0.f, 0.f, 0.f, 0.f);
-    reinterpret_cast<int4 *>(o)[3] = make_int4(1, 1, 0, 0);
+    reinterpret_cast<int4 *>(rec + r * kRecFloats)[3] = make_int4(1, 1, 0, 0);
     touched[r] = 0;
 }
 
