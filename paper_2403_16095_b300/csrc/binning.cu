@@ -278,18 +278,76 @@ __device__ bool cta_radix_pass(const uint64_t *src, uint64_t *dst, int n, int sh
 }
 
 // ---------------------------------------------------------------------------
+// Bitonic sort of n <= 256 K keys by one CTA of kThreads threads with the keys
+// in registers: thread t holds positions t K .. t K + K - 1 (padding = the
+// all-ones key, which sorts last). A stage with stride below K stays in the
+// thread, one below 32 K is a warp shuffle, and only strides of 32 K or more go
+// through shared memory -- the sort is bound by shared-memory bandwidth when
+// every stage goes through it. Leaves the sorted keys in s_a[0, n).
+template <int K>
+__device__ void cta_sort_regs(const uint64_t *keys, int n, uint64_t *s_a) {
+    constexpr int NP = kThreads * K;
+    const int t = threadIdx.x;
+    uint64_t x[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int p = t * K + j;
+        x[j] = p < n ? keys[p] : ~0ull;
+    }
+    for (int size = 2; size <= NP; size <<= 1) {
+        for (int stride = size >> 1; stride >= K; stride >>= 1) {
+            if (stride >= 32 * K) {  // partner in another warp
+#pragma unroll
+                for (int j = 0; j < K; ++j) s_a[t * K + j] = x[j];
+                __syncthreads();
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    const int p = t * K + j;
+                    const uint64_t y = s_a[p ^ stride];
+                    const bool keep_min = ((p & stride) == 0) == ((p & size) == 0);
+                    x[j] = keep_min ? (y < x[j] ? y : x[j]) : (y > x[j] ? y : x[j]);
+                }
+                __syncthreads();
+            } else if (stride >= K) {  // partner in another lane of the warp
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    const int p = t * K + j;
+                    const uint64_t y = __shfl_xor_sync(0xffffffffu, x[j], stride / K);
+                    const bool keep_min = ((p & stride) == 0) == ((p & size) == 0);
+                    x[j] = keep_min ? (y < x[j] ? y : x[j]) : (y > x[j] ? y : x[j]);
+                }
+            }
+        }
+        // strides below K: both elements in this thread (compile-time indices)
+#pragma unroll
+        for (int stride = K / 2; stride > 0; stride >>= 1) {
+            if (stride >= size) continue;
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                if (j & stride) continue;
+                const uint64_t a = x[j], b = x[j + stride];
+                const bool up = ((t * K + j) & size) == 0;
+                if ((a > b) == up) {
+                    x[j] = b;
+                    x[j + stride] = a;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) s_a[t * K + j] = x[j];
+    __syncthreads();
+}
+
 // k_tile_sort: heaviest tiles first when the launch order is given. With the
 // order, tiles of fewer than kWarpSortKeys entries (most of them) are sorted one
 // per warp, 8 per CTA, with warp barriers only; the others take one CTA each.
-// Buckets of at most kSmemKeys keys are sorted in shared memory by a bitonic
-// network (padding = the all-ones key, which sorts last; low keys are unique
-// within a bucket, so the result is the same as a stable radix sort).
-// Warp w owns the contiguous segment [w S, (w + 1) S), S = padded size / 8, and
-// the pairs whose elements lie in it: a stage whose stride is below S stays
-// inside each segment and needs only a warp barrier, so a 256-key bucket takes
-// 9 CTA barriers instead of 36. Larger buckets take a stable LSD radix sort
-// that ping-pongs in global memory.
-__global__ void __launch_bounds__(kThreads, 8)
+// Bitonic networks (low keys are unique within a bucket, so the result is the
+// same as a stable radix sort). A CTA sorts its bucket with the keys in
+// registers (cta_sort_regs); buckets
+// of more than kSmemKeys keys take a stable LSD radix sort that ping-pongs in
+// global memory.
+__global__ void __launch_bounds__(kThreads, 4)
     k_tile_sort(uint64_t *low_keys, uint64_t *tmp, const uint32_t *__restrict__ ranges,
                 const uint32_t *__restrict__ order, const int *__restrict__ misc, int n_tiles,
                 uint32_t *__restrict__ values, uint64_t *__restrict__ keys_out, int rec_bits,
@@ -341,35 +399,15 @@ __global__ void __launch_bounds__(kThreads, 8)
     const int n = (int)(e - s);
     if (n <= 0) return;
     if (n <= kSmemKeys) {
-        int np = 16;
+        int np = kThreads;
         while (np < n) np <<= 1;
-        for (int i = tid; i < np; i += kThreads) s_a[i] = i < n ? low_keys[s + i] : ~0ull;
-        __syncthreads();
-        const int lane = tid & 31, warp = tid >> 5;
-        const int seg = np / kWarps;            // elements per warp segment (>= 2)
-        const int seg_pairs = seg >> 1;         // pairs per warp and stage
-        for (int size = 2; size <= np; size <<= 1)
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                const bool cross = stride >= seg;  // pairs span two warps' segments
-                for (int u = lane; u < seg_pairs; u += 32) {
-                    const int t = warp * seg_pairs + u;
-                    const int i = ((t & ~(stride - 1)) << 1) | (t & (stride - 1));  // lower index of pair t
-                    const int j = i + stride;
-                    const uint64_t x = s_a[i], y = s_a[j];
-                    const bool up = (i & size) == 0;
-                    if ((x > y) == up) {
-                        s_a[i] = y;
-                        s_a[j] = x;
-                    }
-                }
-                // a CTA barrier where this stage or the next one crosses segments
-                const int next_stride = stride > 1 ? (stride >> 1) : size;
-                if (cross || next_stride >= seg)
-                    __syncthreads();
-                else
-                    __syncwarp();
-            }
-        __syncthreads();
+        switch (np / kThreads) {
+            case 1: cta_sort_regs<1>(low_keys + s, n, s_a); break;
+            case 2: cta_sort_regs<2>(low_keys + s, n, s_a); break;
+            case 4: cta_sort_regs<4>(low_keys + s, n, s_a); break;
+            default: cta_sort_regs<8>(low_keys + s, n, s_a); break;
+        }
+        // cta_sort_regs leaves the sorted keys in s_a[0, n)
         for (int i = tid; i < n; i += kThreads) {
             const uint64_t k = s_a[i];
             values[s + i] = (uint32_t)k;
