@@ -169,3 +169,38 @@ def test_tracker_fused_equals_unfused(room_small):
         tr.prepare(tcol, tdep, T0)
         out.append(tr.track(tcol, tdep, T0))
     assert torch.equal(out[0], out[1])
+
+
+def test_tracking_pass_two_frames_with_adam_equals_separate_calls(room_small):
+    """The tracking pass over a batch of two frames (different poses, one launch)
+    gives each frame the same pose gradient and the same Adam update as the
+    separate forward, backward and gs_pose_adam_step calls."""
+    from paper_2403_16095_b300 import Rasterizer
+    from paper_2403_16095_b300 import _abi as A
+    from paper_2403_16095_b300.raster import pose_state
+    sc, cam, poses = room_small
+    g = to_gpu_gaussians(sc)
+    tgt = [_targets(sc, cam, poses[f]) for f in (0, 2)]
+    tc = torch.cat([t[0].reshape(-1) for t in tgt])
+    td = torch.cat([t[1].reshape(-1) for t in tgt])
+    T0 = np.stack([synth.jitter_pose(poses[f], seed=40 + f) for f in (0, 2)])
+    loss = dict(w_color=0.2, w_depth=1.0, unc_tau=0.025, target_color=tc, target_depth=td)
+    adam = A.gs_adam(0.0015, 0.00215, 0.9, 0.999, 1e-8)
+    out = []
+    for fused in (False, True):
+        r = Rasterizer([cam, cam], sc.n, tile=16, mode=A.GS_MODE_POSE, channels="track")
+        Tt = poses_gpu(T0).clone()
+        state = pose_state(torch.from_numpy(T0).cuda()).contiguous()
+        r.render(g, Tt, td)
+        if fused:
+            r.fwd_bwd_pose(loss, adam_state=state, adam=adam, T_cw=Tt)
+        else:
+            r.forward(td)
+            r.backward(obs_depth=td, loss=loss)
+            A.gs_pose_adam_step(state, r.pose_grad, Tt, 2, adam, r.status)
+        torch.cuda.synchronize()
+        assert r.read_status()[0] == 0
+        out.append((r.pose_grad.clone(), state.clone(), Tt.clone()))
+    for a, b in zip(out[0], out[1]):
+        assert torch.equal(a, b)
+    assert float(out[0][0][0].abs().max()) > 0 and float(out[0][0][1].abs().max()) > 0
