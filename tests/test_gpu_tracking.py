@@ -204,3 +204,48 @@ def test_tracking_pass_two_frames_with_adam_equals_separate_calls(room_small):
     for a, b in zip(out[0], out[1]):
         assert torch.equal(a, b)
     assert float(out[0][0][0].abs().max()) > 0 and float(out[0][0][1].abs().max()) > 0
+
+
+@pytest.mark.parametrize("fused", [True, False])
+def test_tracker_recovers_from_pair_overflow(room_small, fused):
+    """A tracker whose pair buffer is far too small: the first attempt overflows
+    (device status, every later kernel of the frame no-ops), the buffer grows,
+    the graph is recaptured and the frame is tracked again from its start pose;
+    the result equals that of a tracker sized correctly up front."""
+    from paper_2403_16095_b300 import Tracker
+    sc, cam, poses = room_small
+    g = to_gpu_gaussians(sc)
+    tcol, tdep = _targets(sc, cam, poses[1])
+    T0 = torch.from_numpy(synth.jitter_pose(poses[1], seed=9))
+    small = Tracker(g, cam, iters=10, graph=True, fused=fused, capacity=64)
+    got = small.track(tcol, tdep, T0)
+    assert small.rast.capacity > 64
+    ref = Tracker(g, cam, iters=10, graph=True, fused=fused)
+    ref.prepare(tcol, tdep, T0)
+    assert torch.equal(got, ref.track(tcol, tdep, T0))
+
+
+def test_tracking_pass_with_every_gaussian_culled():
+    """All Gaussians behind the camera: the tracking pass renders nothing, the
+    pose gradient is exactly zero, and the Adam step leaves the pose unchanged."""
+    from paper_2403_16095_b300 import Rasterizer
+    from paper_2403_16095_b300 import _abi as A
+    from paper_2403_16095_b300.raster import pose_state
+    sc, _, _ = synth.tiny_scene(n=200, seed=1205)
+    behind = synth.Scene(sc.means * np.float32([1, 1, -1]), sc.log_scales, sc.quats, sc.opacity_logit, sc.colors,
+                         sc.nu)
+    cam = synth.Camera(64, 48, 50.0, 50.0, 32.0, 24.0)
+    T = np.c_[np.eye(3), np.zeros(3)]
+    r = Rasterizer([cam], behind.n, tile=16, mode=A.GS_MODE_POSE, channels="track")
+    Tt = poses_gpu(T).clone()
+    r.render(to_gpu_gaussians(behind), Tt)
+    tc = torch.rand(3 * 64 * 48, device="cuda")
+    td = torch.rand(64 * 48, device="cuda") + 1.0
+    state = pose_state(torch.from_numpy(T).cuda()).contiguous()
+    r.fwd_bwd_pose(dict(w_color=0.2, w_depth=1.0, unc_tau=0.025, target_color=tc, target_depth=td), images=True,
+                   adam_state=state, adam=A.gs_adam(0.0015, 0.00215, 0.9, 0.999, 1e-8), T_cw=Tt)
+    torch.cuda.synchronize()
+    assert r.read_status() == (0, 0)
+    assert float(r.pose_grad.abs().max()) == 0.0
+    assert torch.equal(Tt, poses_gpu(T))
+    assert bool(torch.all(r.img["T_final"] == 1.0)) and float(r.img["color"].abs().max()) == 0.0
