@@ -302,9 +302,11 @@ __global__ void __launch_bounds__(kProjThreads)
     const bool valid_i = i < n;
     float g_mean[3] = {0.f, 0.f, 0.f}, g_ls[3] = {0.f, 0.f, 0.f}, g_q[4] = {0.f, 0.f, 0.f, 0.f};
     float g_op = 0.f, g_col[3] = {0.f, 0.f, 0.f}, g_nu = 0.f;
-    __shared__ df s_wdf[kProjThreads / 32][6];
+    constexpr int NW = kProjThreads / 32;
+    __shared__ df s_pf[GS_MAX_FRAMES][NW][6];  // per frame, per warp: pose sums
     __shared__ df s_red[kRedSlots][6];
     __shared__ int s_flag;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     for (int f = 0; f < ft.n; ++f) {
         const FrameDesc &fd = ft.f[f];
@@ -414,13 +416,37 @@ __global__ void __launch_bounds__(kProjThreads)
             pc[4] += 2.f * Z[2][0];
             pc[5] += 2.f * Z[0][1];
         }
-        // per-CTA pose partial (double-float, fixed tree); the last CTA of the
-        // frame reduces the frame's partials into the FP64 pose gradient
-        float *part_f = pose_partials + (size_t)f * per_frame * 12;
-        cta_pose_partial(pc, part_f + (size_t)blockIdx.x * 12, s_wdf);
-        if (pose_grad)
-            last_cta_pose_reduce(part_f, per_frame, gridDim.x, counters + f, pose_grad + 6 * f, s_red, &s_flag);
+        // this warp's pose sum for frame f (double-float, fixed butterfly); the
+        // CTA combines the warps once, after the frame loop, so the loop has no
+        // CTA barrier
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const df v = df_warp_sum(df{pc[k], 0.f});
+            if (lane == 0) s_pf[f][warp][k] = v;
+        }
+    }
+    // per-CTA pose partial of every frame (warps summed in order: the same
+    // values as a per-frame CTA tree), then the last CTA reduces all frames
+    __syncthreads();
+    for (int e = threadIdx.x; e < ft.n * 6; e += kProjThreads) {
+        const int f = e / 6, k = e % 6;
+        df sum = {0.f, 0.f};
+        for (int w = 0; w < NW; ++w) sum = df_add(sum, s_pf[f][w][k]);
+        reinterpret_cast<float2 *>(pose_partials + ((size_t)f * per_frame + blockIdx.x) * 12)[k] =
+            make_float2(sum.hi, sum.lo);
+    }
+    if (pose_grad) {
+        __threadfence();
         __syncthreads();
+        if (threadIdx.x == 0) s_flag = (atomicAdd(counters, 1u) == gridDim.x - 1);
+        __syncthreads();
+        if (s_flag) {
+            __threadfence();
+            for (int f = 0; f < ft.n; ++f) {
+                reduce_pose_partials(pose_partials + (size_t)f * per_frame * 12, per_frame, pose_grad + 6 * f, s_red);
+                __syncthreads();  // s_red is reused by the next frame
+            }
+        }
     }
     if (!valid_i) return;
     if (out.means) for (int k = 0; k < 3; ++k) out.means[3 * i + k] = g_mean[k];
