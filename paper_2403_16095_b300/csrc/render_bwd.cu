@@ -227,7 +227,17 @@ __global__ void __launch_bounds__(TILE *TILE)
                     }
                 }
             } else {
-                if (__any_sync(0xffffffffu, act)) {
+                const unsigned am = __ballot_sync(0xffffffffu, act);
+                if (am != 0u && (am & (am - 1u)) == 0u) {
+                    // one lane blended the entry: it adds its own gradients
+                    // (three 128-bit atomics; no warp reduction needed)
+                    if (act) {
+                        float4 *gp = reinterpret_cast<float4 *>(grad2d + (size_t)s_idx[k] * kGrad2d);
+                        atomicAdd(gp, make_float4(v[0], v[1], v[2], v[3]));
+                        atomicAdd(gp + 1, make_float4(v[4], v[5], v[6], v[7]));
+                        atomicAdd(gp + 2, make_float4(v[8], v[9], v[10], 0.f));
+                    }
+                } else if (am != 0u) {
                     // warp sum of the 11 gradients by recursive halving: at each
                     // step a lane keeps half of its values and adds its partner's
                     // copy of them (16 shuffles instead of 11 x 5); lane pairs end
