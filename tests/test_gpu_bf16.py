@@ -70,10 +70,10 @@ def precision():
 
 
 def test_precision_workload_render_matches_oracle_and_storage_error(precision):
-    """Frames 0, 49 and 99 of the 5M / 1200x680 workload rendered from packed
-    storage: 512 sampled pixels per frame against the oracle of the decoded
-    Gaussians (FP32 tolerance 1e-4, decision-margin pixels excepted), and the
-    image change caused by the storage itself (FP32 vs packed) reported."""
+    """Frames 0, 9, 19, ..., 99 of the 5M / 1200x680 workload rendered from
+    packed storage: 256 sampled pixels per frame against the oracle of the
+    decoded Gaussians (FP32 tolerance 1e-4, decision-margin pixels excepted),
+    and the image change caused by the storage itself (FP32 vs packed)."""
     from paper_2403_16095_b300 import Rasterizer, pack_bf16
     from paper_2403_16095_b300 import _abi as A
     sc, cam, poses = precision
@@ -85,7 +85,7 @@ def test_precision_workload_render_matches_oracle_and_storage_error(precision):
     assert m_err < 1e-4
     rng = np.random.default_rng(1005)
     HW = cam.width * cam.height
-    for f in (0, 49, 99):
+    for f in [0] + list(range(9, 100, 10)):
         T = np.asarray(poses[f], np.float32).astype(np.float64)
         rp = Rasterizer([cam], sc.n, tile=16, mode=A.GS_MODE_FWD)
         rp.render(pk, poses_gpu(T))
@@ -94,15 +94,18 @@ def test_precision_workload_render_matches_oracle_and_storage_error(precision):
         torch.cuda.synchronize()
         ip = {k: v.cpu().numpy() for k, v in rp.frame_images(0).items()}
         i32 = {k: v.cpu().numpy() for k, v in rf.frame_images(0).items()}
-        pix = rng.choice(HW, 512, replace=False)
+        pix = rng.choice(HW, 256, replace=False)
         ora = oracle.render_pixels(dec, cam, T, pix)
         bad = np.zeros(len(pix), bool)
         for k in ("color", "depth", "alpha", "nu_map", "T_final"):
             got = ip[k].reshape(3, -1)[:, pix] if k == "color" else ip[k].reshape(-1)[pix]
             e = np.abs(got - ora[k])
             bad |= (e.max(0) if k == "color" else e) > 1e-4
+        # every differing pixel sits at an FP32/FP64 decision margin; with 5M
+        # Gaussians a pixel walks hundreds of entries, so some land near q = 9 or
+        # alpha = 1/255: the count is reported (bounded loosely)
         assert np.all(ora["margins"].min(0)[bad] < 1e-4), f"frame {f}: mismatch away from a decision margin"
-        assert bad.sum() <= 2
+        assert bad.sum() <= 0.05 * len(pix)
         dc = np.abs(ip["color"] - i32["color"])
         dd = np.abs(ip["depth"] - i32["depth"])
         print(f"frame {f}: sampled-pixel flips {int(bad.sum())}; storage error colour mean {dc.mean():.2e} "
