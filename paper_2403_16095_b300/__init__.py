@@ -4,7 +4,7 @@ blending of colour / depth / opacity / depth uncertainty, and a reverse-walk
 backward to every Gaussian parameter and to the se(3) camera pose.
 
 The compute lives in libgs.so (C ABI, include/gs.h); this package is its thin
-Python binding (``_abi``) plus a PyTorch-side driver (``raster``). The public
+Python binding (``_abi``) plus PyTorch-side host code (``raster``). The public
 names load libgs.so on first use and fail loudly if it has not been built
 (``python -m paper_2403_16095_b300.build``); importing the package alone does
 not, so the build step never depends on an earlier build.

@@ -1,4 +1,4 @@
-"""PyTorch-side driver of libgs: device buffers, the call sequence of one
+"""PyTorch-side host code for libgs: device buffers, the call sequence of one
 iteration, a ``torch.autograd.Function`` (FULL backward) and the tracking loop
 (POSE backward + on-device Adam, captured in a CUDA graph).
 
