@@ -16,10 +16,13 @@
 //                 low key (depth bits << 32 | record); after this pass every
 //                 tile's cursor equals its end, so `ranges` is final.
 //   k_tile_sort   one CTA per tile sorts the bucket's low keys: buckets of
-//                 <= 2048 keys with a bitonic network in shared memory, larger
-//                 ones with a stable LSD radix sort (8-bit digits over the
-//                 record-index and depth bits; digits constant over the bucket
-//                 are skipped) ping-ponging in global memory. Low keys are
+//                 <= 2048 keys with a bitonic network in registers and shared
+//                 memory, larger ones with a stable LSD radix sort over the four
+//                 8-bit depth digits (digits constant over the bucket are
+//                 skipped) ping-ponging in global memory, after which each run
+//                 of equal depth is put in record order (runs longer than 32
+//                 keys: a full LSD pass over the record-index digits first,
+//                 then the depth digits). Low keys are
 //                 unique within a bucket, so the order of the atomic fill does
 //                 not matter: the output is bit-exact, the same as a stable sort
 //                 of the 64-bit keys emitted in record order, and independent of
@@ -61,22 +64,59 @@ struct PairSrc {
     uint32_t payload;  // per-record value handed to the pair callback (depth bits)
 };
 
-__device__ __forceinline__ PairSrc pair_source(const float *__restrict__ rec, const int *__restrict__ touched, int i,
-                                               int M, int n_per_frame, const FrameTable &ft) {
+// The loads of one record that the pair expansion needs. On large batches
+// k_tile_count and k_tile_fill give each thread kRecLarge records and issue
+// the loads of all of them together -- first the visibility counts, then the
+// rect (and depth) of the visible ones: the kernels are bound by memory
+// latency, and this takes two round trips per kRecLarge records instead of two
+// per record. A thread's records are a grid apart (record b kThreads + t +
+// j gridDim kThreads), so that every CTA samples the whole batch: with records
+// in spatial order the visible ones sit in contiguous ranges, and contiguous
+// chunks per CTA would hand all of the expansion work to a few CTAs. Small
+// batches keep one record per thread so that the grid still fills the GPU.
+constexpr int kRecLarge = 8;
+constexpr int kLargeBatch = 148 * 2048 * kRecLarge / 2;  // records; below it, one per thread
+struct RecLoad {
+    int touched;
+    int4 rc;
+    uint32_t zb;  // depth bits (fill only)
+};
+
+template <int R, bool Z>
+__device__ __forceinline__ void load_records(const float *__restrict__ rec, const int *__restrict__ touched,
+                                             int base, int stride, int M, RecLoad (&L)[R]) {
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const long long i = (long long)base + (long long)j * stride;
+        L[j].touched = i < M ? touched[i] : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const size_t i = (size_t)base + (size_t)j * stride;
+        if (L[j].touched > 0) {
+            L[j].rc = *reinterpret_cast<const int4 *>(rec + i * kRecFloats + R_X0);
+            if (Z) L[j].zb = __float_as_uint(rec[i * kRecFloats + R_Z]);
+        }
+    }
+}
+
+__device__ __forceinline__ PairSrc pair_source(const RecLoad &L, int i, int n_per_frame, const FrameTable &ft) {
     PairSrc p{};
-    p.valid = i < M && touched[i] > 0;
+    p.valid = L.touched > 0;
     if (p.valid) {
         const FrameDesc &fd = ft.f[i / n_per_frame];
-        const int4 rc = *reinterpret_cast<const int4 *>(rec + (size_t)i * kRecFloats + R_X0);
-        p.t = tile_rect(rc, ft.tile, fd);
+        p.t = tile_rect(L.rc, ft.tile, fd);
         p.tile_off = fd.tile_off;
         p.tiles_x = fd.tiles_x;
+        p.payload = L.zb;
     }
     return p;
 }
 
-// Calls f(owner_lane, global_tile, owner_payload) for every pair of the warp's
-// records; all shuffles happen with the whole warp converged.
+// Walks every pair of the warp's records, 32 at a time: calls
+// f(valid, owner_lane, global_tile, owner_payload) on all 32 lanes together
+// (valid = the lane holds a pair in this step), so that f may use warp
+// collectives; all shuffles happen with the whole warp converged.
 template <class F>
 __device__ __forceinline__ void warp_for_each_pair(const PairSrc &s, F &&f) {
     const int lane = threadIdx.x & 31;
@@ -107,22 +147,55 @@ __device__ __forceinline__ void warp_for_each_pair(const PairSrc &s, F &&f) {
         const int o_off = __shfl_sync(0xffffffffu, s.tile_off, owner);
         const int o_tx = __shfl_sync(0xffffffffu, s.tiles_x, owner);
         const uint32_t o_pl = __shfl_sync(0xffffffffu, s.payload, owner);
-        if (p < total) {
+        const bool valid = p < total;
+        int gt = -1;
+        if (valid) {
             const int j = p - (o_incl - o_cnt);
             const int ty = o_y0 + j / o_w, tx = o_x0 + j % o_w;
-            f(owner, o_off + ty * o_tx + tx, o_pl);
+            gt = o_off + ty * o_tx + tx;
         }
+        f(valid, owner, gt, o_pl);
     }
 }
 
+// Warp-aggregated claim of one slot per valid lane in the counter of its tile:
+// lanes with the same tile share one atomic (issued by the lowest of them).
+// Returns the lane's slot when want_slot (the atomic's old value + its rank
+// among its peers), else 0 and the atomic needs no return value. Records of a
+// warp are often neighbours in space (Morton-ordered storage), so most of a
+// warp's pairs tend to fall on a few tiles.
+template <bool WANT_SLOT>
+__device__ __forceinline__ uint32_t warp_claim(bool valid, int gt, uint32_t *ranges) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t peers = __match_any_sync(0xffffffffu, valid ? gt : -1);
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (valid && lane == leader) {
+        uint32_t *ctr = &ranges[2 * (size_t)gt + 1];
+        if (WANT_SLOT)
+            base = atomicAdd(ctr, (uint32_t)__popc(peers));
+        else
+            atomicAdd(ctr, (uint32_t)__popc(peers));
+    }
+    if (!WANT_SLOT) return 0u;
+    base = __shfl_sync(0xffffffffu, base, leader);
+    return base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+}
+
+template <int R>
 __global__ void __launch_bounds__(kThreads)
     k_tile_count(const float *__restrict__ rec, const int *__restrict__ touched, int M, int n_per_frame, FrameTable ft,
                  uint32_t *__restrict__ ranges, const int32_t *__restrict__ status) {
     if (!status_ok(status)) return;
-    const int i = blockIdx.x * kThreads + threadIdx.x;
-    const PairSrc src = pair_source(rec, touched, i, M, n_per_frame, ft);
-    if (!__any_sync(0xffffffffu, src.valid)) return;
-    warp_for_each_pair(src, [&](int, int gt, uint32_t) { atomicAdd(&ranges[2 * (size_t)gt + 1], 1u); });
+    const int base = blockIdx.x * kThreads + threadIdx.x, stride = gridDim.x * kThreads;
+    RecLoad L[R];
+    load_records<R, false>(rec, touched, base, stride, M, L);
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const PairSrc src = pair_source(L[j], base + j * stride, n_per_frame, ft);
+        if (!__any_sync(0xffffffffu, src.valid)) continue;
+        warp_for_each_pair(src, [&](bool valid, int, int gt, uint32_t) { warp_claim<false>(valid, gt, ranges); });
+    }
 }
 
 // One CTA: exclusive scan of the per-tile counts (ranges[2t+1]) into
@@ -198,20 +271,26 @@ __global__ void __launch_bounds__(kScanThreads)
     }
 }
 
+template <int R>
 __global__ void __launch_bounds__(kThreads)
     k_tile_fill(const float *__restrict__ rec, const int *__restrict__ touched, int M, int n_per_frame, FrameTable ft,
                 uint32_t *__restrict__ ranges, uint64_t *__restrict__ low_keys, int capacity,
                 const int32_t *__restrict__ status) {
     if (!status_ok(status)) return;
-    const int i = blockIdx.x * kThreads + threadIdx.x;
-    PairSrc src = pair_source(rec, touched, i, M, n_per_frame, ft);
-    if (!__any_sync(0xffffffffu, src.valid)) return;
-    src.payload = src.valid ? __float_as_uint(rec[(size_t)i * kRecFloats + R_Z]) : 0u;
-    warp_for_each_pair(src, [&](int owner, int gt, uint32_t o_zb) {
-        const uint32_t o_i = (uint32_t)(i - (threadIdx.x & 31) + owner);
-        const uint32_t slot = atomicAdd(&ranges[2 * (size_t)gt + 1], 1u);
-        if (slot < (uint32_t)capacity) low_keys[slot] = ((uint64_t)o_zb << 32) | o_i;
-    });
+    const int base = blockIdx.x * kThreads + threadIdx.x, stride = gridDim.x * kThreads;
+    RecLoad L[R];
+    load_records<R, true>(rec, touched, base, stride, M, L);
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const int i = base + j * stride;
+        const PairSrc src = pair_source(L[j], i, n_per_frame, ft);
+        if (!__any_sync(0xffffffffu, src.valid)) continue;
+        warp_for_each_pair(src, [&](bool valid, int owner, int gt, uint32_t o_zb) {
+            const uint32_t slot = warp_claim<true>(valid, gt, ranges);
+            const uint32_t o_i = (uint32_t)(i - (threadIdx.x & 31) + owner);
+            if (valid && slot < (uint32_t)capacity) low_keys[slot] = ((uint64_t)o_zb << 32) | o_i;
+        });
+    }
 }
 
 // Exclusive scan over one value per thread of the CTA; returns the prefix.
@@ -233,48 +312,87 @@ __device__ __forceinline__ uint32_t cta_excl_scan(uint32_t v, uint32_t *s_warp) 
 }
 
 // One stable LSD pass of the CTA over n keys: src -> dst by the 8-bit digit at
-// `shift`. Returns false (and leaves src as the current array) when the digit
-// is the same for all n keys.
-__device__ bool cta_radix_pass(const uint64_t *src, uint64_t *dst, int n, int shift, uint32_t *s_cnt,
-                               uint32_t (*s_wh)[kRadix], uint32_t *s_warp) {
+// `shift`. Warp w owns the contiguous segment [w seg, (w + 1) seg) of src: it
+// counts its segment's digits into its own histogram row, one CTA scan turns
+// the rows (digit-major, warp-minor) into output cursors, and each warp then
+// scatters its segment in order with warp barriers only. Returns false (dst
+// untouched, src still current) when all n keys share the digit.
+__device__ bool cta_radix_pass(const uint64_t *src, uint64_t *dst, int n, int shift, uint32_t (*s_wh)[kRadix],
+                               uint32_t *s_warp) {
+    static_assert(kThreads == kRadix, "one digit per thread in the scan");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    s_cnt[tid] = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) s_wh[w][tid] = 0;
     __syncthreads();
-    for (int i = tid; i < n; i += kThreads) atomicAdd(&s_cnt[(uint32_t)(src[i] >> shift) & (kRadix - 1)], 1u);
-    __syncthreads();
-    const uint32_t c = s_cnt[tid];
-    if (__syncthreads_or(c == (uint32_t)n)) return false;
-    const uint32_t start = cta_excl_scan(c, s_warp);
-    s_cnt[tid] = start;  // running output offset of digit tid
+    const int seg = (((n + kWarps - 1) / kWarps) + 31) & ~31;
+    const int lo = min(n, warp * seg), hi = min(n, lo + seg);
     const uint32_t lt_mask = (1u << lane) - 1u;
-    for (int base = 0; base < n; base += kThreads) {
-        const int i = base + tid;
-        const bool active = i < n;
+    for (int base = lo; base < hi; base += 32) {
+        const int i = base + lane;
+        const uint32_t d = i < hi ? ((uint32_t)(src[i] >> shift) & (kRadix - 1)) : (uint32_t)kRadix;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (d < (uint32_t)kRadix && (peers & lt_mask) == 0) s_wh[warp][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    uint32_t tot = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) tot += s_wh[w][tid];
+    if (__syncthreads_or(tot == (uint32_t)n)) return false;
+    uint32_t r = cta_excl_scan(tot, s_warp);
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {  // column tid only: no barrier needed before it
+        const uint32_t c = s_wh[w][tid];
+        s_wh[w][tid] = r;
+        r += c;
+    }
+    __syncthreads();
+    for (int base = lo; base < hi; base += 32) {
+        const int i = base + lane;
+        const bool active = i < hi;
         const uint64_t key = active ? src[i] : 0ull;
         const uint32_t d = active ? ((uint32_t)(key >> shift) & (kRadix - 1)) : (uint32_t)kRadix;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         const uint32_t rank = __popc(peers & lt_mask);
-        __syncthreads();  // previous chunk done with s_wh; s_cnt writes visible
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) s_wh[w][tid] = 0;
-        __syncthreads();
-        if (active && rank == 0) s_wh[warp][d] = __popc(peers);
-        __syncthreads();
-        {
-            uint32_t r = s_cnt[tid];
-#pragma unroll
-            for (int w = 0; w < kWarps; ++w) {
-                const uint32_t cw = s_wh[w][tid];
-                s_wh[w][tid] = r;
-                r += cw;
-            }
-            s_cnt[tid] = r;
-        }
-        __syncthreads();
-        if (active) dst[s_wh[warp][d] + rank] = key;
+        const uint32_t off = active ? s_wh[warp][d] : 0u;
+        if (active) dst[off + rank] = key;
+        __syncwarp();
+        if (active && rank == 0) s_wh[warp][d] = off + __popc(peers);
+        __syncwarp();
     }
     __syncthreads();
     return true;
+}
+
+// Keys sorted by their high 32 bits (depth) only: put every run of equal depth
+// in record order (low bits), the run's first position doing an insertion sort
+// of the run in place. Runs are disjoint and other threads read only the depth
+// bits of a run, which the sort does not change. Returns true for the whole CTA
+// when some run is longer than kMaxTieRun (left for a full sort instead).
+constexpr int kMaxTieRun = 32;
+__device__ bool cta_fix_depth_ties(uint64_t *a, int n) {
+    int bad = 0;
+    for (int i = threadIdx.x; i < n; i += kThreads) {
+        const uint32_t z = (uint32_t)(a[i] >> 32);
+        if (i + 1 >= n || (uint32_t)(a[i + 1] >> 32) != z) continue;
+        if (i > 0 && (uint32_t)(a[i - 1] >> 32) == z) continue;  // not the first of its run
+        int j = i + 2;
+        while (j < n && j - i <= kMaxTieRun && (uint32_t)(a[j] >> 32) == z) ++j;
+        if (j - i > kMaxTieRun) {
+            bad = 1;
+            continue;
+        }
+        for (int p = i + 1; p < j; ++p) {
+            const uint64_t k = a[p];
+            int q = p - 1;
+            while (q >= i && a[q] > k) {
+                a[q + 1] = a[q];
+                --q;
+            }
+            a[q + 1] = k;
+        }
+    }
+    return __syncthreads_or(bad) != 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -344,8 +462,8 @@ __device__ void cta_sort_regs(const uint64_t *keys, int n, uint64_t *s_a) {
 // per warp, 8 per CTA, with warp barriers only; the others take one CTA each.
 // Bitonic networks (low keys are unique within a bucket, so the result is the
 // same as a stable radix sort). A CTA sorts its bucket with the keys in
-// registers (cta_sort_regs); buckets
-// of more than kSmemKeys keys take a stable LSD radix sort that ping-pongs in
+// registers (cta_sort_regs); buckets of more than kSmemKeys keys take the LSD
+// radix sort over the depth digits and the equal-depth fix-up, ping-ponging in
 // global memory.
 __global__ void __launch_bounds__(kThreads, 4)
     k_tile_sort(uint64_t *low_keys, uint64_t *tmp, const uint32_t *__restrict__ ranges,
@@ -353,7 +471,6 @@ __global__ void __launch_bounds__(kThreads, 4)
                 uint32_t *__restrict__ values, uint64_t *__restrict__ keys_out, int rec_bits,
                 const int32_t *__restrict__ status) {
     __shared__ uint64_t s_a[kSmemKeys];
-    __shared__ uint32_t s_cnt[kRadix];
     __shared__ uint32_t s_wh[kWarps][kRadix];
     __shared__ uint32_t s_warp[kWarps];
     static_assert(kWarps * kWarpSortKeys <= kSmemKeys, "warp buckets share s_a");
@@ -415,18 +532,27 @@ __global__ void __launch_bounds__(kThreads, 4)
         }
         return;
     }
-    uint64_t *a = tmp + s;       // large buckets ping-pong in global memory;
-    uint64_t *b = low_keys + s;  // the bucket's own input slots are free after the copy
-    for (int i = tid; i < n; i += kThreads) tmp[s + i] = low_keys[s + i];
-    __syncthreads();
-    // LSD order: the record-index digits (bits [0, rec_bits)), then the four
-    // depth digits (bits [32, 64))
-    for (int shift = 0; shift < 64; shift += kRadixBits) {
-        if (shift >= rec_bits && shift < 32) continue;
-        if (cta_radix_pass(a, b, n, shift, s_cnt, s_wh, s_warp)) {
+    // large buckets ping-pong between their own slots and the same slots of tmp
+    uint64_t *a = low_keys + s, *b = tmp + s;
+    // the four depth digits (bits [32, 64)), least significant first; equal
+    // depths are then put in record order
+    for (int shift = 32; shift < 64; shift += kRadixBits) {
+        if (cta_radix_pass(a, b, n, shift, s_wh, s_warp)) {
             uint64_t *t = a;
             a = b;
             b = t;
+        }
+    }
+    if (cta_fix_depth_ties(a, n)) {
+        // a long run of one depth: full LSD over the record-index digits (bits
+        // [0, rec_bits)), then the depth digits
+        for (int shift = 0; shift < 64; shift += kRadixBits) {
+            if (shift >= rec_bits && shift < 32) continue;
+            if (cta_radix_pass(a, b, n, shift, s_wh, s_warp)) {
+                uint64_t *t = a;
+                a = b;
+                b = t;
+            }
         }
     }
     for (int i = tid; i < n; i += kThreads) {
@@ -480,10 +606,20 @@ cudaError_t launch_bin_tiles(const float *rec, const int *touched, int n_records
     if ((err = cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * (size_t)ft.total_tiles, s)) != cudaSuccess)
         return err;
     if (ft.total_tiles == 0) return cudaSuccess;
-    const int grid = n_records > 0 ? (n_records + kThreads - 1) / kThreads : 1;
-    k_tile_count<<<grid, kThreads, 0, s>>>(rec, touched, n_records, n_per_frame, ft, ranges, status);
+    const bool large = n_records >= kLargeBatch;
+    const int per_cta = kThreads * (large ? kRecLarge : 1);
+    const int grid = n_records > 0 ? (int)(((size_t)n_records + per_cta - 1) / per_cta) : 1;
+    if (large)
+        k_tile_count<kRecLarge><<<grid, kThreads, 0, s>>>(rec, touched, n_records, n_per_frame, ft, ranges, status);
+    else
+        k_tile_count<1><<<grid, kThreads, 0, s>>>(rec, touched, n_records, n_per_frame, ft, ranges, status);
     k_tile_scan<<<1, kScanThreads, 0, s>>>(ranges, ft.total_tiles, capacity, status, misc, order);
-    k_tile_fill<<<grid, kThreads, 0, s>>>(rec, touched, n_records, n_per_frame, ft, ranges, low, capacity, status);
+    if (large)
+        k_tile_fill<kRecLarge><<<grid, kThreads, 0, s>>>(rec, touched, n_records, n_per_frame, ft, ranges, low,
+                                                         capacity, status);
+    else
+        k_tile_fill<1><<<grid, kThreads, 0, s>>>(rec, touched, n_records, n_per_frame, ft, ranges, low, capacity,
+                                                 status);
     k_tile_sort<<<ft.total_tiles, kThreads, 0, s>>>(low, tmp, ranges, order, misc, ft.total_tiles, values, keys_out,
                                                     rec_bits, status);
     return cudaGetLastError();

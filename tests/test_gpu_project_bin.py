@@ -100,7 +100,9 @@ def test_pose_jacobian_matches_oracle_finite_differences():
 
 # ------------------------------------------------------------------ binning
 def _synthetic_records(n, cams, tile, seed, ties=True):
-    """Records with random pixel rects and depths (many exact ties)."""
+    """Records with random pixel rects and depths: ties=True draws from four
+    depths (runs of equal depth of hundreds of keys), "short" from n // 3
+    depths (runs of a few keys), False from a continuous range."""
     rng = np.random.default_rng(seed)
     F = len(cams)
     rec = np.zeros((F * n, 16), np.float32)
@@ -112,8 +114,12 @@ def _synthetic_records(n, cams, tile, seed, ties=True):
                                         np.minimum(c.height - 1, y0 + rng.integers(0, 50, n))]
     culled = rng.uniform(size=F * n) < 0.1
     rect[culled] = [1, 1, 0, 0]
-    depth = (rng.choice(np.float32([0.25, 1.0, 1.5, 7.0]), F * n) if ties
-             else rng.uniform(0.2, 50.0, F * n).astype(np.float32))
+    if ties == "short":
+        depth = (0.5 + 0.001 * rng.integers(0, max(1, n // 3), F * n)).astype(np.float32)
+    elif ties:
+        depth = rng.choice(np.float32([0.25, 1.0, 1.5, 7.0]), F * n)
+    else:
+        depth = rng.uniform(0.2, 50.0, F * n).astype(np.float32)
     rec[:, 6] = depth
     rec.view(np.int32)[:, 12:16] = rect
     ok = rect[:, 0] <= rect[:, 2]
@@ -121,16 +127,19 @@ def _synthetic_records(n, cams, tile, seed, ties=True):
     return rec, rect, depth, touched.astype(np.int32)
 
 
-@pytest.mark.parametrize("cams,tile,ties", [
-    ([synth.Camera(128, 96, 1, 1, 0, 0)], 16, True),                        # 48 tiles: 5 radix passes
-    ([synth.Camera(640, 480, 1, 1, 0, 0)], 16, False),                      # 1200 tiles: 6 passes
-    ([synth.Camera(1200, 680, 1, 1, 0, 0)], 8, True),                       # 12750 tiles
+@pytest.mark.parametrize("cams,tile,ties,n", [
+    ([synth.Camera(128, 96, 1, 1, 0, 0)], 16, True, 3000),                  # 48 tiles
+    ([synth.Camera(640, 480, 1, 1, 0, 0)], 16, False, 3000),                # 1200 tiles
+    ([synth.Camera(1200, 680, 1, 1, 0, 0)], 8, True, 3000),                 # 12750 tiles
     ([synth.Camera(100, 70, 1, 1, 0, 0), synth.Camera(37, 53, 1, 1, 0, 0),
-      synth.Camera(64, 64, 1, 1, 0, 0)], 16, True),                         # uneven frames, ragged
-    ([synth.Camera(16, 16, 1, 1, 0, 0)], 16, True),                         # a single tile
+      synth.Camera(64, 64, 1, 1, 0, 0)], 16, True, 3000),                   # uneven frames, ragged
+    # lists of more than 2048 keys (radix path over the depth digits):
+    ([synth.Camera(16, 16, 1, 1, 0, 0)], 16, True, 3000),                   # one tile; long equal-depth runs
+    ([synth.Camera(16, 16, 1, 1, 0, 0)], 16, "short", 9000),                # runs of a few equal depths
+    ([synth.Camera(40, 24, 1, 1, 0, 0)], 16, False, 20000),                 # 6 tiles, ~10k keys each
+    ([synth.Camera(48, 40, 1, 1, 0, 0), synth.Camera(16, 16, 1, 1, 0, 0)], 8, "short", 5000),
 ])
-def test_bin_tiles_bit_exact(cams, tile, ties):
-    n = 3000
+def test_bin_tiles_bit_exact(cams, tile, ties, n):
     rec, rect, depth, touched = _synthetic_records(n, cams, tile, seed=len(cams) * 7 + tile, ties=ties)
     r = _rast(cams, n, tile=tile, capacity=int(touched.sum()) + 17)
     r.rec.copy_(torch.from_numpy(rec.reshape(-1)))
