@@ -474,7 +474,8 @@ def run_batch(a):
                          "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                          "traffic": None, "flop_per_contribution": BWD_FULL_FLOP_PER_CONTRIB,
                          "avg_launch_ms": bwd_ms},
-            "cpu_baseline": None, "gpu_launches": 8 * a.steps, "clocks": clk}
+            # project, 5 binning kernels, forward, FULL backward, projection adjoint
+            "cpu_baseline": None, "gpu_launches": 9 * a.steps, "clocks": clk}
     print(json.dumps(line), flush=True)
 
 

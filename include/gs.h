@@ -59,7 +59,7 @@ extern "C" {
 #endif
 
 #define GS_MAX_FRAMES 64
-#define GS_ABI_VERSION 6
+#define GS_ABI_VERSION 7
 
 typedef struct CUstream_st *gs_stream; /* a cudaStream_t; NULL = legacy default stream */
 
@@ -301,7 +301,11 @@ gs_status gs_render_fwd(const gs_projected *proj, const gs_tiles *tiles, int n_f
  * K = gs_pose_partials_per_frame(); unused slots are zeroed. If pose_grad is
  * not NULL, the last CTA of each frame also reduces that frame's partials into
  * pose_grad[f][6] (FP64), exactly as gs_pose_grad_reduce would (bit-identical),
- * saving a launch. ws: gs_render_bwd_workspace_size bytes, 256-byte aligned. */
+ * saving a launch. ws: gs_render_bwd_workspace_size bytes, 256-byte aligned,
+ * zero-filled before its first use (one cudaMemset after allocating it): its
+ * last 256 bytes hold the arrival counters of that reduction, which every call
+ * leaves at zero again, so no call clears them. A ws whose counters are not
+ * zero gives a wrong pose_grad.                                              */
 int gs_pose_partials_per_frame(int mode, int n_gaussians, int n_frames, const gs_camera *cams, int tile);
 size_t gs_render_bwd_workspace_size(int n_records, int mode);
 gs_status gs_render_bwd(const gs_projected *proj, const gs_tiles *tiles, int n_frames,

@@ -100,7 +100,7 @@ EXPORTS = ("gs_abi_version", "gs_last_error", "gs_project", "gs_bin_tiles_worksp
            "gs_render_bwd", "gs_render_fwd_bwd_pose", "gs_project_bf16", "gs_spatial_order_workspace_size", "gs_spatial_order",
            "gs_pack_bf16", "gs_nu_accumulate", "gs_nu_finalize", "gs_pose_grad_reduce", "gs_pose_adam_step")
 GS_NOALLOC_MAX_PAIRS = 1 << 19
-ABI_VERSION = 6  # GS_ABI_VERSION of the gs.h these structures mirror
+ABI_VERSION = 7  # GS_ABI_VERSION of the gs.h these structures mirror
 
 
 def _load():

@@ -103,7 +103,9 @@ gs_status check_tiles(const gs_tiles *t, const gs::FrameTable &ft) {
     } while (0)
 
 // Backward workspace: [FULL: per-record 2D gradient accumulators][per-frame
-// arrival counters of the fused pose reduction, GS_MAX_FRAMES x uint32].
+// arrival counters of the fused pose reduction, GS_MAX_FRAMES x uint32]. The
+// counters are zero before the first call (the caller zero-fills ws once) and
+// every launch leaves them zero: each wraps back to 0 at its last arrival.
 constexpr size_t kAlign = 256;
 size_t grad2d_bytes(int n_records, int mode) {
     if (mode != GS_MODE_FULL) return 0;
@@ -281,8 +283,6 @@ gs_status gs_render_bwd(const gs_projected *proj, const gs_tiles *tiles, int n_f
         return fail(GS_ERR_INVALID_ARG, "workspace %zu bytes < %zu needed (256-aligned)", ws_bytes, need);
     unsigned *counters = reinterpret_cast<unsigned *>(static_cast<char *>(ws) + grad2d_bytes(M, mode));
     cudaError_t e;
-    if (pose_grad && (e = cudaMemsetAsync(counters, 0, sizeof(unsigned) * n_frames, stream)) != cudaSuccess)
-        return cuda_status(e, "gs_render_bwd memset");
     if (mode == GS_MODE_POSE) {
         if (!proj->pose_jac) return fail(GS_ERR_INVALID_ARG, "POSE mode needs projected.pose_jac");
         for (int f = 0; f < n_frames; ++f) {
@@ -350,8 +350,6 @@ gs_status gs_render_fwd_bwd_pose(const gs_projected *proj, const gs_tiles *tiles
         return fail(GS_ERR_INVALID_ARG, "workspace %zu bytes < %zu needed (256-aligned)", ws_bytes, need);
     unsigned *counters = reinterpret_cast<unsigned *>(static_cast<char *>(ws) + grad2d_bytes(M, GS_MODE_POSE));
     cudaError_t e;
-    if (pose_grad && (e = cudaMemsetAsync(counters, 0, sizeof(unsigned) * n_frames, stream)) != cudaSuccess)
-        return cuda_status(e, "gs_render_fwd_bwd_pose memset");
     for (int f = 0; f < n_frames; ++f) {
         const int used = ft.f[f].tiles_x * ft.f[f].tiles_y;
         if (used < per_frame) {

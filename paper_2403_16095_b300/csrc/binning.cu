@@ -186,6 +186,7 @@ template <int R>
 __global__ void __launch_bounds__(kThreads)
     k_tile_count(const float *__restrict__ rec, const int *__restrict__ touched, int M, int n_per_frame, FrameTable ft,
                  uint32_t *__restrict__ ranges, const int32_t *__restrict__ status) {
+    dep_wait();
     if (!status_ok(status)) return;
     const int base = blockIdx.x * kThreads + threadIdx.x, stride = gridDim.x * kThreads;
     RecLoad L[R];
@@ -198,6 +199,16 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+// Zeroes the per-tile counters (ranges) and the scalars of the call before the
+// count: a kernel rather than two memsets, so that the chain of launches stays
+// kernel to kernel.
+__global__ void __launch_bounds__(kThreads) k_bin_clear(uint32_t *__restrict__ ranges, int n_words, int *__restrict__ misc) {
+    dep_wait();
+    const int stride = gridDim.x * kThreads;
+    for (int i = blockIdx.x * kThreads + threadIdx.x; i < n_words; i += stride) ranges[i] = 0u;
+    if (blockIdx.x == 0 && threadIdx.x < 16) misc[threadIdx.x] = 0;
+}
+
 // One CTA: exclusive scan of the per-tile counts (ranges[2t+1]) into
 // ranges[2t] = ranges[2t+1] = start (the fill then advances ranges[2t+1] to end).
 constexpr int kOrderBuckets = kScanThreads;  // list length / 4, clipped
@@ -208,6 +219,7 @@ __device__ __forceinline__ int order_bucket(uint32_t len) { return (int)min(len 
 __global__ void __launch_bounds__(kScanThreads)
     k_tile_scan(uint32_t *__restrict__ ranges, int n_tiles, int capacity, int32_t *__restrict__ status,
                 int *__restrict__ misc, uint32_t *__restrict__ order) {
+    dep_wait();
     __shared__ long long s_w[kScanThreads / 32];
     __shared__ uint32_t s_hist[kOrderBuckets];
     __shared__ uint32_t s_bw[kScanThreads / 32];
@@ -276,6 +288,7 @@ __global__ void __launch_bounds__(kThreads)
     k_tile_fill(const float *__restrict__ rec, const int *__restrict__ touched, int M, int n_per_frame, FrameTable ft,
                 uint32_t *__restrict__ ranges, uint64_t *__restrict__ low_keys, int capacity,
                 const int32_t *__restrict__ status) {
+    dep_wait();
     if (!status_ok(status)) return;
     const int base = blockIdx.x * kThreads + threadIdx.x, stride = gridDim.x * kThreads;
     RecLoad L[R];
@@ -470,6 +483,7 @@ __global__ void __launch_bounds__(kThreads, 4)
                 const uint32_t *__restrict__ order, const int *__restrict__ misc, int n_tiles,
                 uint32_t *__restrict__ values, uint64_t *__restrict__ keys_out, int rec_bits,
                 const int32_t *__restrict__ status) {
+    dep_wait();
     __shared__ uint64_t s_a[kSmemKeys];
     __shared__ uint32_t s_wh[kWarps][kRadix];
     __shared__ uint32_t s_warp[kWarps];
@@ -602,26 +616,28 @@ cudaError_t launch_bin_tiles(const float *rec, const int *touched, int n_records
     // low key = depth bits << 32 | record index; only the index bits that can be set are sorted
     const int rec_bits = bit_width((unsigned)(n_records > 0 ? n_records - 1 : 0));
     cudaError_t err;
-    if ((err = cudaMemsetAsync(misc, 0, sizeof(int) * 16, s)) != cudaSuccess) return err;
-    if ((err = cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * (size_t)ft.total_tiles, s)) != cudaSuccess)
+    const int n_words = 2 * ft.total_tiles;
+    const int clear_grid = n_words > 0 ? min((n_words + kThreads - 1) / kThreads, 4 * 148) : 1;
+    if ((err = launch_chained(k_bin_clear, dim3(clear_grid), dim3(kThreads), 0, s, ranges, n_words, misc)) != cudaSuccess)
         return err;
     if (ft.total_tiles == 0) return cudaSuccess;
     const bool large = n_records >= kLargeBatch;
     const int per_cta = kThreads * (large ? kRecLarge : 1);
     const int grid = n_records > 0 ? (int)(((size_t)n_records + per_cta - 1) / per_cta) : 1;
-    if (large)
-        k_tile_count<kRecLarge><<<grid, kThreads, 0, s>>>(rec, touched, n_records, n_per_frame, ft, ranges, status);
-    else
-        k_tile_count<1><<<grid, kThreads, 0, s>>>(rec, touched, n_records, n_per_frame, ft, ranges, status);
-    k_tile_scan<<<1, kScanThreads, 0, s>>>(ranges, ft.total_tiles, capacity, status, misc, order);
-    if (large)
-        k_tile_fill<kRecLarge><<<grid, kThreads, 0, s>>>(rec, touched, n_records, n_per_frame, ft, ranges, low,
-                                                         capacity, status);
-    else
-        k_tile_fill<1><<<grid, kThreads, 0, s>>>(rec, touched, n_records, n_per_frame, ft, ranges, low, capacity,
-                                                 status);
-    k_tile_sort<<<ft.total_tiles, kThreads, 0, s>>>(low, tmp, ranges, order, misc, ft.total_tiles, values, keys_out,
-                                                    rec_bits, status);
+    auto count = large ? k_tile_count<kRecLarge> : k_tile_count<1>;
+    auto fill = large ? k_tile_fill<kRecLarge> : k_tile_fill<1>;
+    if ((err = launch_chained(count, dim3(grid), dim3(kThreads), 0, s, rec, touched, n_records, n_per_frame, ft, ranges,
+                              status)) != cudaSuccess)
+        return err;
+    if ((err = launch_chained(k_tile_scan, dim3(1), dim3(kScanThreads), 0, s, ranges, ft.total_tiles, capacity, status,
+                              misc, order)) != cudaSuccess)
+        return err;
+    if ((err = launch_chained(fill, dim3(grid), dim3(kThreads), 0, s, rec, touched, n_records, n_per_frame, ft, ranges,
+                              low, capacity, status)) != cudaSuccess)
+        return err;
+    if ((err = launch_chained(k_tile_sort, dim3(ft.total_tiles), dim3(kThreads), 0, s, low, tmp, ranges, order, misc,
+                              ft.total_tiles, values, keys_out, rec_bits, status)) != cudaSuccess)
+        return err;
     return cudaGetLastError();
 }
 

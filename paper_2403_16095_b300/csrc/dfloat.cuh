@@ -101,7 +101,9 @@ __device__ __forceinline__ void last_cta_pose_reduce(const float *partials_f, in
                                                      double *pose_grad, df (*s_red)[6], int *s_flag) {
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) *s_flag = (atomicAdd(counter, 1u) == (unsigned)(n_ctas - 1));
+    // atomicInc wraps the counter back to 0 at the last arrival, so it is
+    // ready for the next launch without a memset
+    if (threadIdx.x == 0) *s_flag = (atomicInc(counter, (unsigned)(n_ctas - 1)) == (unsigned)(n_ctas - 1));
     __syncthreads();
     if (*s_flag) {
         __threadfence();

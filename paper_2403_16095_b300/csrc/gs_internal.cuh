@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "../../include/gs.h"
 
 namespace gs {
@@ -54,6 +56,35 @@ struct LossParams {
     const float *target_color, *target_depth;
     const float *g_color, *g_depth, *g_alpha, *g_unc, *g_nu, *g_median;
 };
+
+// Programmatic dependent launch. The kernels of one iteration (projection,
+// the four binning kernels, the tracking pass) are launched with
+// launch_chained(): the next kernel in the stream may be scheduled while the
+// current one drains, instead of after it has completed. Every such kernel
+// calls dep_wait() before it touches global memory (reads or writes); the wait
+// returns once all earlier work in the stream has completed and its writes are
+// visible, so the stream order is kept. For a kernel launched without the
+// attribute the wait returns at once. No kernel signals its dependents early
+// (griddepcontrol.launch_dependents): a dependent grid parked on the SMs
+// during the tail of the one before it measured 6% slower per iteration than
+// launching it as the CTAs of that one retire.
+__device__ __forceinline__ void dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                  Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // frame of a global tile id (frames are few: linear scan of a uniform table)
 __device__ __forceinline__ int frame_of_tile(const FrameTable &ft, int gtile) {

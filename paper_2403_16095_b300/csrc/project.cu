@@ -190,6 +190,7 @@ __global__ void __launch_bounds__(kProjThreads)
     k_project(Src src, int n, FrameTable ft, const float *__restrict__ T_cw, float jclamp, float nu_cull,
               float *__restrict__ rec, int *__restrict__ touched, float *__restrict__ jac,
               const int32_t *__restrict__ status) {
+    dep_wait();
     if (status[0] != 0) return;
     const int i = blockIdx.x * kProjThreads + threadIdx.x;
     const int f = blockIdx.y;
@@ -438,7 +439,7 @@ __global__ void __launch_bounds__(kProjThreads)
     if (pose_grad) {
         __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) s_flag = (atomicAdd(counters, 1u) == gridDim.x - 1);
+        if (threadIdx.x == 0) s_flag = (atomicInc(counters, gridDim.x - 1) == gridDim.x - 1);  // wraps to 0
         __syncthreads();
         if (s_flag) {
             __threadfence();
@@ -465,10 +466,10 @@ cudaError_t launch_src(const Src &src, int n, const FrameTable &ft, const float 
     if (n == 0) return cudaSuccess;
     dim3 grid((n + kProjThreads - 1) / kProjThreads, ft.n);
     if (mode == GS_MODE_POSE)
-        k_project<true><<<grid, kProjThreads, 0, s>>>(src, n, ft, T_cw, jclamp, nu_cull, rec, touched, jac, status);
-    else
-        k_project<false><<<grid, kProjThreads, 0, s>>>(src, n, ft, T_cw, jclamp, nu_cull, rec, touched, jac, status);
-    return cudaGetLastError();
+        return launch_chained(k_project<true, Src>, grid, dim3(kProjThreads), 0, s, src, n, ft, T_cw, jclamp, nu_cull,
+                              rec, touched, jac, status);
+    return launch_chained(k_project<false, Src>, grid, dim3(kProjThreads), 0, s, src, n, ft, T_cw, jclamp, nu_cull,
+                          rec, touched, jac, status);
 }
 
 cudaError_t launch_project(const GaussPtrs &g, int n, const FrameTable &ft, const float *T_cw, float jclamp,

@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(TILE *TILE)
                         float *__restrict__ pose_partials, int per_frame, double *__restrict__ pose_grad,
                         unsigned *__restrict__ counters, double *__restrict__ adam_state, gs_adam adam,
                         float *__restrict__ T_cw, const int32_t *__restrict__ status) {
+    dep_wait();
     using SM = FusedSmem<TILE>;
     constexpr int NT = SM::NT;
     constexpr int BATCH = SM::BATCH;
@@ -268,10 +269,8 @@ cudaError_t launch_tile(const float4 *rec, const float4 *jac, const uint32_t *va
         if (e != cudaSuccess) return e;
         if (dev < 64) done.fetch_or(1ull << dev);
     }
-    k_render_fused_pose<TILE><<<ft.total_tiles, TILE * TILE, smem, s>>>(rec, jac, values, ranges, order, ft, out, lp,
-                                                                        pp, per_frame, pg, cnt, adam_state, adam,
-                                                                        T_cw, status);
-    return cudaGetLastError();
+    return launch_chained(k_render_fused_pose<TILE>, dim3(ft.total_tiles), dim3(TILE * TILE), smem, s, rec, jac, values,
+                          ranges, order, ft, out, lp, pp, per_frame, pg, cnt, adam_state, adam, T_cw, status);
 }
 
 }  // namespace

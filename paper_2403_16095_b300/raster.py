@@ -82,7 +82,8 @@ class Rasterizer:
             # double-float partials: [F][per_frame][6][2] (hi, lo)
             self.pose_partials = torch.zeros(self.F * self.per_frame * 12, dtype=torch.float32, device=dev)
             self.pose_grad = torch.zeros(self.F, 6, dtype=torch.float64, device=dev)
-            self.bwd_ws = torch.empty(A.gs_render_bwd_workspace_size(self.M, mode), dtype=torch.uint8, device=dev)
+            # zero-filled once: the arrival counters in it must start at zero
+            self.bwd_ws = torch.zeros(A.gs_render_bwd_workspace_size(self.M, mode), dtype=torch.uint8, device=dev)
 
     # --------------------------------------------------------------- buffers
     def set_capacity(self, capacity: int) -> None:
@@ -378,11 +379,12 @@ class Tracker:
             A.gs_pose_adam_step(self.state, r.pose_grad, self.T_cw, 1, self.adam, r.status, stream)
 
     def kernel_launches_per_iteration(self) -> int:
-        """libgs kernels one iteration launches (memsets not counted): project;
-        tile count, scan, fill, per-tile sort; then either the tracking pass
-        (forward, backward, pose reduction and Adam step in one launch) or the
-        forward, the backward (with the pose reduction) and the Adam step."""
-        return 1 + 4 + (1 if self.fused else 3)
+        """libgs kernels one iteration launches: project; the binning's counter
+        clear, tile count, scan, fill and per-tile sort; then either the
+        tracking pass (forward, backward, pose reduction and Adam step in one
+        launch) or the forward, the backward (with the pose reduction) and the
+        Adam step. No memsets."""
+        return 1 + 5 + (1 if self.fused else 3)
 
     def _capture(self):
         """Capture all ``iters`` iterations of a frame in one CUDA graph."""
