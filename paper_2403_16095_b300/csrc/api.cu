@@ -361,7 +361,7 @@ gs_status gs_render_fwd_bwd_pose(const gs_projected *proj, const gs_tiles *tiles
     const gs_adam ad = adam ? *adam : gs_adam{};
     return cuda_status(gs::launch_render_fused_pose(proj->rec, proj->pose_jac, tiles->values, tiles->ranges,
                                                     tiles->order, ft, ip, lp, pose_partials, per_frame, pose_grad,
-                                                    counters, adam_state, ad, T_cw, status, stream),
+                                                    counters, adam_state, ad, T_cw, status, M, stream),
                        "gs_render_fwd_bwd_pose");
 }
 

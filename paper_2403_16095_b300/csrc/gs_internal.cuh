@@ -134,7 +134,7 @@ cudaError_t launch_render_fused_pose(const float *rec, const float *jac, const u
                                      const uint32_t *ranges, const uint32_t *order, const FrameTable &ft,
                                      const ImagePtrs &out, const LossParams &lp, float *pose_partials, int per_frame,
                                      double *pose_grad, unsigned *counters, double *adam_state, const gs_adam &adam,
-                                     float *T_cw, const int32_t *status, cudaStream_t s);
+                                     float *T_cw, const int32_t *status, int n_records, cudaStream_t s);
 // nu.cu
 cudaError_t launch_nu_accumulate(const float *rec, const uint32_t *values, const FrameTable &ft, int n_gaussians,
                                  const float *obs_depth, const int32_t *dom_pos, const float *dom_weight,
