@@ -57,18 +57,18 @@ BWD_FLOP_PER_CONTRIB = 122
 # channel dot product (9 with opacity, U and the median), dL/dalpha and suffix
 # sum (5), gradients of mean2d, conic, opacity, depth and colour (21).
 BWD_FULL_FLOP_PER_CONTRIB = 52
-# DRAM bytes (read + write) of one k_render_bwd<16,POSE> launch of this workload,
-# from one ncu capture of the current kernel (profiles/k_render_blend_track-640x480-300k.md,
-# cold cache); None once the kernel changes.
-BWD_DRAM_BYTES_PER_LAUNCH = 27.48928e6 + 768
+# DRAM bytes (read + write) of one k_render_bwd<16,POSE> launch: None, since
+# the kernel changed after its last ncu capture.
+BWD_DRAM_BYTES_PER_LAUNCH = None
 # forward per blended entry: offsets (2), q (7), exponent argument (1), opacity x G
 # (1), clamp (1), 1 - alpha and T' (2), w (1), colour, depth and nu
 # accumulation (10), ex2 (1)
 FWD_FLOP_PER_CONTRIB = 26
-# DRAM bytes (read + write) of one k_render_fused_pose<16> launch of this workload,
-# from one ncu capture of the current kernel (profiles/k_render_fused_pose_track-640x480-300k.md,
-# cold cache); None once the kernel changes.
-FUSED_DRAM_BYTES_PER_LAUNCH = 16.352512e6 + 0
+# DRAM bytes (read + write) of one k_render_fused_pose<16, 3> launch of this
+# workload, from one ncu capture of the current kernel
+# (profiles/k_render_fused_pose_track-640x480-300k.md, cold cache); None once
+# the kernel changes.
+FUSED_DRAM_BYTES_PER_LAUNCH = 16.352768e6 + 0
 FP32_LANES_PER_SM = 128
 N_SM = 148
 
@@ -333,8 +333,11 @@ def run_ours(a):
     bwd_avg_ms = statistics.mean(bwd_ms)
     E = statistics.mean(contrib)
     if tr.fused:
-        kname, flop, traffic = f"k_render_fused_pose<{a.tile}>", FWD_FLOP_PER_CONTRIB + BWD_FLOP_PER_CONTRIB, \
-            (FUSED_DRAM_BYTES_PER_LAUNCH if a.tile == 16 else None)
+        # the library's build choice: 4 CTAs per SM at >= 800 records per tile, else 3 (tile 16)
+        dense = g.n >= 800 * tr.rast.n_tiles
+        minb = (4 if dense else 3) if a.tile == 16 else 1
+        kname, flop, traffic = f"k_render_fused_pose<{a.tile}, {minb}>", FWD_FLOP_PER_CONTRIB + BWD_FLOP_PER_CONTRIB, \
+            (FUSED_DRAM_BYTES_PER_LAUNCH if (a.tile == 16 and not dense) else None)
     else:
         kname, flop, traffic = f"k_render_bwd<{a.tile},POSE>", BWD_FLOP_PER_CONTRIB, \
             (BWD_DRAM_BYTES_PER_LAUNCH if a.tile == 16 else None)
