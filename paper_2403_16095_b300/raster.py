@@ -437,6 +437,64 @@ class Tracker:
         torch.cuda.current_stream().synchronize()
         return out
 
+    # ------------------------------------------------------------ streaming
+    def submit(self, target_color, target_depth, T_init, out) -> None:
+        """Enqueue one frame from pinned host memory and return at once.
+
+        The frame's RGB-D target and initial pose (pinned host tensors) are
+        copied on a separate copy stream into one of two device staging
+        buffers, so the upload of frame k + 1 overlaps the tracking of frame k.
+        The frame is then set and tracked in stream order after everything
+        already enqueued on the caller's current stream. Its refined pose
+        (FP64 [3, 4]) is copied to ``out`` (pinned host) and its status word to
+        an internal pinned slot, both without a host sync. The host tensors
+        must stay untouched until drain() returns. Needs a captured graph
+        (prepare() or one track()/track_host() call first)."""
+        if self.graph_enabled and self.graph is None:
+            raise RuntimeError("submit() needs the graph captured: call prepare() or track() once first")
+        dev = self.state.device
+        if not hasattr(self, "_copy_stream"):
+            self._copy_stream = torch.cuda.Stream(device=dev)
+            self._stage = [(torch.empty_like(self.target_color), torch.empty_like(self.target_depth),
+                            torch.empty(3, 4, dtype=torch.float64, device=dev)) for _ in range(2)]
+            self._staged = [torch.cuda.Event() for _ in range(2)]
+            self._consumed = [torch.cuda.Event() for _ in range(2)]
+            self._pending = []
+        k = len(self._pending)
+        slot = k % 2
+        col, dep, T0 = self._stage[slot]
+        cur = torch.cuda.current_stream()
+        with torch.cuda.stream(self._copy_stream):
+            if k >= 2:  # the slot's previous frame has been copied out of it
+                self._copy_stream.wait_event(self._consumed[slot])
+            col.copy_(target_color.reshape(-1), non_blocking=True)
+            dep.copy_(target_depth.reshape(-1), non_blocking=True)
+            T0.copy_(T_init.reshape(3, 4), non_blocking=True)
+            self._staged[slot].record(self._copy_stream)
+        cur.wait_event(self._staged[slot])
+        self.set_frame(col, dep, T0)
+        self._consumed[slot].record(cur)
+        self.run()
+        status = torch.empty(2, dtype=torch.int32).pin_memory()
+        out.copy_(state_pose(self.state)[0], non_blocking=True)
+        status.copy_(self.rast.status[:2], non_blocking=True)
+        self._pending.append((target_color, target_depth, T_init, out, status))
+
+    def drain(self, max_retries: int = 3) -> int:
+        """Wait for every submitted frame; a frame whose pair buffer overflowed
+        is tracked again (synchronously, with a larger buffer) into its
+        ``out``. Returns the number of frames completed; raises GsError for any
+        other device status."""
+        torch.cuda.current_stream().synchronize()
+        pending, self._pending = getattr(self, "_pending", []), []
+        for color, depth, T_init, out, status in pending:
+            code = int(status[0])
+            if code == A.GS_ERR_CAPACITY:
+                self.track_host(color, depth, T_init, out)
+            elif code != 0:
+                raise A.GsError(code, "device status during tracking")
+        return len(pending)
+
     def track(self, target_color, target_depth, T_init, max_retries: int = 3) -> torch.Tensor:
         """Track one frame; returns the refined pose [3,4] (FP64, on device).
         Grows the pair capacity (and re-captures the graph) on overflow."""

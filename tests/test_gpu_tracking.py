@@ -225,6 +225,60 @@ def test_tracker_recovers_from_pair_overflow(room_small, fused):
     assert torch.equal(got, ref.track(tcol, tdep, T0))
 
 
+def _host_frames(sc, cam, poses, seeds):
+    """Pinned host RGB-D targets and start poses of a few frames."""
+    hc, hd, hT = [], [], []
+    for k, seed in enumerate(seeds):
+        tcol, tdep = _targets(sc, cam, poses[k % len(poses)])
+        hc.append(tcol.cpu().pin_memory())
+        hd.append(tdep.cpu().pin_memory())
+        hT.append(torch.from_numpy(synth.jitter_pose(poses[k % len(poses)], seed=seed)).pin_memory())
+    return hc, hd, hT
+
+
+def test_streaming_submit_equals_track_host(room_small):
+    """Tracker.submit/drain (uploads on a copy stream into two staging buffers,
+    overlapped with the tracking of the previous frame) gives, frame by frame,
+    the same poses as the synchronous track_host; six frames reuse each staging
+    buffer three times."""
+    from paper_2403_16095_b300 import Tracker
+    sc, cam, poses = room_small
+    g = to_gpu_gaussians(sc)
+    hc, hd, hT = _host_frames(sc, cam, poses, seeds=[21, 22, 23, 24, 25, 26])
+    tr = Tracker(g, cam, iters=10, graph=True)
+    tr.prepare(hc[0].cuda(), hd[0].cuda(), hT[0])
+    ref = [tr.track_host(hc[k], hd[k], hT[k]) for k in range(6)]
+    outs = [torch.full((3, 4), float("nan"), dtype=torch.float64).pin_memory() for _ in range(6)]
+    for k in range(6):
+        tr.submit(hc[k], hd[k], hT[k], outs[k])
+    assert tr.drain() == 6
+    for k in range(6):
+        assert torch.equal(outs[k], ref[k]), k
+    assert not torch.equal(ref[0], ref[1])
+
+
+def test_streaming_redoes_frames_that_overflowed(room_small):
+    """Frames submitted to a tracker whose pair buffer is far too small all
+    overflow on the device; drain() tracks each of them again synchronously
+    (growing the buffer) and their poses equal a correctly sized tracker's."""
+    from paper_2403_16095_b300 import Tracker
+    sc, cam, poses = room_small
+    g = to_gpu_gaussians(sc)
+    hc, hd, hT = _host_frames(sc, cam, poses, seeds=[31, 32, 33])
+    small = Tracker(g, cam, iters=10, graph=True, capacity=64)
+    small.set_frame(hc[0].cuda(), hd[0].cuda(), hT[0])
+    small._capture()
+    outs = [torch.empty(3, 4, dtype=torch.float64).pin_memory() for _ in range(3)]
+    for k in range(3):
+        small.submit(hc[k], hd[k], hT[k], outs[k])
+    small.drain()
+    assert small.rast.capacity > 64
+    ref = Tracker(g, cam, iters=10, graph=True)
+    ref.prepare(hc[0].cuda(), hd[0].cuda(), hT[0])
+    for k in range(3):
+        assert torch.equal(outs[k], ref.track_host(hc[k], hd[k], hT[k])), k
+
+
 def test_tracking_pass_with_every_gaussian_culled():
     """All Gaussians behind the camera: the tracking pass renders nothing, the
     pose gradient is exactly zero, and the Adam step leaves the pose unchanged."""
