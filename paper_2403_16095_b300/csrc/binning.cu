@@ -427,14 +427,17 @@ __device__ void cta_sort_regs(const uint64_t *keys, int n, uint64_t *s_a) {
     }
     for (int size = 2; size <= NP; size <<= 1) {
         for (int stride = size >> 1; stride >= K; stride >>= 1) {
-            if (stride >= 32 * K) {  // partner in another warp
+            if (stride >= 32 * K) {  // partner in another warp: exchange through shared
+                // memory, position q at s_a[(q % K) kThreads + q / K] (consecutive
+                // threads on consecutive words: no bank conflicts)
 #pragma unroll
-                for (int j = 0; j < K; ++j) s_a[t * K + j] = x[j];
+                for (int j = 0; j < K; ++j) s_a[j * kThreads + t] = x[j];
                 __syncthreads();
 #pragma unroll
                 for (int j = 0; j < K; ++j) {
                     const int p = t * K + j;
-                    const uint64_t y = s_a[p ^ stride];
+                    const int q = p ^ stride;
+                    const uint64_t y = s_a[(q % K) * kThreads + q / K];
                     const bool keep_min = ((p & stride) == 0) == ((p & size) == 0);
                     x[j] = keep_min ? (y < x[j] ? y : x[j]) : (y > x[j] ? y : x[j]);
                 }
@@ -470,9 +473,62 @@ __device__ void cta_sort_regs(const uint64_t *keys, int n, uint64_t *s_a) {
     __syncthreads();
 }
 
+// Bitonic sort of n <= 32 K keys by one warp with the keys in registers: lane
+// l holds positions l K .. l K + K - 1 (padding = the all-ones key). Strides
+// below K stay in the thread, the others are shuffles; no shared memory. The
+// sorted keys go to values[s + i] (record index) and, if keys_out, to
+// keys_out[s + i] (tile << 32 | depth bits).
+template <int K>
+__device__ void warp_sort_regs(const uint64_t *__restrict__ keys, int n, uint32_t *__restrict__ values,
+                               uint64_t *__restrict__ keys_out, uint32_t s, uint32_t tile) {
+    constexpr int NP = 32 * K;
+    const int lane = threadIdx.x & 31;
+    uint64_t x[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int p = lane * K + j;
+        x[j] = p < n ? keys[p] : ~0ull;
+    }
+#pragma unroll
+    for (int size = 2; size <= NP; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride >= K; stride >>= 1) {
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                const int p = lane * K + j;
+                const uint64_t y = __shfl_xor_sync(0xffffffffu, x[j], stride / K);
+                const bool keep_min = ((p & stride) == 0) == ((p & size) == 0);
+                x[j] = keep_min ? (y < x[j] ? y : x[j]) : (y > x[j] ? y : x[j]);
+            }
+        }
+#pragma unroll
+        for (int stride = K / 2; stride > 0; stride >>= 1) {
+            if (stride >= size) continue;
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                if (j & stride) continue;
+                const uint64_t a = x[j], b = x[j + stride];
+                const bool up = ((lane * K + j) & size) == 0;
+                if ((a > b) == up) {
+                    x[j] = b;
+                    x[j + stride] = a;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int p = lane * K + j;
+        if (p < n) {
+            values[s + p] = (uint32_t)x[j];
+            if (keys_out) keys_out[s + p] = ((uint64_t)tile << 32) | (x[j] >> 32);
+        }
+    }
+}
+
 // k_tile_sort: heaviest tiles first when the launch order is given. With the
 // order, tiles of fewer than kWarpSortKeys entries (most of them) are sorted one
-// per warp, 8 per CTA, with warp barriers only; the others take one CTA each.
+// per warp, 8 per CTA, in registers (warp_sort_regs); the others take one CTA each.
 // Bitonic networks (low keys are unique within a bucket, so the result is the
 // same as a stable radix sort). A CTA sorts its bucket with the keys in
 // registers (cta_sort_regs); buckets of more than kSmemKeys keys take the LSD
@@ -487,42 +543,21 @@ __global__ void __launch_bounds__(kThreads, 4)
     __shared__ uint64_t s_a[kSmemKeys];
     __shared__ uint32_t s_wh[kWarps][kRadix];
     __shared__ uint32_t s_warp[kWarps];
-    static_assert(kWarps * kWarpSortKeys <= kSmemKeys, "warp buckets share s_a");
     if (!status_ok(status)) return;
     const int tid = threadIdx.x;
     const int n_large = order ? misc[1] : n_tiles;
     if ((int)blockIdx.x >= n_large) {  // one short tile per warp
-        const int lane = tid & 31, warp = tid >> 5;
+        const int warp = tid >> 5;
         const int ti = n_large + ((int)blockIdx.x - n_large) * kWarps + warp;
         if (ti >= n_tiles) return;
         const int tile = (int)order[ti];
         const uint32_t s = ranges[2 * (size_t)tile], e = ranges[2 * (size_t)tile + 1];
         const int n = (int)(e - s);
-        if (n <= 0) return;
-        uint64_t *wa = s_a + warp * kWarpSortKeys;
-        int np = 2;
-        while (np < n) np <<= 1;
-        for (int i = lane; i < np; i += 32) wa[i] = i < n ? low_keys[s + i] : ~0ull;
-        __syncwarp();
-        for (int size = 2; size <= np; size <<= 1)
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int t = lane; t < (np >> 1); t += 32) {
-                    const int i = ((t & ~(stride - 1)) << 1) | (t & (stride - 1));
-                    const int j = i + stride;
-                    const uint64_t x = wa[i], y = wa[j];
-                    const bool up = (i & size) == 0;
-                    if ((x > y) == up) {
-                        wa[i] = y;
-                        wa[j] = x;
-                    }
-                }
-                __syncwarp();
-            }
-        for (int i = lane; i < n; i += 32) {
-            const uint64_t k = wa[i];
-            values[s + i] = (uint32_t)k;
-            if (keys_out) keys_out[s + i] = ((uint64_t)tile << 32) | (k >> 32);
-        }
+        if (n <= 0) return;  // n is the same on the whole warp
+        if (n <= 32) warp_sort_regs<1>(low_keys + s, n, values, keys_out, s, (uint32_t)tile);
+        else if (n <= 64) warp_sort_regs<2>(low_keys + s, n, values, keys_out, s, (uint32_t)tile);
+        else if (n <= 128) warp_sort_regs<4>(low_keys + s, n, values, keys_out, s, (uint32_t)tile);
+        else warp_sort_regs<8>(low_keys + s, n, values, keys_out, s, (uint32_t)tile);
         return;
     }
     const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
