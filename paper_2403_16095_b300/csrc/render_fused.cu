@@ -30,6 +30,8 @@ namespace {
 
 __device__ __forceinline__ float sgn_f(float v) { return v > 0.f ? 1.f : (v < 0.f ? -1.f : 0.f); }
 
+constexpr int kCullGroups = 64;  // cached warp-cull ballots per warp: lists of up to 2,048 entries
+
 template <int TILE>
 struct FusedSmem {
     static constexpr int NT = TILE * TILE;
@@ -69,6 +71,10 @@ __global__ void __launch_bounds__(TILE *TILE, MINB)
     __shared__ uint32_t s_wmax[NWARP];
     __shared__ df s_wdf[NWARP][6];
     __shared__ int s_flag;
+    // the forward's warp-cull ballot of every 32-entry group of the list (first
+    // kCullGroups groups): the backward walks the same entries with the same
+    // warp and reuses them instead of evaluating warp_block_may_hit again
+    __shared__ uint32_t s_cull[NWARP][kCullGroups];
     if (status[0] != 0) return;
 
     const int gtile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;  // heaviest tiles first
@@ -119,6 +125,8 @@ __global__ void __launch_bounds__(TILE *TILE, MINB)
                 const int kt = g0 + lane;
                 const bool hit = kt < cnt && warp_block_may_hit(s_a[kt], s_b[kt], s_r[kt], wx0, wy0);
                 unsigned mask = __ballot_sync(0xffffffffu, hit);
+                const int gi = ((int)(base - range.x) + g0) >> 5;
+                if (lane == 0 && gi < kCullGroups) s_cull[warp][gi] = mask;
                 while (mask) {  // surviving entries, front to back
                     const int k = g0 + __ffs(mask) - 1;
                     mask &= mask - 1;
@@ -196,11 +204,18 @@ __global__ void __launch_bounds__(TILE *TILE, MINB)
             __syncthreads();
         }
         const int cnt = bend - bstart;
-        for (int g1 = cnt, g0 = max(0, cnt - 32); g1 > 0; g1 = g0, g0 = max(0, g0 - 32)) {
+        // groups aligned with the forward's (batch start + 32 i), last first
+        for (int g0 = ((cnt - 1) >> 5) << 5; g0 >= 0; g0 -= 32) {
             const int kt = g0 + lane;
-            const bool hit = kt < g1 && (uint32_t)(bstart + kt) < warp_last &&
-                             warp_block_may_hit(s_a[kt], s_b[kt], s_r[kt], wx0, wy0);
-            unsigned mask = __ballot_sync(0xffffffffu, hit);
+            const bool live = kt < cnt && (uint32_t)(bstart + kt) < warp_last;
+            const int gi = (bstart - (int)range.x + g0) >> 5;
+            unsigned mask;
+            if (gi < kCullGroups) {
+                __syncwarp();
+                mask = __ballot_sync(0xffffffffu, live) & s_cull[warp][gi];
+            } else {
+                mask = __ballot_sync(0xffffffffu, live && warp_block_may_hit(s_a[kt], s_b[kt], s_r[kt], wx0, wy0));
+            }
             while (mask) {  // surviving entries, back to front
                 const int bit = 31 - __clz(mask);
                 mask &= ~(1u << bit);
