@@ -40,6 +40,40 @@ __device__ __forceinline__ df df_warp_sum(df v) {
     return v;
 }
 
+// Warp sum of six FP32 values per lane as double-floats, by recursive halving:
+// at each of three steps (lane bits 4, 3, 2) a lane keeps half of its slots
+// (8 slots, the last two zero) and adds its partner's copy of them, then two
+// full butterfly steps (lane bits 1, 0) finish. Lane l ends with the total of
+// slot ((l >> 4) & 1) * 4 + ((l >> 3) & 1) * 2 + ((l >> 2) & 1), written to
+// `slot`; the four lanes sharing bits 2-4 hold the same value (df_add is
+// symmetric). A fixed order, so the result is deterministic; ~14 shuffles
+// instead of 60 for six separate butterflies.
+__device__ __forceinline__ df df_warp_sum6(const float v[6], int &slot) {
+    const int lane = threadIdx.x & 31;
+    const bool up4 = (lane & 16) != 0, up3 = (lane & 8) != 0, up2 = (lane & 4) != 0;
+    df h[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float lo_slot = v[i], hi_slot = i + 4 < 6 ? v[i + 4] : 0.f;
+        const float keep = up4 ? hi_slot : lo_slot, send = up4 ? lo_slot : hi_slot;
+        h[i] = df_two_sum(keep, __shfl_xor_sync(0xffffffffu, send, 16));
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const df keep = up3 ? h[i + 2] : h[i], send = up3 ? h[i] : h[i + 2];
+        h[i] = df_add(keep, df{__shfl_xor_sync(0xffffffffu, send.hi, 8), __shfl_xor_sync(0xffffffffu, send.lo, 8)});
+    }
+    {
+        const df keep = up2 ? h[1] : h[0], send = up2 ? h[0] : h[1];
+        h[0] = df_add(keep, df{__shfl_xor_sync(0xffffffffu, send.hi, 4), __shfl_xor_sync(0xffffffffu, send.lo, 4)});
+    }
+#pragma unroll
+    for (int o = 2; o > 0; o >>= 1)
+        h[0] = df_add(h[0], df{__shfl_xor_sync(0xffffffffu, h[0].hi, o), __shfl_xor_sync(0xffffffffu, h[0].lo, o)});
+    slot = (up4 ? 4 : 0) + (up3 ? 2 : 0) + (up2 ? 1 : 0);
+    return h[0];
+}
+
 }  // namespace gs
 
 namespace gs {

@@ -308,16 +308,22 @@ __global__ void __launch_bounds__(kProjThreads)
     __shared__ df s_red[kRedSlots][6];
     __shared__ int s_flag;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // frames in which this Gaussian was visible: the rects of all frames are
+    // loaded up front, side by side, rather than one round trip per frame
+    uint64_t live_mask = 0;
+    if (valid_i) {
+#pragma unroll 8
+        for (int f = 0; f < ft.n; ++f) {
+            const int4 rc = reinterpret_cast<const int4 *>(rec + ((size_t)f * n + i) * kRecFloats)[3];
+            if (rc.x <= rc.z) live_mask |= 1ull << f;
+        }
+    }
 
     for (int f = 0; f < ft.n; ++f) {
         const FrameDesc &fd = ft.f[f];
         float pc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         const size_t r = (size_t)f * n + i;
-        bool live = valid_i;
-        if (live) {
-            const int4 rc = reinterpret_cast<const int4 *>(rec + r * kRecFloats)[3];
-            live = rc.x <= rc.z;
-        }
+        const bool live = ((live_mask >> f) & 1ull) != 0;
         if (live) {
             float W[3][3], t[3];
             load_pose(T_cw + 12 * f, W, t);
@@ -417,13 +423,15 @@ __global__ void __launch_bounds__(kProjThreads)
             pc[4] += 2.f * Z[2][0];
             pc[5] += 2.f * Z[0][1];
         }
-        // this warp's pose sum for frame f (double-float, fixed butterfly); the
-        // CTA combines the warps once, after the frame loop, so the loop has no
-        // CTA barrier
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            const df v = df_warp_sum(df{pc[k], 0.f});
-            if (lane == 0) s_pf[f][warp][k] = v;
+        // this warp's pose sum for frame f (double-float, fixed halving order);
+        // the CTA combines the warps once, after the frame loop, so the loop
+        // has no CTA barrier
+        if (__any_sync(0xffffffffu, live)) {
+            int slot;
+            const df v = df_warp_sum6(pc, slot);
+            if ((lane & 3) == 0 && slot < 6) s_pf[f][warp][slot] = v;
+        } else if (lane < 6) {
+            s_pf[f][warp][lane] = df{0.f, 0.f};
         }
     }
     // per-CTA pose partial of every frame (warps summed in order: the same
