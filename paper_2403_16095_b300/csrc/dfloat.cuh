@@ -115,11 +115,9 @@ __device__ __forceinline__ void reduce_pose_partials(const float *p, int K, doub
 // writes the partial (hi, lo pairs) to out12. s_w: [n_warps][6] double-floats.
 __device__ __forceinline__ void cta_pose_partial(const float acc[6], float *out12, df (*s_w)[6]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        const df v = df_warp_sum(df{acc[k], 0.f});
-        if (lane == 0) s_w[warp][k] = v;
-    }
+    int slot;
+    const df v = df_warp_sum6(acc, slot);
+    if ((lane & 3) == 0 && slot < 6) s_w[warp][slot] = v;
     __syncthreads();
     if (threadIdx.x < 6) {
         df s = {0.f, 0.f};
