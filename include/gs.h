@@ -59,7 +59,7 @@ extern "C" {
 #endif
 
 #define GS_MAX_FRAMES 64
-#define GS_ABI_VERSION 7
+#define GS_ABI_VERSION 8
 
 typedef struct CUstream_st *gs_stream; /* a cudaStream_t; NULL = legacy default stream */
 
@@ -259,6 +259,22 @@ size_t gs_bin_tiles_workspace_size(int n_records, int capacity);
 gs_status gs_bin_tiles(const gs_projected *proj, int n_frames, const gs_camera *cams,
                        const gs_opts *opts, gs_tiles *tiles, int32_t *status, void *ws,
                        size_t ws_bytes, gs_stream stream);
+
+/* gs_project (gs_project_bf16) followed by gs_bin_tiles, in one call: the
+ * projection kernel also counts each visible record's (record, tile) pairs into
+ * the tile counters, so the binning skips its count pass (one pass over the
+ * records and one launch fewer). Arguments: those of the two calls (ws: the
+ * binning workspace); the same validation; outputs (records, tiles_touched,
+ * pose_jac, tiles) bit-identical to the two calls. It pays for one frame at a
+ * time (tracking: 199.7 -> 196.5 us per iteration at 640x480 / 300k); on
+ * multi-frame batches the separate count kernel, 8 records per thread, is the
+ * faster one (8 x 640x480 / 1M: 0.92 vs 0.96 ms).                          */
+gs_status gs_project_bin(const gs_gaussians *g, int n_frames, const gs_camera *cams, const float *T_cw,
+                         const gs_opts *opts, gs_projected *out, gs_tiles *tiles, int32_t *status,
+                         void *ws, size_t ws_bytes, gs_stream stream);
+gs_status gs_project_bin_bf16(const gs_gaussians_bf16 *g, int n_frames, const gs_camera *cams,
+                              const float *T_cw, const gs_opts *opts, gs_projected *out, gs_tiles *tiles,
+                              int32_t *status, void *ws, size_t ws_bytes, gs_stream stream);
 
 /* gs_bin_tiles for callers that cannot allocate device memory (the paper has no
  * counterpart; this is an interface convenience). Some callers cannot call

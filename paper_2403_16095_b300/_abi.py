@@ -98,9 +98,10 @@ class gs_adam(C.Structure):
 EXPORTS = ("gs_abi_version", "gs_last_error", "gs_project", "gs_bin_tiles_workspace_size", "gs_bin_tiles",
            "gs_bin_tiles_noalloc", "gs_render_fwd", "gs_pose_partials_per_frame", "gs_render_bwd_workspace_size",
            "gs_render_bwd", "gs_render_fwd_bwd_pose", "gs_project_bf16", "gs_spatial_order_workspace_size", "gs_spatial_order",
-           "gs_pack_bf16", "gs_nu_accumulate", "gs_nu_finalize", "gs_pose_grad_reduce", "gs_pose_adam_step")
+           "gs_pack_bf16", "gs_nu_accumulate", "gs_nu_finalize", "gs_pose_grad_reduce", "gs_pose_adam_step",
+           "gs_project_bin", "gs_project_bin_bf16")
 GS_NOALLOC_MAX_PAIRS = 1 << 19
-ABI_VERSION = 7  # GS_ABI_VERSION of the gs.h these structures mirror
+ABI_VERSION = 8  # GS_ABI_VERSION of the gs.h these structures mirror
 
 
 def _load():
@@ -123,6 +124,12 @@ def _load():
     lib.gs_bin_tiles_workspace_size.restype = C.c_size_t
     lib.gs_bin_tiles.argtypes = [C.POINTER(gs_projected), C.c_int, C.POINTER(gs_camera), C.POINTER(gs_opts),
                                  C.POINTER(gs_tiles), _vp, _vp, C.c_size_t, _vp]
+    lib.gs_project_bin.argtypes = [C.POINTER(gs_gaussians), C.c_int, C.POINTER(gs_camera), _vp,
+                                   C.POINTER(gs_opts), C.POINTER(gs_projected), C.POINTER(gs_tiles), _vp, _vp,
+                                   C.c_size_t, _vp]
+    lib.gs_project_bin_bf16.argtypes = [C.POINTER(gs_gaussians_bf16), C.c_int, C.POINTER(gs_camera), _vp,
+                                        C.POINTER(gs_opts), C.POINTER(gs_projected), C.POINTER(gs_tiles), _vp, _vp,
+                                        C.c_size_t, _vp]
     lib.gs_bin_tiles_noalloc.argtypes = [C.POINTER(gs_projected), C.c_int, C.POINTER(gs_camera),
                                          C.POINTER(gs_opts), C.POINTER(gs_tiles), _vp, _vp]
     lib.gs_bin_tiles_noalloc.restype = C.c_int
@@ -316,6 +323,29 @@ def gs_bin_tiles(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tensor, tiles
     _check(lib.gs_bin_tiles(C.byref(proj), F, cameras(cams), C.byref(opts), C.byref(tiles),
                             _ptr(status, torch.int32, "status", 4), _ptr(ws, torch.uint8, "ws"), ws.numel(),
                             _stream(stream)))
+
+
+def gs_project_bin(g, cams, T_cw: torch.Tensor, opts: gs_opts, rec: torch.Tensor, tiles_touched: torch.Tensor,
+                   pose_jac: Optional[torch.Tensor], values: torch.Tensor, keys: Optional[torch.Tensor],
+                   ranges: torch.Tensor, status: torch.Tensor, ws: torch.Tensor, stream=None,
+                   order: Optional[torch.Tensor] = None) -> None:
+    """gs_project (g: Gaussians) or gs_project_bf16 (g: PackedGaussians) and
+    gs_bin_tiles in one call, the projection counting the pairs."""
+    F = len(cams)
+    M = F * g.n
+    proj = gs_projected(g.n, F, _ptr(rec, torch.float32, "rec", M * GS_REC_FLOATS),
+                        _ptr(tiles_touched, torch.int32, "tiles_touched", M),
+                        _ptr(pose_jac, torch.float32, "pose_jac", M * GS_JAC_FLOATS))
+    cap = values.numel()
+    if keys is not None and keys.numel() < cap:
+        raise ValueError("keys must hold as many entries as values")
+    tiles = gs_tiles(cap, ranges.numel() // 2, _ptr(values, torch.int32, "values"),
+                     _ptr(keys, torch.int64, "keys"), _ptr(ranges, torch.int32, "ranges"),
+                     _ptr(order, torch.int32, "order", ranges.numel() // 2))
+    fn = lib.gs_project_bin_bf16 if isinstance(g, PackedGaussians) else lib.gs_project_bin
+    _check(fn(C.byref(g.struct()), F, cameras(cams), _ptr(T_cw, torch.float32, "T_cw", 12 * F), C.byref(opts),
+              C.byref(proj), C.byref(tiles), _ptr(status, torch.int32, "status", 4), _ptr(ws, torch.uint8, "ws"),
+              ws.numel(), _stream(stream)))
 
 
 def gs_bin_tiles_noalloc(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tensor, tiles_touched: torch.Tensor,

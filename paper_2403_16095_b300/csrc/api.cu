@@ -137,7 +137,7 @@ gs_status gs_project(const gs_gaussians *g, int n_frames, const gs_camera *cams,
     if (opts->mode == GS_MODE_POSE && (!out->pose_jac || !aligned(out->pose_jac, 16)))
         return fail(GS_ERR_INVALID_ARG, "POSE mode needs a 16-byte aligned pose_jac");
     return cuda_status(gs::launch_project(gauss_ptrs(g), g->n, ft, T_cw, opts->jclamp, opts->nu_cull, opts->mode,
-                                          out->rec, out->tiles_touched, out->pose_jac, status, stream),
+                                          out->rec, out->tiles_touched, out->pose_jac, nullptr, status, stream),
                        "gs_project");
 }
 
@@ -157,7 +157,8 @@ gs_status gs_project_bf16(const gs_gaussians_bf16 *g, int n_frames, const gs_cam
     if (opts->mode == GS_MODE_POSE && (!out->pose_jac || !aligned(out->pose_jac, 16)))
         return fail(GS_ERR_INVALID_ARG, "POSE mode needs a 16-byte aligned pose_jac");
     return cuda_status(gs::launch_project_bf16(g->anchors, g->packed, g->n, ft, T_cw, opts->jclamp, opts->nu_cull,
-                                               opts->mode, out->rec, out->tiles_touched, out->pose_jac, status, stream),
+                                               opts->mode, out->rec, out->tiles_touched, out->pose_jac, nullptr, status,
+                                               stream),
                        "gs_project_bf16");
 }
 
@@ -205,6 +206,76 @@ gs_status gs_bin_tiles(const gs_projected *proj, int n_frames, const gs_camera *
     return cuda_status(gs::launch_bin_tiles(proj->rec, proj->tiles_touched, M, npf, ft, tiles->capacity, tiles->values,
                                             tiles->keys, tiles->ranges, tiles->order, status, ws, stream),
                        "gs_bin_tiles");
+}
+
+// gs_project (or gs_project_bf16) followed by gs_bin_tiles in one call, with
+// the pair count done by the projection kernel: clear, project + count, scan,
+// fill, sort. The arguments are those of the two calls; validated the same way.
+namespace {
+gs_status check_bin_call(const gs_projected *out, int n_frames, const gs::FrameTable &ft, const gs_tiles *tiles,
+                         const int32_t *status, const void *ws, size_t ws_bytes) {
+    GS_TRY(check_tiles(tiles, ft));
+    if (!status) return fail(GS_ERR_INVALID_ARG, "status NULL");
+    const size_t need = gs::bin_workspace_bytes(out->n_gaussians * n_frames, tiles->capacity);
+    if (!ws || ws_bytes < need) return fail(GS_ERR_INVALID_ARG, "workspace %zu bytes < %zu needed", ws_bytes, need);
+    if (!aligned(ws, 256)) return fail(GS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    return GS_OK;
+}
+
+gs_status bin_after_counting_projection(const gs_projected *out, int n_frames, const gs::FrameTable &ft,
+                                        gs_tiles *tiles, int32_t *status, void *ws, gs_stream stream) {
+    const int npf = out->n_gaussians > 0 ? out->n_gaussians : 1;
+    return cuda_status(gs::launch_bin_tiles(out->rec, out->tiles_touched, out->n_gaussians * n_frames, npf, ft,
+                                            tiles->capacity, tiles->values, tiles->keys, tiles->ranges, tiles->order,
+                                            status, ws, stream, true),
+                       "gs_project_bin (binning)");
+}
+}  // namespace
+
+gs_status gs_project_bin(const gs_gaussians *g, int n_frames, const gs_camera *cams, const float *T_cw,
+                         const gs_opts *opts, gs_projected *out, gs_tiles *tiles, int32_t *status, void *ws,
+                         size_t ws_bytes, gs_stream stream) {
+    GS_TRY(check_gauss(g));
+    GS_TRY(check_opts(opts));
+    gs::FrameTable ft;
+    GS_TRY(make_frames(n_frames, cams, opts->tile, ft));
+    GS_TRY(check_proj(out, n_frames));
+    if (out->n_gaussians != g->n) return fail(GS_ERR_INVALID_ARG, "projected.n_gaussians != gaussians.n");
+    if (!T_cw) return fail(GS_ERR_INVALID_ARG, "T_cw NULL");
+    if (opts->mode == GS_MODE_POSE && (!out->pose_jac || !aligned(out->pose_jac, 16)))
+        return fail(GS_ERR_INVALID_ARG, "POSE mode needs a 16-byte aligned pose_jac");
+    GS_TRY(check_bin_call(out, n_frames, ft, tiles, status, ws, ws_bytes));
+    GS_TRY(cuda_status(gs::launch_bin_clear(tiles->ranges, ft, tiles->capacity, ws, stream), "gs_project_bin (clear)"));
+    GS_TRY(cuda_status(gs::launch_project(gauss_ptrs(g), g->n, ft, T_cw, opts->jclamp, opts->nu_cull, opts->mode,
+                                          out->rec, out->tiles_touched, out->pose_jac, tiles->ranges, status, stream),
+                       "gs_project_bin (projection)"));
+    return bin_after_counting_projection(out, n_frames, ft, tiles, status, ws, stream);
+}
+
+gs_status gs_project_bin_bf16(const gs_gaussians_bf16 *g, int n_frames, const gs_camera *cams, const float *T_cw,
+                              const gs_opts *opts, gs_projected *out, gs_tiles *tiles, int32_t *status, void *ws,
+                              size_t ws_bytes, gs_stream stream) {
+    if (!g) return fail(GS_ERR_INVALID_ARG, "gaussians is NULL");
+    if (g->n < 0) return fail(GS_ERR_INVALID_ARG, "n < 0");
+    if (g->n > 0 && (!g->anchors || !g->packed)) return fail(GS_ERR_INVALID_ARG, "anchors/packed NULL");
+    if (!aligned(g->anchors, 16) || !aligned(g->packed, 16)) return fail(GS_ERR_INVALID_ARG, "anchors/packed must be 16-byte aligned");
+    GS_TRY(check_opts(opts));
+    if (opts->mode == GS_MODE_FULL) return fail(GS_ERR_UNSUPPORTED, "FULL mode needs FP32 parameters (gs_project_bin)");
+    gs::FrameTable ft;
+    GS_TRY(make_frames(n_frames, cams, opts->tile, ft));
+    GS_TRY(check_proj(out, n_frames));
+    if (out->n_gaussians != g->n) return fail(GS_ERR_INVALID_ARG, "projected.n_gaussians != gaussians.n");
+    if (!T_cw) return fail(GS_ERR_INVALID_ARG, "T_cw NULL");
+    if (opts->mode == GS_MODE_POSE && (!out->pose_jac || !aligned(out->pose_jac, 16)))
+        return fail(GS_ERR_INVALID_ARG, "POSE mode needs a 16-byte aligned pose_jac");
+    GS_TRY(check_bin_call(out, n_frames, ft, tiles, status, ws, ws_bytes));
+    GS_TRY(cuda_status(gs::launch_bin_clear(tiles->ranges, ft, tiles->capacity, ws, stream),
+                       "gs_project_bin_bf16 (clear)"));
+    GS_TRY(cuda_status(gs::launch_project_bf16(g->anchors, g->packed, g->n, ft, T_cw, opts->jclamp, opts->nu_cull,
+                                               opts->mode, out->rec, out->tiles_touched, out->pose_jac, tiles->ranges,
+                                               status, stream),
+                       "gs_project_bin_bf16 (projection)"));
+    return bin_after_counting_projection(out, n_frames, ft, tiles, status, ws, stream);
 }
 
 gs_status gs_render_fwd(const gs_projected *proj, const gs_tiles *tiles, int n_frames, const gs_camera *cams,

@@ -98,12 +98,14 @@ void set_error_message(const char *msg);
 
 // ----------------------------------------------------------------- launchers
 // project.cu
+// tile_counts: NULL, or the tile counters (ranges) of a following binning,
+// zeroed by launch_bin_clear: the projection then also counts the pairs
 cudaError_t launch_project(const GaussPtrs &g, int n, const FrameTable &ft, const float *T_cw, float jclamp,
-                           float nu_cull, int mode, float *rec, int *touched, float *jac, const int32_t *status,
-                           cudaStream_t s);
+                           float nu_cull, int mode, float *rec, int *touched, float *jac, uint32_t *tile_counts,
+                           const int32_t *status, cudaStream_t s);
 cudaError_t launch_project_bf16(const float *anchors, const uint16_t *packed, int n, const FrameTable &ft,
                                 const float *T_cw, float jclamp, float nu_cull, int mode, float *rec, int *touched,
-                                float *jac, const int32_t *status, cudaStream_t s);
+                                float *jac, uint32_t *tile_counts, const int32_t *status, cudaStream_t s);
 cudaError_t launch_project_bwd(const GaussPtrs &g, int n, const FrameTable &ft, const float *T_cw, float jclamp,
                                const float *rec, const float *grad2d, gs_grads grads, float *pose_partials,
                                int per_frame, double *pose_grad, unsigned *counters, const int32_t *status,
@@ -112,7 +114,10 @@ cudaError_t launch_project_bwd(const GaussPtrs &g, int n, const FrameTable &ft, 
 size_t bin_workspace_bytes(int n_records, int capacity);
 cudaError_t launch_bin_tiles(const float *rec, const int *touched, int n_records, int n_per_frame,
                              const FrameTable &ft, int capacity, uint32_t *values, uint64_t *keys_out,
-                             uint32_t *ranges, uint32_t *order, int32_t *status, void *ws, cudaStream_t s);
+                             uint32_t *ranges, uint32_t *order, int32_t *status, void *ws, cudaStream_t s,
+                             bool counted = false);  // counted: clear + count already done (counting projection)
+// zeroes the tile counters and the binning's scalars (ws) ahead of a counting projection
+cudaError_t launch_bin_clear(uint32_t *ranges, const FrameTable &ft, int capacity, void *ws, cudaStream_t s);
 // render_fwd.cu
 cudaError_t launch_render_fwd(const float *rec, const uint32_t *values, const uint32_t *ranges, const uint32_t *order,
                               const FrameTable &ft, const float *obs_depth, const ImagePtrs &out,

@@ -10,6 +10,7 @@
 //                quaternion, opacity logit, colour and nu (summed over frames,
 //                no atomics) and writes one FP64 pose partial per (frame, CTA).
 #include "gs_internal.cuh"
+#include "pairs.cuh"
 #include "dfloat.cuh"
 
 namespace gs {
@@ -185,32 +186,62 @@ __device__ __forceinline__ void write_culled(float *rec, int *touched, size_t r)
     touched[r] = 0;
 }
 
-template <bool JAC, class Src>
+// COUNT: the projection also counts the (record, tile) pairs of the visible
+// records into the tile counters ranges[2 t + 1] (zeroed before the launch),
+// with the same warp-balanced walk and warp-aggregated atomics as
+// k_tile_count, so that the binning can skip its count pass. Every lane then
+// stays to the end of the walk (no early return).
+template <bool JAC, bool COUNT, class Src>
 __global__ void __launch_bounds__(kProjThreads)
     k_project(Src src, int n, FrameTable ft, const float *__restrict__ T_cw, float jclamp, float nu_cull,
               float *__restrict__ rec, int *__restrict__ touched, float *__restrict__ jac,
-              const int32_t *__restrict__ status) {
+              uint32_t *__restrict__ ranges, const int32_t *__restrict__ status) {
     dep_wait();
     if (status[0] != 0) return;
     const int i = blockIdx.x * kProjThreads + threadIdx.x;
     const int f = blockIdx.y;
-    if (i >= n) return;
+    if (!COUNT && i >= n) return;
     const FrameDesc &fd = ft.f[f];
     const size_t r = (size_t)f * n + i;
-    float W[3][3], t[3];
-    load_pose(T_cw + 12 * f, W, t);
     Geo o;
-    const typename Src::Rec G = src.fetch(i);
-    if (!geometry(src, G, fd, W, t, jclamp, nu_cull, o)) { write_culled(rec, touched, r); return; }
-
-    const float mx = fmaf(fd.fx, o.u, fd.cx), my = fmaf(fd.fy, o.v, fd.cy);
-    const float half = 0.5f * (o.a - o.c);
-    const float lam = 0.5f * (o.a + o.c) + sqrtf(fmaxf(half * half + o.b * o.b, 0.f));
-    const float rad = ceilf(3.f * sqrtf(lam));
-    const float x0 = fmaxf(0.f, ceilf(mx - 0.5f - rad)), x1 = fminf((float)(fd.W - 1), floorf(mx - 0.5f + rad));
-    const float y0 = fmaxf(0.f, ceilf(my - 0.5f - rad)), y1 = fminf((float)(fd.H - 1), floorf(my - 0.5f + rad));
-    if (!(x0 <= x1 && y0 <= y1)) { write_culled(rec, touched, r); return; }
-    const int ix0 = (int)x0, ix1 = (int)x1, iy0 = (int)y0, iy1 = (int)y1;
+    typename Src::Rec G{};
+    bool vis = false;
+    float mx = 0.f, my = 0.f, rad = 0.f;
+    int ix0 = 1, iy0 = 1, ix1 = 0, iy1 = 0;
+    if (i < n) {
+        float W[3][3], t[3];
+        load_pose(T_cw + 12 * f, W, t);
+        G = src.fetch(i);
+        if (geometry(src, G, fd, W, t, jclamp, nu_cull, o)) {
+            mx = fmaf(fd.fx, o.u, fd.cx);
+            my = fmaf(fd.fy, o.v, fd.cy);
+            const float half = 0.5f * (o.a - o.c);
+            const float lam = 0.5f * (o.a + o.c) + sqrtf(fmaxf(half * half + o.b * o.b, 0.f));
+            rad = ceilf(3.f * sqrtf(lam));
+            const float x0 = fmaxf(0.f, ceilf(mx - 0.5f - rad)), x1 = fminf((float)(fd.W - 1), floorf(mx - 0.5f + rad));
+            const float y0 = fmaxf(0.f, ceilf(my - 0.5f - rad)), y1 = fminf((float)(fd.H - 1), floorf(my - 0.5f + rad));
+            if (x0 <= x1 && y0 <= y1) {
+                vis = true;
+                ix0 = (int)x0;
+                ix1 = (int)x1;
+                iy0 = (int)y0;
+                iy1 = (int)y1;
+            }
+        }
+        if (!vis) write_culled(rec, touched, r);
+    }
+    if (COUNT) {
+        PairSrc ps{};
+        ps.valid = vis;
+        if (vis) {
+            ps.t = tile_rect(make_int4(ix0, iy0, ix1, iy1), ft.tile, fd);
+            ps.tile_off = fd.tile_off;
+            ps.tiles_x = fd.tiles_x;
+        }
+        if (__any_sync(0xffffffffu, ps.valid))
+            warp_for_each_pair(ps, [&](bool valid, int, int gt, uint32_t) { warp_claim<false>(valid, gt, ranges); });
+    }
+    if (!vis) return;
     const int ts = ft.tile;
     touched[r] = (ix1 / ts - ix0 / ts + 1) * (iy1 / ts - iy0 / ts + 1);
 
@@ -470,27 +501,34 @@ __global__ void __launch_bounds__(kProjThreads)
 
 template <class Src>
 cudaError_t launch_src(const Src &src, int n, const FrameTable &ft, const float *T_cw, float jclamp, float nu_cull,
-                       int mode, float *rec, int *touched, float *jac, const int32_t *status, cudaStream_t s) {
+                       int mode, float *rec, int *touched, float *jac, uint32_t *ranges, const int32_t *status,
+                       cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     dim3 grid((n + kProjThreads - 1) / kProjThreads, ft.n);
-    if (mode == GS_MODE_POSE)
-        return launch_chained(k_project<true, Src>, grid, dim3(kProjThreads), 0, s, src, n, ft, T_cw, jclamp, nu_cull,
-                              rec, touched, jac, status);
-    return launch_chained(k_project<false, Src>, grid, dim3(kProjThreads), 0, s, src, n, ft, T_cw, jclamp, nu_cull,
-                          rec, touched, jac, status);
+    const dim3 block(kProjThreads);
+    const bool jacob = mode == GS_MODE_POSE;
+    if (ranges)
+        return jacob ? launch_chained(k_project<true, true, Src>, grid, block, 0, s, src, n, ft, T_cw, jclamp, nu_cull,
+                                      rec, touched, jac, ranges, status)
+                     : launch_chained(k_project<false, true, Src>, grid, block, 0, s, src, n, ft, T_cw, jclamp, nu_cull,
+                                      rec, touched, jac, ranges, status);
+    return jacob ? launch_chained(k_project<true, false, Src>, grid, block, 0, s, src, n, ft, T_cw, jclamp, nu_cull,
+                                  rec, touched, jac, ranges, status)
+                 : launch_chained(k_project<false, false, Src>, grid, block, 0, s, src, n, ft, T_cw, jclamp, nu_cull,
+                                  rec, touched, jac, ranges, status);
 }
 
 cudaError_t launch_project(const GaussPtrs &g, int n, const FrameTable &ft, const float *T_cw, float jclamp,
-                           float nu_cull, int mode, float *rec, int *touched, float *jac, const int32_t *status,
-                           cudaStream_t s) {
-    return launch_src(F32Src{g}, n, ft, T_cw, jclamp, nu_cull, mode, rec, touched, jac, status, s);
+                           float nu_cull, int mode, float *rec, int *touched, float *jac, uint32_t *tile_counts,
+                           const int32_t *status, cudaStream_t s) {
+    return launch_src(F32Src{g}, n, ft, T_cw, jclamp, nu_cull, mode, rec, touched, jac, tile_counts, status, s);
 }
 
 cudaError_t launch_project_bf16(const float *anchors, const uint16_t *packed, int n, const FrameTable &ft,
                                 const float *T_cw, float jclamp, float nu_cull, int mode, float *rec, int *touched,
-                                float *jac, const int32_t *status, cudaStream_t s) {
+                                float *jac, uint32_t *tile_counts, const int32_t *status, cudaStream_t s) {
     const BF16Src src{reinterpret_cast<const float4 *>(anchors), reinterpret_cast<const uint4 *>(packed)};
-    return launch_src(src, n, ft, T_cw, jclamp, nu_cull, mode, rec, touched, jac, status, s);
+    return launch_src(src, n, ft, T_cw, jclamp, nu_cull, mode, rec, touched, jac, tile_counts, status, s);
 }
 
 cudaError_t launch_project_bwd(const GaussPtrs &g, int n, const FrameTable &ft, const float *T_cw, float jclamp,

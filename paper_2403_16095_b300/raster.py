@@ -113,6 +113,12 @@ class Rasterizer:
         A.gs_bin_tiles(self.N, self.cams, self.opts, self.rec, self.touched, self.values, self.keys, self.ranges,
                        self.status, self.bin_ws, stream, order=self.order)
 
+    def project_bin(self, g, T_cw: torch.Tensor, stream=None) -> None:
+        """project() then bin() in one call, the projection counting the pairs
+        (bit-identical outputs, one pass over the records fewer)."""
+        A.gs_project_bin(g, self.cams, T_cw, self.opts, self.rec, self.touched, self.jac, self.values, self.keys,
+                         self.ranges, self.status, self.bin_ws, stream, order=self.order)
+
     def forward(self, obs_depth: Optional[torch.Tensor] = None, stream=None) -> None:
         A.gs_render_fwd(self.N, self.cams, self.opts, self.rec, self.values, self.ranges, obs_depth, self.img,
                         self.status, stream, order=self.order)
@@ -360,8 +366,7 @@ class Tracker:
     # one iteration, enqueued on `stream`
     def _iteration(self, stream=None, it: int = 0):
         r = self.rast
-        r.project(self.g, self.T_cw, stream)
-        r.bin(stream)
+        r.project_bin(self.g, self.T_cw, stream)
         ev = self.bwd_events[it] if self.bwd_events is not None else None
         if self.fused:  # forward, backward, pose reduction and Adam step in one launch
             if ev:
@@ -379,12 +384,12 @@ class Tracker:
             A.gs_pose_adam_step(self.state, r.pose_grad, self.T_cw, 1, self.adam, r.status, stream)
 
     def kernel_launches_per_iteration(self) -> int:
-        """libgs kernels one iteration launches: project; the binning's counter
-        clear, tile count, scan, fill and per-tile sort; then either the
-        tracking pass (forward, backward, pose reduction and Adam step in one
-        launch) or the forward, the backward (with the pose reduction) and the
-        Adam step. No memsets."""
-        return 1 + 5 + (1 if self.fused else 3)
+        """libgs kernels one iteration launches: the tile-counter clear, the
+        projection (which also counts the pairs), the tile scan, fill and
+        per-tile sort; then either the tracking pass (forward, backward, pose
+        reduction and Adam step in one launch) or the forward, the backward
+        (with the pose reduction) and the Adam step. No memsets."""
+        return 5 + (1 if self.fused else 3)
 
     def _capture(self):
         """Capture all ``iters`` iterations of a frame in one CUDA graph."""

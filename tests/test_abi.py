@@ -42,7 +42,7 @@ def test_header_compiles_as_plain_c(tmp_path):
 
 
 def test_pure_host_queries(A):
-    assert A.lib.gs_abi_version() == A.ABI_VERSION == 7
+    assert A.lib.gs_abi_version() == A.ABI_VERSION == 8
     assert A.gs_bin_tiles_workspace_size(1000, 5000) >= 5000 * (8 + 8)
     assert A.gs_bin_tiles_workspace_size(10, 0) == 0
     cams = [type("C", (), dict(width=640, height=480, fx=600, fy=600, cx=320, cy=240, znear=0.2))()]
