@@ -335,7 +335,8 @@ class Tracker:
 
     def __init__(self, g, cam, tile: int = 16, iters: int = 30, lam=(0.2, 1.0), unc_tau: float = 0.025,
                  lr_rot: float = 0.0015, lr_trans: float = 0.00215, jclamp: float = 1.3, graph: bool = True,
-                 capacity: Optional[int] = None, timing: bool = False, fused: bool = True):
+                 capacity: Optional[int] = None, timing: bool = False, fused: bool = True,
+                 timing_every: int = 1):
         self.g = g
         self.cam = cam
         self.iters = iters
@@ -344,10 +345,15 @@ class Tracker:
         # otherwise gs_render_fwd then gs_render_bwd (same results, bit for bit)
         self.fused = fused
         # optional per-iteration CUDA events around each backward launch (recorded
-        # inside the captured graph as event nodes), for per-kernel timing
+        # inside the captured graph as event nodes), for per-kernel timing; with
+        # timing_every = k only iterations 0, k, 2k, ... carry them (each pair of
+        # event nodes costs ~9 us of an iteration: it also breaks the kernel-to-
+        # kernel launch chaining around the timed launch)
         self.timing = timing
+        self.timing_every = max(1, int(timing_every))
         self.bwd_events = ([(torch.cuda.Event(enable_timing=True, external=True),
-                             torch.cuda.Event(enable_timing=True, external=True)) for _ in range(iters)]
+                             torch.cuda.Event(enable_timing=True, external=True))
+                            if it % self.timing_every == 0 else None for it in range(iters)]
                            if timing else None)
         dev = (g.packed if isinstance(g, PackedGaussians) else g.means).device
         self.rast = Rasterizer([cam], g.n, tile=tile, mode=A.GS_MODE_POSE, capacity=capacity, jclamp=jclamp,
@@ -405,7 +411,7 @@ class Tracker:
         """Per-iteration duration of the backward launch in the last frame (the
         fused forward + backward launch when fused; needs timing=True and a
         completed frame)."""
-        return [a.elapsed_time(b) for a, b in self.bwd_events]
+        return [e[0].elapsed_time(e[1]) for e in self.bwd_events if e is not None]
 
     def set_frame(self, target_color: torch.Tensor, target_depth: torch.Tensor, T_init: torch.Tensor) -> None:
         self.target_color.copy_(target_color.reshape(-1), non_blocking=True)
