@@ -69,7 +69,7 @@ FWD_FLOP_PER_CONTRIB = 26
 # workload, from one ncu capture of the current kernel
 # (profiles/k_render_fused_pose_track-640x480-300k.md, cold cache); None once
 # the kernel changes.
-FUSED_DRAM_BYTES_PER_LAUNCH = 16.352768e6 + 0
+FUSED_DRAM_BYTES_PER_LAUNCH = 16.350208e6 + 0
 FP32_LANES_PER_SM = 128
 N_SM = 148
 
