@@ -38,6 +38,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kScanThreads = 1024;
+constexpr int kPassUnroll = 4;  // 32-key groups per step of a radix pass (loads issued together)
 constexpr int kSmemKeys = 2048;  // bucket size sorted entirely in shared memory
 
 __device__ __forceinline__ bool status_ok(const int32_t *status) { return status[0] == 0; }
@@ -249,12 +250,23 @@ __device__ bool cta_radix_pass(const uint64_t *src, uint64_t *dst, int n, int sh
     const int seg = (((n + kWarps - 1) / kWarps) + 31) & ~31;
     const int lo = min(n, warp * seg), hi = min(n, lo + seg);
     const uint32_t lt_mask = (1u << lane) - 1u;
-    for (int base = lo; base < hi; base += 32) {
-        const int i = base + lane;
-        const uint32_t d = i < hi ? ((uint32_t)(src[i] >> shift) & (kRadix - 1)) : (uint32_t)kRadix;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        if (d < (uint32_t)kRadix && (peers & lt_mask) == 0) s_wh[warp][d] += __popc(peers);
-        __syncwarp();
+    // kPassUnroll groups of 32 keys per step: their loads are issued together
+    // (the passes are bound by the latency of these L2 reads), then the groups
+    // are taken in index order
+    for (int base = lo; base < hi; base += 32 * kPassUnroll) {
+        uint32_t dg[kPassUnroll];
+#pragma unroll
+        for (int u = 0; u < kPassUnroll; ++u) {
+            const int i = base + 32 * u + lane;
+            dg[u] = i < hi ? ((uint32_t)(src[i] >> shift) & (kRadix - 1)) : (uint32_t)kRadix;
+        }
+#pragma unroll
+        for (int u = 0; u < kPassUnroll; ++u) {
+            const uint32_t d = dg[u];
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            if (d < (uint32_t)kRadix && (peers & lt_mask) == 0) s_wh[warp][d] += __popc(peers);
+            __syncwarp();
+        }
     }
     __syncthreads();
     uint32_t tot = 0;
@@ -269,18 +281,26 @@ __device__ bool cta_radix_pass(const uint64_t *src, uint64_t *dst, int n, int sh
         r += c;
     }
     __syncthreads();
-    for (int base = lo; base < hi; base += 32) {
-        const int i = base + lane;
-        const bool active = i < hi;
-        const uint64_t key = active ? src[i] : 0ull;
-        const uint32_t d = active ? ((uint32_t)(key >> shift) & (kRadix - 1)) : (uint32_t)kRadix;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t rank = __popc(peers & lt_mask);
-        const uint32_t off = active ? s_wh[warp][d] : 0u;
-        if (active) dst[off + rank] = key;
-        __syncwarp();
-        if (active && rank == 0) s_wh[warp][d] = off + __popc(peers);
-        __syncwarp();
+    for (int base = lo; base < hi; base += 32 * kPassUnroll) {
+        uint64_t kg[kPassUnroll];
+#pragma unroll
+        for (int u = 0; u < kPassUnroll; ++u) {
+            const int i = base + 32 * u + lane;
+            kg[u] = i < hi ? src[i] : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < kPassUnroll; ++u) {
+            const bool active = base + 32 * u + lane < hi;
+            const uint64_t key = kg[u];
+            const uint32_t d = active ? ((uint32_t)(key >> shift) & (kRadix - 1)) : (uint32_t)kRadix;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t rank = __popc(peers & lt_mask);
+            const uint32_t off = active ? s_wh[warp][d] : 0u;
+            if (active) dst[off + rank] = key;
+            __syncwarp();
+            if (active && rank == 0) s_wh[warp][d] = off + __popc(peers);
+            __syncwarp();
+        }
     }
     __syncthreads();
     return true;
