@@ -39,6 +39,7 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kScanThreads = 1024;
 constexpr int kPassUnroll = 4;  // 32-key groups per step of a radix pass (loads issued together)
+constexpr int kRadixMinKeys = 1024;  // CTA lists above this (up to kSmemKeys) take the shared-memory radix sort
 constexpr int kSmemKeys = 2048;  // bucket size sorted entirely in shared memory
 
 __device__ __forceinline__ bool status_ok(const int32_t *status) { return status[0] == 0; }
@@ -240,7 +241,7 @@ __device__ __forceinline__ uint32_t cta_excl_scan(uint32_t v, uint32_t *s_warp) 
 // the rows (digit-major, warp-minor) into output cursors, and each warp then
 // scatters its segment in order with warp barriers only. Returns false (dst
 // untouched, src still current) when all n keys share the digit.
-__device__ bool cta_radix_pass(const uint64_t *src, uint64_t *dst, int n, int shift, uint32_t (*s_wh)[kRadix],
+__device__ __forceinline__ bool cta_radix_pass(const uint64_t *src, uint64_t *dst, int n, int shift, uint32_t (*s_wh)[kRadix],
                                uint32_t *s_warp) {
     static_assert(kThreads == kRadix, "one digit per thread in the scan");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -312,7 +313,7 @@ __device__ bool cta_radix_pass(const uint64_t *src, uint64_t *dst, int n, int sh
 // bits of a run, which the sort does not change. Returns true for the whole CTA
 // when some run is longer than kMaxTieRun (left for a full sort instead).
 constexpr int kMaxTieRun = 32;
-__device__ bool cta_fix_depth_ties(uint64_t *a, int n) {
+__device__ __forceinline__ bool cta_fix_depth_ties(uint64_t *a, int n) {
     int bad = 0;
     for (int i = threadIdx.x; i < n; i += kThreads) {
         const uint32_t z = (uint32_t)(a[i] >> 32);
@@ -469,7 +470,7 @@ __global__ void __launch_bounds__(kThreads, 4)
                 uint32_t *__restrict__ values, uint64_t *__restrict__ keys_out, int rec_bits,
                 const int32_t *__restrict__ status) {
     dep_wait();
-    __shared__ uint64_t s_a[kSmemKeys];
+    __shared__ uint64_t s_a[kSmemKeys], s_b[kSmemKeys];
     __shared__ uint32_t s_wh[kWarps][kRadix];
     __shared__ uint32_t s_warp[kWarps];
     if (!status_ok(status)) return;
@@ -493,6 +494,37 @@ __global__ void __launch_bounds__(kThreads, 4)
     const uint32_t s = ranges[2 * (size_t)tile], e = ranges[2 * (size_t)tile + 1];
     const int n = (int)(e - s);
     if (n <= 0) return;
+    if (n > kRadixMinKeys && n <= kSmemKeys) {
+        // LSD radix over the depth digits in shared memory (4 passes of ~25
+        // instructions per key against ~6 per key for each of the 45-66 stages
+        // of a bitonic network), then the equal-depth fix-up
+        for (int i = tid; i < n; i += kThreads) s_a[i] = low_keys[s + i];
+        __syncthreads();
+        uint64_t *a = s_a, *b = s_b;
+        for (int shift = 32; shift < 64; shift += kRadixBits) {
+            if (cta_radix_pass(a, b, n, shift, s_wh, s_warp)) {
+                uint64_t *t = a;
+                a = b;
+                b = t;
+            }
+        }
+        if (cta_fix_depth_ties(a, n)) {
+            for (int shift = 0; shift < 64; shift += kRadixBits) {
+                if (shift >= rec_bits && shift < 32) continue;
+                if (cta_radix_pass(a, b, n, shift, s_wh, s_warp)) {
+                    uint64_t *t = a;
+                    a = b;
+                    b = t;
+                }
+            }
+        }
+        for (int i = tid; i < n; i += kThreads) {
+            const uint64_t k = a[i];
+            values[s + i] = (uint32_t)k;
+            if (keys_out) keys_out[s + i] = ((uint64_t)tile << 32) | (k >> 32);
+        }
+        return;
+    }
     if (n <= kSmemKeys) {
         int np = kThreads;
         while (np < n) np <<= 1;
