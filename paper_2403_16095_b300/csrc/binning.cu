@@ -355,7 +355,11 @@ __device__ void cta_sort_regs(const uint64_t *keys, int n, uint64_t *s_a) {
         const int p = t * K + j;
         x[j] = p < n ? keys[p] : ~0ull;
     }
+    // fully unrolled: every stage's stride is a constant, so the network is
+    // straight-line code (as loops its branches saturated the branch unit)
+#pragma unroll
     for (int size = 2; size <= NP; size <<= 1) {
+#pragma unroll
         for (int stride = size >> 1; stride >= K; stride >>= 1) {
             if (stride >= 32 * K) {  // partner in another warp: exchange through shared
                 // memory, position q at s_a[(q % K) kThreads + q / K] (consecutive
