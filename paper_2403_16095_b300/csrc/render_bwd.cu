@@ -32,11 +32,16 @@ __device__ __forceinline__ float sgnf(float v) { return v > 0.f ? 1.f : (v < 0.f
 // Entries staged per batch and the dynamic shared memory that holds them:
 // record (4 x 16 B) + index (4 B), plus the 144-B pose Jacobian in POSE mode.
 // The last CTA of a frame reuses the same bytes for the pose reduction.
+constexpr int kFullBatch = 512;
+
 template <int TILE, int MODE>
 struct BwdSmem {
     static constexpr int NT = TILE * TILE;
     static constexpr bool POSE = MODE == GS_MODE_POSE;
-    static constexpr int BATCH = NT < 256 ? NT : 256;
+    // FULL mode stages 512 entries per batch (68 B each): half the CTA barriers
+    // of 256, which bound the kernel's warps (they wait for the tile's busiest
+    // warp at every batch)
+    static constexpr int BATCH = NT < 256 ? NT : (POSE ? 256 : kFullBatch);
     static constexpr size_t kEntry = 4 * sizeof(float4) + sizeof(uint32_t) + (POSE ? 9 * sizeof(float4) : 0);
     static constexpr size_t kStage = BATCH * kEntry;
     static constexpr size_t kRed = POSE ? sizeof(df) * kRedSlots * 6 : 0;
@@ -160,18 +165,18 @@ __global__ void __launch_bounds__(TILE *TILE, (TILE == 16 && MODE == GS_MODE_FUL
     for (int bend = (int)block_last; bend > (int)range.x; bend -= BATCH) {
         const int bstart = max((int)range.x, bend - BATCH);
         __syncthreads();
-        if (tid < bend - bstart) {
-            const uint32_t r = values[bstart + tid];
+        for (int e = tid; e < bend - bstart; e += NT) {
+            const uint32_t r = values[bstart + e];
             const float4 *R = rec + (size_t)r * 4;
-            s_a[tid] = R[0];
-            s_b[tid] = R[1];
-            s_c[tid] = R[2];
-            s_r[tid] = reinterpret_cast<const int4 *>(R)[3];
-            s_idx[tid] = r;
+            s_a[e] = R[0];
+            s_b[e] = R[1];
+            s_c[e] = R[2];
+            s_r[e] = reinterpret_cast<const int4 *>(R)[3];
+            s_idx[e] = r;
             if (POSE) {
                 const float4 *J = jac + (size_t)r * 9;
 #pragma unroll
-                for (int q = 0; q < 9; ++q) s_j[tid * 9 + q] = J[q];
+                for (int q = 0; q < 9; ++q) s_j[e * 9 + q] = J[q];
             }
         }
         __syncthreads();
