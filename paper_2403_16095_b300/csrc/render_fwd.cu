@@ -22,13 +22,16 @@
 namespace gs {
 namespace {
 
+constexpr int kFwdBatch = 512;  // entries staged per batch at 16x16 and larger tiles (512: half the
+                                // CTA barriers of 256; mapping forward 1.20 -> 1.05 ms)
+
 template <int TILE, bool DOM, bool LITE>
 __global__ void __launch_bounds__(TILE *TILE, 1024 / (TILE * TILE))
     k_render_fwd(const float4 *__restrict__ rec, const uint32_t *__restrict__ values,
                  const uint2 *__restrict__ ranges, const uint32_t *__restrict__ order, FrameTable ft,
                  const float *__restrict__ obs_depth, ImagePtrs out, const int32_t *__restrict__ status) {
     constexpr int NT = TILE * TILE;
-    constexpr int BATCH = NT < 256 ? NT : 256;
+    constexpr int BATCH = NT < 256 ? NT : kFwdBatch;
     __shared__ float4 s_a[BATCH], s_b[BATCH], s_c[BATCH];
     __shared__ int4 s_r[BATCH];
     if (status[0] != 0) return;
@@ -58,13 +61,12 @@ __global__ void __launch_bounds__(TILE *TILE, 1024 / (TILE * TILE))
 
     for (uint32_t base = range.x; base < range.y; base += BATCH) {
         if (__syncthreads_count(done) == NT) break;  // also orders smem reuse
-        const uint32_t j = base + tid;
-        if (tid < BATCH && j < range.y) {
-            const float4 *R = rec + (size_t)values[j] * 4;
-            s_a[tid] = R[0];
-            s_b[tid] = R[1];
-            s_c[tid] = R[2];
-            s_r[tid] = reinterpret_cast<const int4 *>(R)[3];
+        for (int e = tid; e < BATCH && base + e < range.y; e += NT) {
+            const float4 *R = rec + (size_t)values[base + e] * 4;
+            s_a[e] = R[0];
+            s_b[e] = R[1];
+            s_c[e] = R[2];
+            s_r[e] = reinterpret_cast<const int4 *>(R)[3];
         }
         __syncthreads();
         const int cnt = min(BATCH, (int)(range.y - base));
