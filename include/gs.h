@@ -8,8 +8,10 @@
  * CUDA graph):
  *
  *   gs_project          Eq. 1-2   activate parameters, EWA-project each Gaussian
- *   gs_bin_tiles        Sec. 3.1  duplicate per overlapped tile, radix-sort the
- *                                 64-bit (tile id, depth) keys, tile ranges
+ *   gs_bin_tiles        Sec. 3.1  duplicate per overlapped tile, sort the 64-bit
+ *                                 (tile id, depth) keys per tile, tile ranges
+ *                                 (gs_project_bin: both calls in one, the
+ *                                 projection counting the pairs)
  *   gs_render_fwd       Eq. 3-10  front-to-back alpha blending per pixel
  *   gs_render_bwd       Eq. 3-10 adjoint (+ Eq. 14/16/19 loss when fused):
  *                                 reverse walk of each tile list; gradients to the

@@ -3,10 +3,14 @@
 // (global tile id << 32 | float bits of depth) with the record index as the
 // final tie-break:
 //
+//   k_bin_clear   zeroes the tile counters (the `ranges` buffer doubles as
+//                 the counters) and the call's scalars.
 //   k_tile_count  MSD digit = the tile id: one atomic increment per
-//                 (record, overlapped tile) into the tile's counter (the
-//                 `ranges` buffer doubles as the counters); pairs are spread
-//                 over the lanes of a warp so large footprints do not serialise.
+//                 (record, overlapped tile) into the tile's counter; pairs are
+//                 spread over the lanes of a warp so large footprints do not
+//                 serialise, and lanes on the same tile share one atomic
+//                 (pairs.cuh). gs_project_bin does this count in the
+//                 projection kernel instead and skips this pass.
 //   k_tile_scan   exclusive scan of the counters -> each tile's [start, start)
 //                 cursor, total pair count P and the capacity check; optionally
 //                 the launch order of the blend kernels: tiles by descending
@@ -15,14 +19,15 @@
 //   k_tile_fill   each pair claims a slot in its tile's bucket and stores the
 //                 low key (depth bits << 32 | record); after this pass every
 //                 tile's cursor equals its end, so `ranges` is final.
-//   k_tile_sort   one CTA per tile sorts the bucket's low keys: buckets of
-//                 <= 2048 keys with a bitonic network in registers and shared
-//                 memory, larger ones with a stable LSD radix sort over the four
-//                 8-bit depth digits (digits constant over the bucket are
-//                 skipped) ping-ponging in global memory, after which each run
-//                 of equal depth is put in record order (runs longer than 32
-//                 keys: a full LSD pass over the record-index digits first,
-//                 then the depth digits). Low keys are
+//   k_tile_sort   sorts each bucket's low keys: buckets under 256 keys by one
+//                 warp in registers; up to 1024 keys by a CTA bitonic network
+//                 in registers and shared memory; larger ones by a stable LSD
+//                 radix sort over the four 8-bit depth digits (digits constant
+//                 over the bucket are skipped) in shared memory up to 2048 keys,
+//                 ping-ponging in global memory beyond, after which each run of
+//                 equal depth is put in record order (runs longer than 32 keys:
+//                 a full LSD pass over the record-index digits first, then the
+//                 depth digits). Low keys are
 //                 unique within a bucket, so the order of the atomic fill does
 //                 not matter: the output is bit-exact, the same as a stable sort
 //                 of the 64-bit keys emitted in record order, and independent of

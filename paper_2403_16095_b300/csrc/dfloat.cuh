@@ -27,18 +27,6 @@ __device__ __forceinline__ df df_add(df a, df b) {
     return {h, __fsub_rn(e, __fsub_rn(h, s.hi))};
 }
 
-__device__ __forceinline__ df df_add_f(df a, float b) { return df_add(a, df{b, 0.f}); }
-
-__device__ __forceinline__ df df_shfl_down(df v, int off) {
-    return {__shfl_down_sync(0xffffffffu, v.hi, off), __shfl_down_sync(0xffffffffu, v.lo, off)};
-}
-
-// Warp sum (fixed butterfly order) of a double-float; the result is in lane 0.
-__device__ __forceinline__ df df_warp_sum(df v) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v = df_add(v, df_shfl_down(v, off));
-    return v;
-}
 
 // Warp sum of six FP32 values per lane as double-floats, by recursive halving:
 // at each of three steps (lane bits 4, 3, 2) a lane keeps half of its slots

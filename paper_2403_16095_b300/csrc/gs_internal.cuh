@@ -13,9 +13,6 @@ namespace gs {
 constexpr int kRecFloats = GS_REC_FLOATS;
 constexpr int kJacFloats = GS_JAC_FLOATS;
 constexpr int kGrad2d = 12;       // FULL-mode per-record accumulators
-constexpr int kScanBlocks = 592;  // 4 CTAs per SM on 148 SMs
-constexpr int kSortBlocks = 592;
-constexpr int kSortThreads = 256;
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 
