@@ -138,6 +138,11 @@ def _synthetic_records(n, cams, tile, seed, ties=True):
     ([synth.Camera(16, 16, 1, 1, 0, 0)], 16, "short", 9000),                # runs of a few equal depths
     ([synth.Camera(40, 24, 1, 1, 0, 0)], 16, False, 20000),                 # 6 tiles, ~10k keys each
     ([synth.Camera(48, 40, 1, 1, 0, 0), synth.Camera(16, 16, 1, 1, 0, 0)], 8, "short", 5000),
+    # lists of 1,025-2,048 keys (radix sort in shared memory), with short runs of
+    # equal depth and with long ones (full-sort fallback)
+    ([synth.Camera(16, 16, 1, 1, 0, 0)], 16, "short", 1800),
+    ([synth.Camera(16, 16, 1, 1, 0, 0)], 16, True, 1800),
+    ([synth.Camera(16, 16, 1, 1, 0, 0)], 16, False, 1300),
 ])
 def test_bin_tiles_bit_exact(cams, tile, ties, n):
     rec, rect, depth, touched = _synthetic_records(n, cams, tile, seed=len(cams) * 7 + tile, ties=ties)
@@ -283,3 +288,29 @@ def test_project_bin_equals_project_then_bin(storage, pose_mode):
         assert np.all(np.diff(np.minimum(lens[order] >> 2, 1023)) <= 0)
     assert np.array_equal(np.minimum(lens[ra.order.cpu().numpy()] >> 2, 1023),
                           np.minimum(lens[rb.order.cpu().numpy()] >> 2, 1023))
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 32, 33, 64, 65, 128, 129, 255, 256, 257])
+def test_bin_tiles_list_length_boundaries(n):
+    """One tile holding exactly n pairs, across the boundaries of the sort paths
+    (one warp in registers with 1, 2, 4 or 8 keys per lane below 256; a CTA
+    bitonic network from 256), with ties: keys equal the oracle's."""
+    cams = [synth.Camera(16, 16, 1, 1, 0, 0)]
+    rng = np.random.default_rng(9000 + n)
+    rec = np.zeros((n, 16), np.float32)
+    rect = np.tile(np.int32([[2, 3, 9, 12]]), (n, 1))
+    depth = (0.5 + 0.01 * rng.integers(0, max(1, n // 2), n)).astype(np.float32)
+    rec[:, 6] = depth
+    rec.view(np.int32)[:, 12:16] = rect
+    touched = np.ones(n, np.int32)
+    r = _rast(cams, n, tile=16, capacity=n + 5)
+    r.rec.copy_(torch.from_numpy(rec.reshape(-1)))
+    r.touched.copy_(torch.from_numpy(touched))
+    r.reset_status()
+    r.bin()
+    torch.cuda.synchronize()
+    code, P = r.read_status()
+    assert code == 0 and P == n
+    keys, vals, ranges = oracle.bin_tiles(rect, depth, n, 16, cams)
+    assert np.array_equal(r.keys[:P].cpu().numpy().view(np.uint64), keys)
+    assert np.array_equal(r.values[:P].cpu().numpy().view(np.uint32), vals)
