@@ -117,7 +117,8 @@ typedef struct {
     float *rec;           /* [F*N][16]                                         */
     int *tiles_touched;   /* [F*N] tiles overlapped (0 if culled)              */
     float *pose_jac;      /* [F*N][6][6] d(mean2d.x, mean2d.y, A, B, C, z)/d(rho, phi),
-                             written in POSE mode only; may be NULL otherwise    */
+                             written in POSE mode only; may be NULL otherwise
+                             (and when F*N = 0)                                 */
 } gs_projected;
 
 /* Tile lists (output of gs_bin_tiles), device, caller-allocated. */

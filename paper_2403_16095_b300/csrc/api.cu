@@ -134,7 +134,7 @@ gs_status gs_project(const gs_gaussians *g, int n_frames, const gs_camera *cams,
     GS_TRY(check_proj(out, n_frames));
     if (out->n_gaussians != g->n) return fail(GS_ERR_INVALID_ARG, "projected.n_gaussians != gaussians.n");
     if (!T_cw || !status) return fail(GS_ERR_INVALID_ARG, "T_cw/status NULL");
-    if (opts->mode == GS_MODE_POSE && (!out->pose_jac || !aligned(out->pose_jac, 16)))
+    if (opts->mode == GS_MODE_POSE && g->n > 0 && n_frames > 0 && (!out->pose_jac || !aligned(out->pose_jac, 16)))
         return fail(GS_ERR_INVALID_ARG, "POSE mode needs a 16-byte aligned pose_jac");
     return cuda_status(gs::launch_project(gauss_ptrs(g), g->n, ft, T_cw, opts->jclamp, opts->nu_cull, opts->mode,
                                           out->rec, out->tiles_touched, out->pose_jac, nullptr, status, stream),
@@ -154,7 +154,7 @@ gs_status gs_project_bf16(const gs_gaussians_bf16 *g, int n_frames, const gs_cam
     GS_TRY(check_proj(out, n_frames));
     if (out->n_gaussians != g->n) return fail(GS_ERR_INVALID_ARG, "projected.n_gaussians != gaussians.n");
     if (!T_cw || !status) return fail(GS_ERR_INVALID_ARG, "T_cw/status NULL");
-    if (opts->mode == GS_MODE_POSE && (!out->pose_jac || !aligned(out->pose_jac, 16)))
+    if (opts->mode == GS_MODE_POSE && g->n > 0 && n_frames > 0 && (!out->pose_jac || !aligned(out->pose_jac, 16)))
         return fail(GS_ERR_INVALID_ARG, "POSE mode needs a 16-byte aligned pose_jac");
     return cuda_status(gs::launch_project_bf16(g->anchors, g->packed, g->n, ft, T_cw, opts->jclamp, opts->nu_cull,
                                                opts->mode, out->rec, out->tiles_touched, out->pose_jac, nullptr, status,
@@ -242,7 +242,7 @@ gs_status gs_project_bin(const gs_gaussians *g, int n_frames, const gs_camera *c
     GS_TRY(check_proj(out, n_frames));
     if (out->n_gaussians != g->n) return fail(GS_ERR_INVALID_ARG, "projected.n_gaussians != gaussians.n");
     if (!T_cw) return fail(GS_ERR_INVALID_ARG, "T_cw NULL");
-    if (opts->mode == GS_MODE_POSE && (!out->pose_jac || !aligned(out->pose_jac, 16)))
+    if (opts->mode == GS_MODE_POSE && g->n > 0 && n_frames > 0 && (!out->pose_jac || !aligned(out->pose_jac, 16)))
         return fail(GS_ERR_INVALID_ARG, "POSE mode needs a 16-byte aligned pose_jac");
     GS_TRY(check_bin_call(out, n_frames, ft, tiles, status, ws, ws_bytes));
     GS_TRY(cuda_status(gs::launch_bin_clear(tiles->ranges, ft, tiles->capacity, ws, stream), "gs_project_bin (clear)"));
@@ -266,7 +266,7 @@ gs_status gs_project_bin_bf16(const gs_gaussians_bf16 *g, int n_frames, const gs
     GS_TRY(check_proj(out, n_frames));
     if (out->n_gaussians != g->n) return fail(GS_ERR_INVALID_ARG, "projected.n_gaussians != gaussians.n");
     if (!T_cw) return fail(GS_ERR_INVALID_ARG, "T_cw NULL");
-    if (opts->mode == GS_MODE_POSE && (!out->pose_jac || !aligned(out->pose_jac, 16)))
+    if (opts->mode == GS_MODE_POSE && g->n > 0 && n_frames > 0 && (!out->pose_jac || !aligned(out->pose_jac, 16)))
         return fail(GS_ERR_INVALID_ARG, "POSE mode needs a 16-byte aligned pose_jac");
     GS_TRY(check_bin_call(out, n_frames, ft, tiles, status, ws, ws_bytes));
     GS_TRY(cuda_status(gs::launch_bin_clear(tiles->ranges, ft, tiles->capacity, ws, stream),
@@ -355,7 +355,7 @@ gs_status gs_render_bwd(const gs_projected *proj, const gs_tiles *tiles, int n_f
     unsigned *counters = reinterpret_cast<unsigned *>(static_cast<char *>(ws) + grad2d_bytes(M, mode));
     cudaError_t e;
     if (mode == GS_MODE_POSE) {
-        if (!proj->pose_jac) return fail(GS_ERR_INVALID_ARG, "POSE mode needs projected.pose_jac");
+        if (!proj->pose_jac && proj->n_gaussians > 0) return fail(GS_ERR_INVALID_ARG, "POSE mode needs projected.pose_jac");
         for (int f = 0; f < n_frames; ++f) {
             const int used = ft.f[f].tiles_x * ft.f[f].tiles_y;
             if (used < per_frame) {
@@ -396,7 +396,7 @@ gs_status gs_render_fwd_bwd_pose(const gs_projected *proj, const gs_tiles *tiles
     GS_TRY(check_proj(proj, n_frames));
     GS_TRY(check_tiles(tiles, ft));
     if (!status || !pose_partials) return fail(GS_ERR_INVALID_ARG, "status/pose_partials NULL");
-    if (!proj->pose_jac) return fail(GS_ERR_INVALID_ARG, "POSE mode needs projected.pose_jac");
+    if (!proj->pose_jac && proj->n_gaussians > 0) return fail(GS_ERR_INVALID_ARG, "POSE mode needs projected.pose_jac");
     if (!loss) return fail(GS_ERR_INVALID_ARG, "loss is NULL");
     if (loss->w_unc != 0.f || loss->w_nu != 0.f || loss->w_align != 0.f)
         return fail(GS_ERR_UNSUPPORTED, "the tracking pass supports colour and depth L1 terms only");

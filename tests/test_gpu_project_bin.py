@@ -314,3 +314,29 @@ def test_bin_tiles_list_length_boundaries(n):
     keys, vals, ranges = oracle.bin_tiles(rect, depth, n, 16, cams)
     assert np.array_equal(r.keys[:P].cpu().numpy().view(np.uint64), keys)
     assert np.array_equal(r.values[:P].cpu().numpy().view(np.uint32), vals)
+
+
+@pytest.mark.parametrize("case", ["no_gaussians", "all_behind"])
+def test_project_bin_empty_inputs(case):
+    """gs_project_bin with no Gaussians, or with every Gaussian behind the camera:
+    status OK, no pairs, every tile empty."""
+    from paper_2403_16095_b300 import Gaussians
+    from paper_2403_16095_b300 import _abi as A
+    cam = synth.Camera(40, 30, 30, 30, 20, 15)
+    T = np.c_[np.eye(3), np.zeros(3)]
+    if case == "no_gaussians":
+        e = torch.zeros(0, device="cuda")
+        g = Gaussians(e.view(0, 3), e.view(0, 3), torch.zeros(0, 4, device="cuda"), e, e.view(0, 3), e)
+        n = 0
+    else:
+        sc, _, _ = synth.tiny_scene(n=50, seed=1203)
+        sc = synth.Scene(sc.means * np.float32([1, 1, -1]), sc.log_scales, sc.quats, sc.opacity_logit, sc.colors,
+                         sc.nu)
+        g, n = to_gpu_gaussians(sc), sc.n
+    r = _rast([cam], n, mode=A.GS_MODE_POSE, capacity=64)
+    r.reset_status()
+    r.project_bin(g, poses_gpu(T))
+    torch.cuda.synchronize()
+    assert r.read_status() == (0, 0)
+    rg = r.ranges.view(-1, 2).cpu().numpy()
+    assert np.all(rg[:, 0] == rg[:, 1])
