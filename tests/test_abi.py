@@ -69,8 +69,12 @@ def test_argument_errors_are_synchronous(A):
     badcam = (A.gs_camera * 1)(A.gs_camera(0, 48, 50.0, 50.0, 32.0, 24.0, 0.2))
     st = lib.gs_project(C.byref(g0), 1, badcam, C.c_void_p(16), C.byref(opts), C.byref(p0), C.c_void_p(16), None)
     assert st == A.GS_ERR_INVALID_ARG
-    # POSE mode without a Jacobian buffer
-    st = lib.gs_project(C.byref(g0), 1, cam, C.c_void_p(16), C.byref(opts), C.byref(p0), C.c_void_p(16), None)
+    # POSE mode without a Jacobian buffer (rejected before any launch; with no
+    # Gaussians there is nothing to write and NULL is accepted)
+    p = C.c_void_p(256)
+    g10 = A.gs_gaussians(10, p, p, p, p, p, p)
+    p10 = A.gs_projected(10, 1, p, p, None)
+    st = lib.gs_project(C.byref(g10), 1, cam, C.c_void_p(16), C.byref(opts), C.byref(p10), C.c_void_p(16), None)
     assert st == A.GS_ERR_INVALID_ARG and "pose_jac" in A.last_error()
     # backward needs POSE or FULL
     fwd_opts = A.gs_opts(16, A.GS_MODE_FWD, 1.3, 0.0)
