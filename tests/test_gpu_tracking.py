@@ -303,3 +303,18 @@ def test_tracking_pass_with_every_gaussian_culled():
     assert float(r.pose_grad.abs().max()) == 0.0
     assert torch.equal(Tt, poses_gpu(T))
     assert bool(torch.all(r.img["T_final"] == 1.0)) and float(r.img["color"].abs().max()) == 0.0
+
+
+def test_tracking_an_empty_map_keeps_the_start_pose(room_small):
+    """A map with no Gaussians: every tile list is empty, the pose gradient is
+    exactly zero, and the Adam steps leave the start pose unchanged."""
+    from paper_2403_16095_b300 import Gaussians, Tracker
+    sc, cam, poses = room_small
+    tcol, tdep = _targets(sc, cam, poses[0])
+    e = torch.zeros(0, device="cuda")
+    g = Gaussians(e.view(0, 3), e.view(0, 3), torch.zeros(0, 4, device="cuda"), e, e.view(0, 3), e)
+    T0 = torch.from_numpy(synth.jitter_pose(poses[0], seed=41))
+    tr = Tracker(g, cam, iters=5, graph=True, capacity=4096)
+    tr.prepare(tcol, tdep, T0)
+    T = tr.track(tcol, tdep, T0).cpu()
+    assert torch.allclose(T, T0.to(T.dtype), rtol=0, atol=1e-12)
