@@ -157,6 +157,46 @@ def test_fused_tracking_pass_equals_forward_then_backward(track_full):
         r.fwd_bwd_pose(dict(loss, w_align=0.1))
 
 
+def test_fused_tracking_pass_dense_build_equals_forward_then_backward():
+    """At 800 or more records per tile the tracking pass runs its 4-CTA-per-SM
+    build (fewer registers): here 12,000 Gaussians over the 12 tiles of a 64x48
+    image (1,000 per tile). Its channels and FP64 pose gradient equal
+    gs_render_fwd + gs_render_bwd bit for bit, as the default build's do."""
+    from paper_2403_16095_b300 import Rasterizer
+    from paper_2403_16095_b300 import _abi as A
+    sc = synth.room_scene(12_000, seed=1309)
+    cam = synth.Camera(64, 48, 60.0, 60.0, 32.0, 24.0)
+    poses = synth.room_track_poses(2, seed=1309)
+    T_gt = poses[0]
+    g = to_gpu_gaussians(sc)
+    r0 = Rasterizer([cam], sc.n, tile=16, mode=A.GS_MODE_FWD)
+    r0.render(g, poses_gpu(T_gt))
+    tc, td = r0.img["color"].clone(), r0.img["depth"].clone()
+    assert sc.n >= 800 * r0.n_tiles
+    T = synth.jitter_pose(T_gt, seed=7)
+    loss = dict(w_color=0.2, w_depth=1.0, unc_tau=0.025, target_color=tc, target_depth=td)
+    res = []
+    for fused in (False, True):
+        r = Rasterizer([cam], sc.n, tile=16, mode=A.GS_MODE_POSE, channels="track")
+        r.render(g, poses_gpu(T), td)
+        for k in r.img:
+            r.img[k].fill_(-1 if r.img[k].dtype == torch.int32 else float("nan"))
+        r.pose_grad.zero_()
+        if fused:
+            r.fwd_bwd_pose(loss, images=True)
+        else:
+            r.forward(td)
+            r.backward(obs_depth=td, loss=loss)
+        torch.cuda.synchronize()
+        code, P = r.read_status()
+        assert code == 0 and P > 10 * r.n_tiles
+        res.append(({k: v.clone() for k, v in r.img.items()}, r.pose_grad.clone()))
+    for k in res[0][0]:
+        assert torch.equal(res[0][0][k], res[1][0][k]), k
+    assert torch.equal(res[0][1], res[1][1])
+    assert float(res[1][1].abs().max()) > 0
+
+
 def test_tracker_fused_equals_unfused(room_small):
     from paper_2403_16095_b300 import Tracker
     sc, cam, poses = room_small
