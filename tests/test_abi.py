@@ -66,6 +66,10 @@ def test_argument_errors_are_synchronous(A):
     assert st == A.GS_ERR_INVALID_ARG and "tile" in A.last_error()
     st = lib.gs_project(C.byref(g0), 0, cam, C.c_void_p(16), C.byref(opts), C.byref(p0), C.c_void_p(16), None)
     assert st == A.GS_ERR_INVALID_ARG and "n_frames" in A.last_error()
+    many = (A.gs_camera * (A.GS_MAX_FRAMES + 1))(*[A.gs_camera(64, 48, 50.0, 50.0, 32.0, 24.0, 0.2)] * (A.GS_MAX_FRAMES + 1))
+    st = lib.gs_project(C.byref(g0), A.GS_MAX_FRAMES + 1, many, C.c_void_p(16), C.byref(opts), C.byref(p0),
+                        C.c_void_p(16), None)
+    assert st == A.GS_ERR_INVALID_ARG and "n_frames" in A.last_error()
     badcam = (A.gs_camera * 1)(A.gs_camera(0, 48, 50.0, 50.0, 32.0, 24.0, 0.2))
     st = lib.gs_project(C.byref(g0), 1, badcam, C.c_void_p(16), C.byref(opts), C.byref(p0), C.c_void_p(16), None)
     assert st == A.GS_ERR_INVALID_ARG

@@ -220,3 +220,47 @@ def test_autotuned_uneven_batch_is_tile_invariant():
         for k in list(PARAMS[:-1]) + ["pose"]:
             a, b = grads[t][k], grads[16][k]
             assert np.abs(a - b).max() <= 1e-5 * np.abs(b).max(), (t, k)
+
+
+def test_maximum_frame_count_in_one_launch():
+    """The largest batch one call takes (64 frames, three image sizes, each its
+    own pose): per-frame images, per-frame pose gradients and the parameter
+    gradients summed over the frames equal 64 separate oracle evaluations."""
+    from paper_2403_16095_b300 import Rasterizer
+    from paper_2403_16095_b300 import _abi as A
+    F = A.GS_MAX_FRAMES
+    sc, _, _ = synth.tiny_scene(n=600, seed=1301)
+    sizes = [(40, 30, 30.0), (33, 21, 25.0), (24, 40, 35.0)]
+    cams = [synth.Camera(w, h, fo, fo, w / 2, h / 2) for w, h, fo in (sizes[f % 3] for f in range(F))]
+    rng = np.random.default_rng(1301)
+    T0 = np.c_[np.eye(3), np.zeros(3)]
+    Ts = [_posed(T0, np.r_[rng.uniform(-0.1, 0.1, 3), rng.uniform(-0.05, 0.05, 3)]).astype(np.float32)
+          .astype(np.float64) for _ in range(F)]
+    tgts = [synth.random_targets(cams[f], 1301 + 1 + f) for f in range(F)]
+    tc = np.concatenate([t[0][0].reshape(-1) for t in tgts])
+    td = np.concatenate([t[1][0].reshape(-1) for t in tgts])
+    g = to_gpu_gaussians(sc)
+    r = Rasterizer(cams, sc.n, tile=16, mode=A.GS_MODE_FULL)
+    Tt = poses_gpu(np.stack(Ts))
+    obs = torch.from_numpy(td).cuda()
+    r.render(g, Tt, obs)
+    loss = dict(w_color=0.7, w_depth=0.25, target_color=torch.from_numpy(tc).cuda(), target_depth=obs)
+    grads = {k: torch.empty_like(getattr(g, k)) for k in PARAMS}
+    r.backward(obs_depth=obs, loss=loss, g=g, T_cw=Tt, grads=grads)
+    torch.cuda.synchronize()
+    assert r.read_status()[0] == 0
+    s64 = f32_scene(sc)
+    want = {k: 0.0 for k in PARAMS}
+    n_flip = 0
+    for f in range(F):
+        n_flip += _n_flip(sc, cams[f], Ts[f], r.frame_images(f))
+        og = oracle.grad(s64, cams[f], Ts[f], oracle.LossSpec(0.7, 0.25, 0, 0, 0, tgts[f][0][0], tgts[f][1][0]))
+        for k in PARAMS:
+            want[k] = want[k] + og[k]
+        _rel(f"pose[{f}]", r.pose_grad[f].cpu().numpy(), og["pose"], elem=1e-4, norm=1e-4)
+    assert n_flip <= 8
+    for k in PARAMS:
+        if k == "nu":
+            assert float(grads[k].abs().max()) == 0.0
+            continue
+        _rel(k, grads[k].cpu().numpy(), want[k], elem=1e-3, norm=1e-4, n_flip=n_flip)
