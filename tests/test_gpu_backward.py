@@ -236,3 +236,59 @@ def test_adam_step_matches_oracle():
     np.testing.assert_allclose(got[25:27], [float(np.float32(0.9)) ** 5, float(np.float32(0.999)) ** 5], rtol=1e-14)
     want = np.c_[st_o[:9].reshape(3, 3), st_o[9:12]].reshape(-1)
     np.testing.assert_allclose(Tf.cpu().numpy(), want, rtol=0, atol=1e-6)
+
+
+def _degenerate_scene():
+    """tiny_scene with the degenerate Gaussians the method meets: zero
+    quaternions (invalid: culled, zero gradient), saturated opacity (alpha
+    clamped at 0.99, so no opacity gradient through the clamp), sub-pixel
+    scales (footprint from the 0.3 px^2 dilation alone), one Gaussian covering
+    every tile, centres outside the image whose footprints reach in (ten at one
+    depth: ties ordered by index), and means just in front of and behind the
+    near plane."""
+    sc, cam, T = synth.tiny_scene(n=800, seed=1401)
+    m, ls, q, o = sc.means.copy(), sc.log_scales.copy(), sc.quats.copy(), sc.opacity_logit.copy()
+    q[0:20] = 0.0
+    o[20:30] = 20.0
+    ls[30:40] = -9.0
+    m[40], ls[40], o[40] = (0.0, 0.0, 3.0), np.log(2.0), -1.0
+    for k, i in enumerate(range(41, 51)):
+        side = 1.0 if k % 2 else -1.0
+        m[i] = (side * 1.48, 0.3 * (k / 10.0 - 0.5), 2.0) if k < 6 else (0.2 * k - 1.4, side * 1.1, 2.0)
+        ls[i] = np.log(0.1)
+    m[51:53, 2] = 0.19   # behind the near plane (0.2): culled
+    m[53:56, 2] = 0.21   # just in front of it: large footprints
+    m[53:56, :2] = [[0.0, 0.0], [0.01, -0.01], [-0.02, 0.015]]
+    f = np.float32
+    sc2 = synth.Scene(m.astype(f), ls.astype(f), q.astype(f), o.astype(f), sc.colors, sc.nu)
+    return sc2, cam, T
+
+
+def test_degenerate_gaussians_match_oracle():
+    from paper_2403_16095_b300 import _abi as A
+    sc, cam, T = _degenerate_scene()
+    T = np.asarray(T, np.float32).astype(np.float64)
+    tc, td = synth.random_targets(cam, 1401 + 1)
+    r, grads = _run(A.GS_MODE_FULL, sc, cam, T, tc[0], td[0], W_ALL)
+    ora = oracle.render(f32_scene(sc), cam, T, obs_depth=td[0])
+    im = {k: v.cpu().numpy() for k, v in r.frame_images(0).items()}
+    bad = np.abs(im["color"] - ora["color"]).max(0) > 1e-4
+    for k in ("depth", "alpha", "unc", "nu_map", "T_final"):
+        bad |= np.abs(im[k] - ora[k]) > 1e-4
+    # a differing pixel must sit at an FP32-vs-FP64 decision flip (the depth-gap
+    # margin, channel 4, is left out: equal depths are ordered by index on both
+    # sides, and the ten Gaussians outside the image share z = 2)
+    flip = ora["margins"][[0, 1, 2, 3, 5]].min(axis=0)
+    assert np.all(flip[bad] < 1e-4) and int(bad.sum()) <= 3, int(bad.sum())
+    og = oracle.grad(f32_scene(sc), cam, T, _spec(W_ALL, tc[0], td[0]))
+    for k in PARAMS:
+        got = grads[k].cpu().numpy()
+        assert np.all(got[0:20] == 0.0) and np.all(got[51:53] == 0.0), k  # culled: exactly zero
+        assert np.all(og[k][0:20] == 0.0) and np.all(og[k][51:53] == 0.0), k
+        _rel_check(k, got.astype(np.float64), og[k])
+    _rel_check("pose", r.pose_grad[0].cpu().numpy(), og["pose"], elem=1e-5, norm=1e-5)
+    # the degenerate Gaussians do reach the image: the covering one and the
+    # near-plane ones get gradients
+    assert np.abs(og["means"][40]).max() > 0 and np.abs(og["means"][53:56]).max() > 0
+    rp, _ = _run(A.GS_MODE_POSE, sc, cam, T, tc[0], td[0], W_ALL)
+    _rel_check("pose(POSE mode)", rp.pose_grad[0].cpu().numpy(), og["pose"], elem=1e-5, norm=1e-5)
