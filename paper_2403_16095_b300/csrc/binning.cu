@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(kScanThreads)
         __syncthreads();
         // tiles of kWarpSortKeys or more entries: the first misc[1] of the order
         if (t == 0) misc[1] = (int)s_hist[kWarpSortKeys / 4 - 1];
+        __syncthreads();  // read before the scatter below advances the cursors
     }
     for (int k = lo; k < hi; ++k) {
         const uint32_t c = ranges[2 * (size_t)k + 1];
