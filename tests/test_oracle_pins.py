@@ -258,3 +258,113 @@ def test_adam_first_step_is_signed_learning_rate():
     th = 0.0015
     want = np.array([[math.cos(th), -math.sin(th), 0], [math.sin(th), math.cos(th), 0], [0, 0, 1]])
     np.testing.assert_allclose(st[:9].reshape(3, 3), want, atol=1e-15)
+
+
+def _exp_so3(w):
+    """Rotation matrix of the rotation vector w (scipy's Rodrigues, a library
+    routine independent of the oracle's own exponential)."""
+    from scipy.spatial.transform import Rotation
+    return Rotation.from_rotvec(np.asarray(w, float)).as_matrix()
+
+
+def _log_so3(R):
+    from scipy.spatial.transform import Rotation
+    return Rotation.from_matrix(R).as_rotvec()
+
+
+def test_pose_update_gradient_conversion_by_finite_differences():
+    """Sec. 3.4 (pose as {so(3) | T}, R <- Exp(dR) R, t <- t + dt): the Adam step
+    turns the left-perturbation gradient (g_rho, g_phi) of T(xi) = Exp(xi) T_cw
+    into the gradient of the paper's parameters (dR, dt). Both gradients are
+    taken here by central differences of one toy loss L(R, t) of a rigid point
+    set, each in its own parametrisation; with a large Adam epsilon the first
+    step is d = -lr g / (|g| + eps), which is inverted exactly to read back the
+    converted gradient the oracle used. t is far from 0, so the conversion is
+    not the identity (it differs from g_phi by several times the tolerance)."""
+    rng = np.random.default_rng(11)
+    pts = rng.normal(size=(7, 3))
+    c = rng.normal(size=3)
+    Aq = rng.normal(size=(3, 3))
+    Aq = Aq @ Aq.T
+
+    def loss(R, t):
+        x = pts @ R.T + t
+        return float(np.sum(x @ c) + 0.5 * np.einsum("ni,ij,nj->", x, Aq, x) + np.sum(np.sin(x[:, 0] * x[:, 1])))
+
+    R0 = _exp_so3([0.4, -0.9, 0.3])
+    t0 = np.array([0.7, -0.4, 1.3])
+    h = 1e-6
+    E = np.eye(3)
+    g_rho = np.array([(loss(R0, t0 + h * E[k]) - loss(R0, t0 - h * E[k])) / (2 * h) for k in range(3)])
+    g_phi = np.array([(loss(_exp_so3(h * E[k]) @ R0, _exp_so3(h * E[k]) @ t0)
+                       - loss(_exp_so3(-h * E[k]) @ R0, _exp_so3(-h * E[k]) @ t0)) / (2 * h) for k in range(3)])
+    G_t = np.array([(loss(R0, t0 + h * E[k]) - loss(R0, t0 - h * E[k])) / (2 * h) for k in range(3)])
+    G_R = np.array([(loss(_exp_so3(h * E[k]) @ R0, t0) - loss(_exp_so3(-h * E[k]) @ R0, t0)) / (2 * h)
+                    for k in range(3)])
+    assert np.abs(G_R - g_phi).max() > 1e3 * 1e-7 * np.abs(G_R).max()  # t really matters
+
+    st = np.zeros(25)
+    st[:9] = R0.reshape(-1)
+    st[9:12] = t0
+    lr, eps = 1.0, 1e3
+    oracle.adam_step(st, np.r_[g_rho, g_phi], lr_rot=lr, lr_trans=lr, eps=eps)
+    d_t = st[9:12] - t0
+    d_R = _log_so3(st[:9].reshape(3, 3) @ R0.T)
+
+    def used(d):  # invert d = -lr g / (|g| + eps)
+        r = -np.asarray(d) / lr
+        return eps * r / (1 - np.abs(r))
+
+    scale = max(np.abs(G_t).max(), np.abs(G_R).max())
+    np.testing.assert_allclose(used(d_t), G_t, rtol=0, atol=1e-7 * scale)
+    np.testing.assert_allclose(used(d_R), G_R, rtol=0, atol=1e-7 * scale)
+
+
+def test_pose_update_rotation_step_from_translation_gradient():
+    """Sec. 3.4: with t = (1, 0, 0), g_phi = 0 and g_rho = (0, 1, 0) (the loss
+    grows as the left perturbation moves points along +y), rotate the pose by a
+    small angle d about z in the paper's parameters, R <- Exp(d e_z) R with t
+    held. In the left perturbation Exp(xi) T that is phi = d e_z together with
+    rho = -phi x t = (0, -d, 0), since Exp(phi) would otherwise also turn t to
+    (1, d, 0). The loss therefore changes by g_rho . rho = -d: the rotation
+    gradient about z is -1 (hand-derived), and x and y are 0. Adam's first step
+    is -lr sign(g): t_y decreases by lr_trans and the pose rotates by +lr_rot
+    about z."""
+    st = np.zeros(25)
+    st[:9] = np.eye(3).reshape(-1)
+    st[9:12] = [1.0, 0.0, 0.0]
+    oracle.adam_step(st, np.array([0, 1.0, 0, 0, 0, 0]), lr_rot=0.0015, lr_trans=0.00215, eps=1e-12)
+    th = 0.0015
+    want = np.array([[math.cos(th), -math.sin(th), 0], [math.sin(th), math.cos(th), 0], [0, 0, 1]])
+    np.testing.assert_allclose(st[:9].reshape(3, 3), want, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(st[9:12], [1.0, -0.00215, 0.0], rtol=0, atol=1e-14)
+
+
+def test_adam_moments_over_three_steps_closed_form():
+    """Adam (Sec. 4 learning rates, beta = (0.9, 0.999)) over gradients g, -g, g:
+    m_1 = (1-b1) g, m_2 = -(1-b1)^2 g, m_3 = (1-b1)(1-b1+b1^2) g and
+    v_k = (1-b2^k) g^2, so the bias-corrected steps are -lr g/(|g|+eps) times 1,
+    -(1-b1)/(1+b1) and (1-b1+b1^2)/(1+b1+b1^2) (hand-derived sums of the
+    geometric recursions). t stays parallel to g_rho = (s, s, s), so the
+    rotation gradient is g_phi at every step; the pose after three steps is the
+    product of the three rotation steps (scipy's exponential) and the sum of the
+    translation steps."""
+    b1, b2, eps, lr_r, lr_t = 0.9, 0.999, 1e-8, 0.0015, 0.00215
+    g = np.array([0.02, 0.02, 0.02, 0.3, -1.7, 0.05])
+    st = np.zeros(25)
+    R0 = _exp_so3([0.1, 0.2, -0.3])
+    st[:9] = R0.reshape(-1)
+    t0 = np.array([0.5, 0.5, 0.5])
+    st[9:12] = t0
+    for k, s in enumerate((1, -1, 1)):
+        oracle.adam_step(st, s * g, lr_rot=lr_r, lr_trans=lr_t, beta1=b1, beta2=b2, eps=eps)
+    assert st[24] == 3
+    np.testing.assert_allclose(st[12:18], (1 - b1) * (1 - b1 + b1 * b1) * g, rtol=1e-13, atol=0)
+    np.testing.assert_allclose(st[18:24], (1 - b2 ** 3) * g * g, rtol=1e-13, atol=0)
+    unit = g / (np.abs(g) + eps)
+    f = [1.0, -(1 - b1) / (1 + b1), (1 - b1 + b1 * b1) / (1 + b1 + b1 * b1)]
+    lr = np.r_[[lr_t] * 3, [lr_r] * 3]
+    d = [-lr * fk * unit for fk in f]
+    np.testing.assert_allclose(st[9:12], t0 + d[0][:3] + d[1][:3] + d[2][:3], rtol=0, atol=1e-15)
+    R = _exp_so3(d[2][3:]) @ _exp_so3(d[1][3:]) @ _exp_so3(d[0][3:]) @ R0
+    np.testing.assert_allclose(st[:9].reshape(3, 3), R, rtol=0, atol=1e-14)
