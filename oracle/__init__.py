@@ -42,7 +42,7 @@ class _Opts(C.Structure):
 class _Loss(C.Structure):
     _fields_ = [("w_color", C.c_double), ("w_depth", C.c_double), ("w_unc", C.c_double),
                 ("w_nu", C.c_double), ("unc_tau", C.c_double), ("target_color", _dp),
-                ("target_depth", _dp), ("w_align", C.c_double)]
+                ("target_depth", _dp), ("w_align", C.c_double), ("mask", C.POINTER(C.c_ubyte))]
 
 
 class _Image(C.Structure):
@@ -80,7 +80,9 @@ def lib():
         _lib.orc_render.argtypes = [C.POINTER(_Scene), C.POINTER(_Cam), _dp, C.POINTER(_Opts), _dp,
                                     C.c_int, C.POINTER(_Image)]
         _lib.orc_render_pixels.argtypes = [C.POINTER(_Scene), C.POINTER(_Cam), _dp, C.POINTER(_Opts),
-                                           _dp, C.c_int, _ip, C.POINTER(_Image)]
+                                           _dp, C.c_int, _ip, C.c_int, C.POINTER(_Image)]
+        _lib.orc_fd_window.argtypes = [C.POINTER(_Scene), C.c_int, C.POINTER(_Cam), _dp, C.POINTER(_Opts),
+                                       C.POINTER(_Loss), C.c_int, _ip, C.c_double, _dp, _ip]
         _lib.orc_loss_value.argtypes = [C.POINTER(_Scene), C.POINTER(_Cam), _dp, C.POINTER(_Opts),
                                         C.POINTER(_Loss), _dp, C.POINTER(C.c_uint64)]
         _lib.orc_grad.argtypes = [C.POINTER(_Scene), C.POINTER(_Cam), _dp, C.POINTER(_Opts),
@@ -140,13 +142,20 @@ class LossSpec:
     target_color: np.ndarray | None = None   # [3,H,W]
     target_depth: np.ndarray | None = None   # [H,W] (also the sensor depth of U)
     w_align: float = 0.0                     # L_align of Eq. 12
+    pixels: np.ndarray | None = None         # flat pixel indices y*W+x: only these enter the sum
 
 
 class _KeepLoss:
-    def __init__(self, L: LossSpec):
+    def __init__(self, L: LossSpec, n_pix: int | None = None):
         self.tc = None if L.target_color is None else _f64(L.target_color)
         self.td = None if L.target_depth is None else _f64(L.target_depth)
-        self.s = _Loss(L.w_color, L.w_depth, L.w_unc, L.w_nu, L.unc_tau, _p(self.tc), _p(self.td), L.w_align)
+        self.mask = None
+        if L.pixels is not None:
+            assert n_pix is not None
+            self.mask = np.zeros(n_pix, np.uint8)
+            self.mask[np.asarray(L.pixels, np.int64)] = 1
+        self.s = _Loss(L.w_color, L.w_depth, L.w_unc, L.w_nu, L.unc_tau, _p(self.tc), _p(self.td), L.w_align,
+                       _p(self.mask, C.POINTER(C.c_ubyte)))
 
 
 # ----------------------------------------------------------------- API
@@ -193,15 +202,17 @@ def render(scene, cam, T, obs_depth=None, mode="rect", jclamp=1.3, nu_cull=0.0):
     return o
 
 
-def render_pixels(scene, cam, T, pix, obs_depth=None, jclamp=1.3, nu_cull=0.0):
-    """Sampled pixels (flat indices y*W+x), each computed on its own by brute force."""
+def render_pixels(scene, cam, T, pix, obs_depth=None, jclamp=1.3, nu_cull=0.0, mode="brute"):
+    """Sampled pixels (flat indices y*W+x): 'brute' scans every Gaussian for
+    each pixel; 'rect' draws the candidates from the row lists, as render()
+    does (cheaper when many pixels are sampled)."""
     k = _Keep(scene)
     Tc = _f64(T).reshape(3, 4)
     od = None if obs_depth is None else _f64(obs_depth)
     pix = np.ascontiguousarray(pix, dtype=np.int32)
     o, im = _image_bufs(len(pix))
     r = lib().orc_render_pixels(C.byref(k.s), C.byref(_cam(cam)), _p(Tc), C.byref(_Opts(jclamp, nu_cull)),
-                                _p(od), len(pix), _p(pix, _ip), C.byref(im))
+                                _p(od), len(pix), _p(pix, _ip), 1 if mode == "rect" else 0, C.byref(im))
     assert r == 0
     return o
 
@@ -209,7 +220,7 @@ def render_pixels(scene, cam, T, pix, obs_depth=None, jclamp=1.3, nu_cull=0.0):
 def loss_value(scene, cam, T, L: LossSpec, jclamp=1.3, nu_cull=0.0):
     """(loss, decision hash) for one frame."""
     k = _Keep(scene)
-    kl = _KeepLoss(L)
+    kl = _KeepLoss(L, cam.width * cam.height)
     Tc = _f64(T).reshape(3, 4)
     v = C.c_double(0)
     h = C.c_uint64(0)
@@ -223,7 +234,7 @@ def grad(scene, cam, T, L: LossSpec, jclamp=1.3, nu_cull=0.0):
     """Loss, parameter gradients, per-Gaussian 2D gradients and the left se(3)
     pose gradient (rho, phi) for one frame, all FP64."""
     k = _Keep(scene)
-    kl = _KeepLoss(L)
+    kl = _KeepLoss(L, cam.width * cam.height)
     n = scene.n
     Tc = _f64(T).reshape(3, 4)
     o = dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
@@ -238,6 +249,33 @@ def grad(scene, cam, T, L: LossSpec, jclamp=1.3, nu_cull=0.0):
     assert r == 0
     o["loss"] = v.value
     return o
+
+
+FD_PARAMS = (("means", 3), ("log_scales", 3), ("quats", 4), ("opacity_logit", 1), ("colors", 3), ("nu", 1))
+
+
+def fd_window(scene, cams, Ts, losses, sel, h=1e-4, jclamp=1.3, nu_cull=0.0):
+    """Central differences (h, FP64) of the window loss sum_f L_f over frames
+    (cams[f], Ts[f], losses[f]) for all 15 parameters of each Gaussian in
+    ``sel``, re-blending only the pixels the perturbed Gaussian can reach (the
+    same value as differencing full-image loss_value() sums).
+
+    Returns (fd [len(sel), 15], stable [len(sel), 15] bool) with the parameters
+    in FD_PARAMS order; stable is False where some pixel's blend decisions or
+    the sign of an absolute-value residual differ between the base and x +- h."""
+    k = _Keep(scene)
+    sel = np.ascontiguousarray(sel, dtype=np.int32)
+    F = len(cams)
+    camarr = (_Cam * F)(*[_cam(c) for c in cams])
+    Tc = _f64(np.stack([np.asarray(T, np.float64).reshape(3, 4) for T in Ts]))
+    keeps = [_KeepLoss(L, c.width * c.height) for L, c in zip(losses, cams)]
+    larr = (_Loss * F)(*[kl.s for kl in keeps])
+    fd = np.zeros((len(sel), 15))
+    st = np.zeros((len(sel), 15), np.int32)
+    r = lib().orc_fd_window(C.byref(k.s), F, camarr, _p(Tc), C.byref(_Opts(jclamp, nu_cull)), larr, len(sel),
+                            _p(sel, _ip), float(h), _p(fd), _p(st, _ip))
+    assert r == 0
+    return fd, st.astype(bool)
 
 
 def nu_estimate(scene, cams, Ts, obs_depths, tau=0.0, low_opacity=0.01, jclamp=1.3, nu_cull=0.0):

@@ -27,6 +27,10 @@
  *     Lie algebra; the derivation is reconstructed here from first principles).
  *   - Tile binning by brute force (Sec. 3.1: visible Gaussians pre-sorted near
  *     to far), for the bit-exact tile-list comparison.
+ *   - Central differences of a keyframe window's loss (Eq. 21) for every
+ *     parameter of chosen Gaussians, re-blending only the pixels the perturbed
+ *     Gaussian can reach, with the active-set check of each element.
+ *   - The Adam step on the pose in the {so(3) | T} form (Sec. 3.4, Sec. 4).
  *
  * Readings where the paper is silent (prior-art values): near plane 0.2 m is a
  * camera input; dilation 0.3 px^2; alpha = min(0.99, opacity*G); entries with
@@ -64,6 +68,8 @@ typedef struct {
     const double *target_color; /* [3][H][W]                            */
     const double *target_depth; /* [H][W]; also the sensor depth D of U */
     double w_align;             /* weight of L_align (Eq. 12)           */
+    const unsigned char *mask;  /* [H][W] or NULL: only pixels with mask != 0 enter the loss
+                                   (sampled comparisons; the 1/(HW) factor stays the image's) */
 } orc_loss;
 
 typedef struct { /* optional outputs; NULL members are skipped */
@@ -427,17 +433,21 @@ int orc_render(const orc_scene *sc, const orc_cam *cam, const double *Tcw, const
     return err ? -1 : 0;
 }
 
-/* Sampled forward: only the listed pixel indices (p = y*W + x), each computed
- * on its own by brute force; outputs are indexed by sample position. */
+/* Sampled forward: only the listed pixel indices (p = y*W + x); outputs are
+ * indexed by sample position. mode 0 = brute force per pixel, 1 = candidates
+ * from the row lists (rect-scatter), as in orc_render. */
 int orc_render_pixels(const orc_scene *sc, const orc_cam *cam, const double *Tcw, const orc_opts *op,
-                      const double *obs_depth, int n_pix, const int *pix, orc_image *im) {
-    int W = cam->width;
+                      const double *obs_depth, int n_pix, const int *pix, int mode, orc_image *im) {
+    int W = cam->width, H = cam->height;
     gproj *G = project_all(sc, cam, Tcw, op);
     if (!G) return -1;
+    rowlists rl = {0, 0}, *prl = NULL;
+    if (mode == 1) { if (build_rows(G, sc->n, H, &rl)) { free(G); return -1; } prl = &rl; }
+    int cap = max_row_len(prl, H, sc->n);
     int err = 0;
 #pragma omp parallel num_threads(orc_get_threads())
     {
-        zent *buf = (zent *)malloc(sizeof(zent) * (size_t)(sc->n > 0 ? sc->n : 1));
+        zent *buf = (zent *)malloc(sizeof(zent) * (size_t)(cap > 0 ? cap : 1));
         if (!buf) {
 #pragma omp atomic write
             err = 1;
@@ -446,14 +456,14 @@ int orc_render_pixels(const orc_scene *sc, const orc_cam *cam, const double *Tcw
         for (int s = 0; s < n_pix; ++s) {
             if (!buf) continue;
             int p = pix[s], px = p % W, py = p / W;
-            int m = collect(G, sc->n, NULL, px, py, buf);
+            int m = collect(G, sc->n, prl, px, py, buf);
             pixout o;
             blend_pixel(sc, G, buf, m, px, py, obs_depth ? obs_depth[p] : 0, obs_depth != NULL, &o, NULL);
             store_pixel(im, n_pix, s, &o);
         }
         free(buf);
     }
-    free(G);
+    free(rl.off); free(rl.idx); free(G);
     return err ? -1 : 0;
 }
 
@@ -480,6 +490,7 @@ int orc_loss_value(const orc_scene *sc, const orc_cam *cam, const double *Tcw, c
             uint64_t h = 1469598103934665603ULL;
             for (int px = 0; px < W; ++px) {
                 int p = py * W + px;
+                if (L->mask && !L->mask[p]) continue;
                 int m = collect(G, sc->n, &rl, px, py, buf);
                 pixout o;
                 double g[8];
@@ -662,6 +673,7 @@ int orc_grad(const orc_scene *sc, const orc_cam *cam, const double *Tcw, const o
             if (!buf || !cb || err) continue;
             for (int px = 0; px < W; ++px) {
                 int p = py * W + px;
+                if (L->mask && !L->mask[p]) continue;
                 int m = collect(G, n, &rl, px, py, buf);
                 double Dp = L->target_depth ? L->target_depth[p] : 0;
                 pixout o;
@@ -741,6 +753,179 @@ int orc_grad(const orc_scene *sc, const orc_cam *cam, const double *Tcw, const o
         if (loss_out) *loss_out = tot;
     }
     free(acc); free(row_loss); free(vid); free(rl.off); free(rl.idx); free(G);
+    return err ? -1 : 0;
+}
+
+/* ---------------------------------------- windowed central differences (O14) */
+/* Per-pixel state the loss is smooth in: the blend decisions of the pixel
+ * (membership, clamp, stop; o->hash), which entry is the median (Eq. 7-8: a
+ * jump of D_median when T crosses 0.5 at another entry) and the sign of every
+ * absolute-value residual of the loss (its kinks). Two evaluations with equal
+ * states differ smoothly, so a central difference across them is a derivative
+ * estimate. */
+static uint64_t loss_state(const orc_loss *L, const pixout *o, int p, int HW) {
+    uint64_t h = fnv(o->hash, (uint64_t)(int64_t)o->med), bits = 0;
+    int b = 0;
+    if (L->w_color != 0 && L->target_color)
+        for (int c = 0; c < 3; ++c) {
+            double d = o->color[c] - L->target_color[c * HW + p];
+            bits |= (uint64_t)(d > 0 ? 1 : (d < 0 ? 2 : 3)) << (2 * b++);
+        }
+    if (L->w_depth != 0 && L->target_depth) {
+        double d = o->depth - L->target_depth[p];
+        bits |= (uint64_t)(d > 0 ? 1 : (d < 0 ? 2 : 3)) << (2 * b++);
+    }
+    if (L->w_unc != 0) bits |= (uint64_t)(o->unc > 0 ? 1 : (o->unc < 0 ? 2 : 3)) << (2 * b++);
+    if (L->w_align != 0) {
+        double d = o->depth - o->median;
+        bits |= (uint64_t)(d > 0 ? 1 : (d < 0 ? 2 : 3)) << (2 * b++);
+    }
+    return fnv(h, bits);
+}
+
+/* The 15 scalar parameters of Gaussian i, in the order means (3), log-scales
+ * (3), quaternion (4), opacity logit, colour (3), nu. */
+static void params_of(const orc_scene *sc, int i, double v[15]) {
+    for (int k = 0; k < 3; ++k) v[k] = sc->means[3 * i + k];
+    for (int k = 0; k < 3; ++k) v[3 + k] = sc->log_scales[3 * i + k];
+    for (int k = 0; k < 4; ++k) v[6 + k] = sc->quats[4 * i + k];
+    v[10] = sc->opacity_logit[i];
+    for (int k = 0; k < 3; ++k) v[11 + k] = sc->colors[3 * i + k];
+    v[14] = sc->nu[i];
+}
+
+/* Central differences (L(x + h e) - L(x - h e)) / 2h of the window loss
+ * sum_f L_f (Eq. 21: one keyframe window, each frame with its own pose and
+ * loss) for all 15 parameters of each listed Gaussian.
+ *
+ * Perturbing Gaussian i changes only the pixels inside the union of its pixel
+ * rects over the base and perturbed projections; every other pixel's list and
+ * blend are identical, so its loss terms cancel. Per frame the full projection
+ * and the row lists are built once; per (Gaussian, frame) the pixels of that
+ * union are blended again for the base and the 30 perturbed variants, each
+ * pixel's list drawn from the frame's row lists (index order kept, so the
+ * (z, index) order is that of the full render). stable[s][k] = 0 when any
+ * re-blended pixel's state (loss_state) under +h or -h differs from the base:
+ * the active set changed, and the difference is not a derivative estimate. */
+int orc_fd_window(const orc_scene *sc, int n_frames, const orc_cam *cams, const double *Tcw,
+                  const orc_opts *op, const orc_loss *losses, int n_sel, const int *sel, double h,
+                  double *fd, int *stable) {
+    enum { NP = 15, NV = 31 };
+    for (int e = 0; e < n_sel * NP; ++e) { fd[e] = 0; stable[e] = 1; }
+    int err = 0;
+    for (int f = 0; f < n_frames && !err; ++f) {
+        const orc_cam *cam = &cams[f];
+        const double *T = Tcw + 12 * f;
+        const orc_loss *L = &losses[f];
+        int W = cam->width, H = cam->height, HW = W * H;
+        gproj *G = project_all(sc, cam, T, op);
+        if (!G) return -1;
+        rowlists rl;
+        if (build_rows(G, sc->n, H, &rl)) { free(G); return -1; }
+#pragma omp parallel num_threads(orc_get_threads())
+        {
+            int cap = 0;
+            int *cand = NULL;
+            gproj *lg = NULL;
+            double *lcol = NULL, *lnu = NULL;
+            zent *buf = NULL;
+            uint64_t *base_state = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)W);
+#pragma omp for schedule(dynamic, 1)
+            for (int s = 0; s < n_sel; ++s) {
+                if (err || !base_state) {
+#pragma omp atomic write
+                    err = 1;
+                    continue;
+                }
+                int i = sel[s];
+                double p0[NP], vc[NV][3], vn[NV];
+                gproj gv[NV];
+                params_of(sc, i, p0);
+                /* variant 0: base; 1 + 2k: +h on parameter k; 2 + 2k: -h */
+                int ux0 = W, uy0 = H, ux1 = -1, uy1 = -1;
+                for (int v = 0; v < NV; ++v) {
+                    double pv[NP];
+                    memcpy(pv, p0, sizeof(pv));
+                    if (v > 0) pv[(v - 1) / 2] += (v & 1) ? h : -h;
+                    orc_scene one = {1, pv, pv + 3, pv + 6, pv + 10, pv + 11, pv + 14};
+                    project_one(&one, 0, cam, T, op, &gv[v]);
+                    for (int c = 0; c < 3; ++c) vc[v][c] = pv[11 + c];
+                    vn[v] = pv[14];
+                    if (gv[v].valid) {
+                        if (gv[v].rect[0] < ux0) ux0 = gv[v].rect[0];
+                        if (gv[v].rect[1] < uy0) uy0 = gv[v].rect[1];
+                        if (gv[v].rect[2] > ux1) ux1 = gv[v].rect[2];
+                        if (gv[v].rect[3] > uy1) uy1 = gv[v].rect[3];
+                    }
+                }
+                if (ux1 < ux0) continue; /* culled in every variant: no pixel changes */
+                double acc[NV];
+                int moved[NV];
+                for (int v = 0; v < NV; ++v) { acc[v] = 0; moved[v] = 0; }
+                for (int y = uy0; y <= uy1; ++y) {
+                    /* candidates of this row over [ux0, ux1], in index order, with a
+                     * slot for Gaussian i at its index position */
+                    int row_n = rl.off[y + 1] - rl.off[y] + 1;
+                    if (row_n > cap) {
+                        cap = row_n * 2;
+                        cand = (int *)realloc(cand, sizeof(int) * (size_t)cap);
+                        lg = (gproj *)realloc(lg, sizeof(gproj) * (size_t)cap);
+                        lcol = (double *)realloc(lcol, sizeof(double) * 3 * (size_t)cap);
+                        lnu = (double *)realloc(lnu, sizeof(double) * (size_t)cap);
+                        buf = (zent *)realloc(buf, sizeof(zent) * (size_t)cap);
+                        if (!cand || !lg || !lcol || !lnu || !buf) {
+#pragma omp atomic write
+                            err = 1;
+                            break;
+                        }
+                    }
+                    int nc = 0, slot = -1;
+                    for (int e = rl.off[y]; e < rl.off[y + 1]; ++e) {
+                        int j = rl.idx[e];
+                        if (j == i) continue;
+                        if (G[j].rect[2] < ux0 || G[j].rect[0] > ux1) continue;
+                        if (slot < 0 && j > i) { slot = nc; cand[nc++] = i; }
+                        cand[nc++] = j;
+                    }
+                    if (slot < 0) { slot = nc; cand[nc++] = i; }
+                    for (int c = 0; c < nc; ++c) {
+                        if (c == slot) continue;
+                        int j = cand[c];
+                        lg[c] = G[j];
+                        for (int k = 0; k < 3; ++k) lcol[3 * c + k] = sc->colors[3 * j + k];
+                        lnu[c] = sc->nu[j];
+                    }
+                    orc_scene lsc = {nc, NULL, NULL, NULL, NULL, lcol, lnu};
+                    for (int v = 0; v < NV; ++v) {
+                        lg[slot] = gv[v];
+                        for (int k = 0; k < 3; ++k) lcol[3 * slot + k] = vc[v][k];
+                        lnu[slot] = vn[v];
+                        for (int x = ux0; x <= ux1; ++x) {
+                            int p = y * W + x;
+                            if (L->mask && !L->mask[p]) continue;
+                            int m = collect(lg, nc, NULL, x, y, buf);
+                            double Dp = L->target_depth ? L->target_depth[p] : 0;
+                            pixout o;
+                            double g8[8];
+                            blend_pixel(&lsc, lg, buf, m, x, y, Dp, L->target_depth != NULL, &o, NULL);
+                            double val = pixel_loss(L, &o, p, HW, g8);
+                            uint64_t st = loss_state(L, &o, p, HW);
+                            if (v == 0) base_state[x] = st;
+                            else if (st != base_state[x]) moved[v] = 1;
+                            acc[v] += val;
+                        }
+                    }
+                }
+                if (err) continue;
+                for (int k = 0; k < NP; ++k) {
+                    fd[s * NP + k] += (acc[1 + 2 * k] - acc[2 + 2 * k]) / (2.0 * h);
+                    if (moved[1 + 2 * k] || moved[2 + 2 * k]) stable[s * NP + k] = 0;
+                }
+            }
+            free(cand); free(lg); free(lcol); free(lnu); free(buf); free(base_state);
+        }
+        free(rl.off); free(rl.idx); free(G);
+    }
     return err ? -1 : 0;
 }
 
