@@ -71,8 +71,33 @@ FWD_FLOP_PER_CONTRIB = 26
 # (profiles/k_render_fused_pose_track-640x480-300k.md, cold cache); None once
 # the kernel changes.
 FUSED_DRAM_BYTES_PER_LAUNCH = 16.350208e6 + 0
+# DRAM bytes (read + write) of one whole tracking iteration (the 6 kernels),
+# from one ncu capture with the caches carried over between kernels; None
+# until captured for the current build.
+DRAM_BYTES_PER_ITERATION = None
 FP32_LANES_PER_SM = 128
-N_SM = 148
+
+
+def _fp32_peak(dev, mhz):
+    """FP32 FMA peak in TFLOP/s: SMs (read from the device) x 128 lanes x 2 x clock."""
+    import torch
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    return n_sm * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, n_sm
+
+
+# Algorithmic HBM bytes of one tracking iteration, per unit (each datum moved
+# once, in this library's layouts): every Gaussian's FP32 parameters read
+# (60 B); per visible record its 64 B record and 144 B pose Jacobian written,
+# its rect + depth read by the binning (20 B) and record + Jacobian read once
+# by the tracking pass (208 B); per culled record its 16 B rect written; per
+# (Gaussian, tile) pair 12 B written by the fill, read and written once by the
+# sort (24 B), and its 4 B index read by the tracking pass; per pixel the RGB-D
+# target read (16 B).
+HBM_B_PER_GAUSSIAN = 60
+HBM_B_PER_VISIBLE = 64 + 144 + 20 + 208
+HBM_B_PER_CULLED = 16
+HBM_B_PER_PAIR = 12 + 24 + 4
+HBM_B_PER_PIXEL = 16
 
 
 def _args():
@@ -185,6 +210,36 @@ def cpu_oracle_iterations(sc, cam, gt_poses, starts, n_iter: int, targets=None):
         g = oracle.grad(sc, cam, Tc, L)
         oracle.adam_step(st, g["pose"])
     return time.perf_counter() - t0, cores
+
+
+def cpu_baseline(sc, cam, gt, starts, n_all: int, n_one: int):
+    """The oracle's tracking iteration timed on all host cores (n_all
+    iterations) and on one core (n_one), plus the brute-force O(HW N) render of
+    the 128x96 / 2k scene; the oracle as it stands, on a bounded sample."""
+    import oracle
+    import synth
+    ref = oracle.render(sc, cam, gt[0])
+    tg = (ref["color"], ref["depth"])
+    cpu_oracle_iterations(sc, cam, gt, starts, 1, tg)  # warm (page-in, thread pool)
+    secs, cores = cpu_oracle_iterations(sc, cam, gt, starts, n_all, tg)
+    out = {"value": n_all / secs, "unit": "iters/s", "cores": cores, "kind": "oracle",
+           "sample": f"{n_all} FP64 oracle tracking iterations (forward + analytic pose gradient + Adam) on "
+                     f"frame 0, 640x480, 300k Gaussians, rect-scatter lists"}
+    if n_one > 0:
+        prev = oracle.threads()
+        oracle.set_threads(1)
+        try:
+            s1, _ = cpu_oracle_iterations(sc, cam, gt, starts, n_one, tg)
+        finally:
+            oracle.set_threads(prev)
+        out["single_core"] = {"value": n_one / s1, "unit": "iters/s", "cores": 1,
+                              "sample": f"{n_one} of the same iterations on one core"}
+    tsc, tcam, tT = synth.tiny_scene()
+    t0 = time.perf_counter()
+    oracle.render(tsc, tcam, tT, mode="brute")
+    out["brute_force_tiny"] = {"value": 1.0 / (time.perf_counter() - t0), "unit": "renders/s", "cores": cores,
+                               "sample": "one brute-force (every Gaussian per pixel) oracle render, 128x96, 2k"}
+    return out
 
 
 def run_reference(a):
@@ -341,7 +396,7 @@ def run_ours(a):
     # launch (or, with --unfused, the POSE backward alone)
     peaks = _peaks()
     mhz = peaks.get("sm_max_mhz", 2032.0)
-    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12  # TFLOP/s
+    fp32_peak, n_sm = _fp32_peak(dev, mhz)  # TFLOP/s
     bwd_avg_ms = statistics.mean(bwd_ms)
     E = statistics.mean(contrib)
     if tr.fused:
@@ -357,21 +412,34 @@ def run_ours(a):
     roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": fp32_peak,
             "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch, cold cache",
-            "peak_source": f"148 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (max SM clock)",
+            "peak_source": f"{n_sm} SMs (device query) x 128 FP32 lanes x 2 x {mhz:.0f} MHz (max SM clock)",
             "flop_per_contribution": flop, "contributions_per_launch": E,
             "avg_launch_ms": bwd_avg_ms, "launches": len(bwd_ms),
             "launch_timing": f"CUDA events around the launch on iterations 0, {TIMING_EVERY}, ... of every timed frame"}
     bwd_share = bwd_avg_ms * ITERS * len(step_ms) / sum(step_ms)
 
+    # ---- achieved HBM fraction: algorithmic bytes of an iteration over its time
+    visible = int((tr.rast.touched > 0).sum())
+    pairs = int(tr.rast.read_status()[1])
+    hw = int(cam.width) * int(cam.height)
+    alg_bytes = (HBM_B_PER_GAUSSIAN * g.n + HBM_B_PER_VISIBLE * visible + HBM_B_PER_CULLED * (g.n - visible)
+                 + HBM_B_PER_PAIR * pairs + HBM_B_PER_PIXEL * hw)
+    ms_it = total_ms / (a.steps * ITERS)
+    hbm_peak = peaks.get("hbm_gbs")
+    hbm = {"algorithmic_bytes_per_iteration": alg_bytes, "achieved_gbs": alg_bytes / (ms_it * 1e-3) / 1e9,
+           "peak_gbs": hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if hbm_peak else None,
+           "frac": (alg_bytes / (ms_it * 1e-3) / 1e9) / hbm_peak if hbm_peak else None,
+           "visible_records": visible, "pairs": pairs, "pixels": hw,
+           "dram_bytes_per_iteration_ncu": DRAM_BYTES_PER_ITERATION,
+           "dram_frac_ncu": (DRAM_BYTES_PER_ITERATION / (ms_it * 1e-3) / 1e9 / hbm_peak
+                             if (DRAM_BYTES_PER_ITERATION and hbm_peak) else None),
+           "bytes": "60 B params per Gaussian; per visible record 64 B record + 144 B Jacobian written, "
+                    "20 B read by binning, 208 B read by the tracking pass; 16 B rect per culled record; "
+                    "40 B per pair (fill, sort, index read); 16 B RGB-D target per pixel"}
+
     cpu = None
     if not a.no_cpu_baseline:
-        n_it = a.cpu_iters or 3
-        import oracle
-        ref = oracle.render(sc, cam, gt[0])
-        secs, cores = cpu_oracle_iterations(sc, cam, gt, starts, n_it, (ref["color"], ref["depth"]))
-        cpu = {"value": n_it / secs, "unit": "iters/s", "cores": cores, "kind": "oracle",
-               "sample": f"{n_it} FP64 oracle tracking iterations (forward + analytic pose gradient + Adam) "
-                         f"on frame 0, 640x480, 300k Gaussians"}
+        cpu = cpu_baseline(sc, cam, gt, starts, a.cpu_iters or 10, 1)
 
     launches = tr.kernel_launches_per_iteration() * ITERS * a.steps
     line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws, "steps": a.steps,
@@ -383,7 +451,7 @@ def run_ours(a):
                        "ms_per_iteration": total_ms / (a.steps * ITERS), "wall_s": wall,
                        "pairs_per_iteration": int(tr.rast.read_status()[1]),
                        "contributions_per_iteration": E, "bwd_share_of_step": bwd_share},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "roofline": roof, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "context": "paper: 7.89 ms x 15 tracking iterations on an RTX 4090 (Table 5, Replica office-0)"}
     print(json.dumps(line), flush=True)
     if ws > 1:
@@ -421,7 +489,9 @@ def run_batch(a):
     pert["means"] += rng.normal(0, 0.01, pert["means"].shape).astype(np.float32)
     pert["colors"] = np.clip(pert["colors"] + rng.normal(0, 0.05, pert["colors"].shape), 0, 1).astype(np.float32)
     g = Gaussians(*(torch.from_numpy(pert[k]).to(dev) for k in names))
-    loss = dict(w_color=0.7, w_depth=0.25, w_unc=0.05, w_align=0.25, target_color=tcol, target_depth=tdep)
+    # the mapping weights of Sec. 4 (Replica): omega_1 colour 0.7, omega_3 geo 0.25,
+    # omega_4 align 0.25, omega_6 var 0.15 (SSIM and L_iso are off the rasterizer)
+    loss = dict(w_color=0.7, w_depth=0.25, w_unc=0.15, w_align=0.25, target_color=tcol, target_depth=tdep)
     tile, tune = a.tile, None
     if a.workload == "uneven":
         tile, tune = autotune_tile(cams, g, Tt, tdep, mode=A.GS_MODE_FULL, loss=loss)
@@ -473,7 +543,7 @@ def run_batch(a):
     value = F * a.steps / (total_ms / 1e3)
     peaks = _peaks()
     mhz = peaks.get("sm_max_mhz", 2032.0)
-    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    fp32_peak, _ = _fp32_peak(dev, mhz)
     bwd_ms = statistics.mean(per["backward"])
     E = statistics.mean(contrib)
     achieved = E * BWD_FULL_FLOP_PER_CONTRIB / (bwd_ms * 1e-3) / 1e12

@@ -200,7 +200,7 @@ def test_autotuned_uneven_batch_is_tile_invariant():
     tg = [synth.random_targets(c, 1006 + 10 + f, depth_range=(0.5, 4.0)) for f, c in enumerate(cams)]
     tc = torch.from_numpy(np.concatenate([t[0].reshape(-1) for t in tg])).cuda()
     td = torch.from_numpy(np.concatenate([t[1].reshape(-1) for t in tg])).cuda()
-    loss = dict(w_color=0.7, w_depth=0.25, w_unc=0.05, w_align=0.25, target_color=tc, target_depth=td)
+    loss = dict(w_color=0.7, w_depth=0.25, w_unc=0.15, w_align=0.25, target_color=tc, target_depth=td)
     best, times = autotune_tile(cams, g, Tt, td, mode=A.GS_MODE_FULL, loss=loss)
     assert best == min(times, key=times.get) and set(times) == {8, 16, 32}
     imgs, grads = {}, {}
