@@ -1,6 +1,7 @@
 // C ABI entry points of libgs (declared in include/gs.h): argument checks,
 // frame tables and kernel launches. Nothing here allocates memory or
 // synchronises with the host.
+#include <atomic>
 #include <climits>
 #include <cstdarg>
 #include <cstdio>
@@ -117,6 +118,23 @@ size_t bwd_ws_bytes(int n_records, int mode) { return grad2d_bytes(n_records, mo
 
 namespace gs {
 void set_error_message(const char *msg) { snprintf(g_msg, sizeof(g_msg), "%s", msg); }
+
+int device_sm_count() {
+    // one slot per device ordinal; 0 = not read yet. A host attribute query,
+    // allowed while a stream is being captured.
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    // (148, the B300 count, only if the query itself fails)
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 148;
+    if (dev < 64) {
+        const int c = cache[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) return 148;
+    if (dev < 64) cache[dev].store(n, std::memory_order_relaxed);
+    return n;
+}
 }  // namespace gs
 
 extern "C" {

@@ -60,7 +60,8 @@ __device__ __forceinline__ bool status_ok(const int32_t *status) { return status
 // chunks per CTA would hand all of the expansion work to a few CTAs. Small
 // batches keep one record per thread so that the grid still fills the GPU.
 constexpr int kRecLarge = 8;
-constexpr int kLargeBatch = 148 * 2048 * kRecLarge / 2;  // records; below it, one per thread
+// records per SM (x 2,048 threads x kRecLarge / 2) from which a batch takes kRecLarge per thread
+constexpr int kLargeBatchPerSm = 2048 * kRecLarge / 2;
 struct RecLoad {
     int touched;
     int4 rc;
@@ -613,7 +614,7 @@ size_t bin_workspace_bytes(int n_records, int capacity) {
 cudaError_t launch_bin_clear(uint32_t *ranges, const FrameTable &ft, int capacity, void *ws, cudaStream_t s) {
     int *misc = reinterpret_cast<int *>(static_cast<char *>(ws) + layout(capacity).misc);
     const int n_words = 2 * ft.total_tiles;
-    const int clear_grid = n_words > 0 ? min((n_words + kThreads - 1) / kThreads, 4 * 148) : 1;
+    const int clear_grid = n_words > 0 ? min((n_words + kThreads - 1) / kThreads, 4 * device_sm_count()) : 1;
     return launch_chained(k_bin_clear, dim3(clear_grid), dim3(kThreads), 0, s, ranges, n_words, misc);
 }
 
@@ -631,7 +632,7 @@ cudaError_t launch_bin_tiles(const float *rec, const int *touched, int n_records
     cudaError_t err;
     if (!counted && (err = launch_bin_clear(ranges, ft, capacity, ws, s)) != cudaSuccess) return err;
     if (ft.total_tiles == 0) return cudaSuccess;
-    const bool large = n_records >= kLargeBatch;
+    const bool large = (long long)n_records >= (long long)kLargeBatchPerSm * device_sm_count();
     const int per_cta = kThreads * (large ? kRecLarge : 1);
     const int grid = n_records > 0 ? (int)(((size_t)n_records + per_cta - 1) / per_cta) : 1;
     auto count = large ? k_tile_count<kRecLarge> : k_tile_count<1>;

@@ -93,6 +93,10 @@ __device__ __forceinline__ int frame_of_tile(const FrameTable &ft, int gtile) {
 // message returned by gs_last_error() on this host thread (api.cu)
 void set_error_message(const char *msg);
 
+// streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount,
+// read once per device and cached; api.cu); grid caps are multiples of it
+int device_sm_count();
+
 // ----------------------------------------------------------------- launchers
 // project.cu
 // tile_counts: NULL, or the tile counters (ranges) of a following binning,

@@ -71,7 +71,8 @@ __global__ void __launch_bounds__(kThreads)
 
 int grid_for(long long items) {
     const long long want = (items + kThreads - 1) / kThreads;
-    return (int)(want < 148 * 8 ? (want > 0 ? want : 1) : 148 * 8);
+    const long long cap = 8LL * device_sm_count();
+    return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
 }  // namespace

@@ -307,7 +307,7 @@ cudaError_t launch_spatial_order(const float *means, int n, uint32_t *perm, void
     float *part = reinterpret_cast<float *>(w + L.part);
     const int nbox = blocks_for(n, kBoxBlocks);
     k_bbox_partial<<<nbox, kThreads, 0, s>>>(means, n, part, status);
-    k_morton<<<blocks_for(n, 148 * 8), kThreads, 0, s>>>(means, n, part, nbox, a, status);
+    k_morton<<<blocks_for(n, 8 * device_sm_count()), kThreads, 0, s>>>(means, n, part, nbox, a, status);
     const int nb = (n + kTileItems - 1) / kTileItems;
     for (int shift = 32; shift < 64; shift += 8) {  // the 30 code bits; ties keep index order
         k_radix_hist<<<nb, kThreads, 0, s>>>(a, n, shift, hist, nb, status);
@@ -317,7 +317,7 @@ cudaError_t launch_spatial_order(const float *means, int n, uint32_t *perm, void
         a = b;
         b = t;
     }
-    k_keys_to_perm<<<blocks_for(n, 148 * 8), kThreads, 0, s>>>(a, n, perm, status);
+    k_keys_to_perm<<<blocks_for(n, 8 * device_sm_count()), kThreads, 0, s>>>(a, n, perm, status);
     return cudaGetLastError();
 }
 
