@@ -112,6 +112,14 @@ def _args():
     p.add_argument("--unfused", action="store_true", help="forward and backward as two launches per iteration")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-iters", type=int, default=0, help="oracle iterations for the CPU baseline (0 = auto)")
+    p.add_argument("--batch", type=int, default=0, choices=(0, 256, 512),
+                   help="mapping/uneven: list entries staged per CTA batch (0 = 512)")
+    p.add_argument("--sched", choices=("auto", "tile", "persistent"), default="auto",
+                   help="mapping/uneven: one CTA per tile or persistent CTAs (auto: the autotuner's pick for "
+                        "uneven, per tile for mapping)")
+    p.add_argument("--no-graph", action="store_true", help="mapping/uneven: launch the step eagerly")
+    p.add_argument("--storage", choices=("16bit", "fp32"), default="16bit",
+                   help="precision: the Gaussians in 16-bit storage or in plain FP32")
     return p.parse_args()
 
 
@@ -459,19 +467,41 @@ def run_ours(a):
 
 
 # ---------------------------------------------------------------- batches
+def _oracle_frame_grad_rate(scene, cam, T, tc, td, loss_w, frames=1):
+    """The oracle's FULL gradient (forward + analytic adjoint to every
+    parameter and the pose) of one frame, timed on this host's cores."""
+    import numpy as np
+
+    import oracle
+    L = oracle.LossSpec(loss_w["w_color"], loss_w["w_depth"], loss_w.get("w_unc", 0.0), 0.0, 0.0,
+                        np.asarray(tc, np.float64), np.asarray(td, np.float64), w_align=loss_w.get("w_align", 0.0))
+    t0 = time.perf_counter()
+    for _ in range(frames):
+        oracle.grad(scene, cam, T, L)
+    return frames / (time.perf_counter() - t0), oracle.threads()
+
+
 def run_batch(a):
     """Mapping window (8 keyframes) or uneven batch (16 mixed frames): one step =
-    project + bin + forward + FULL backward (fused loss) over the whole batch."""
+    project + bin + forward + FULL backward (fused loss) over the whole batch,
+    captured once in a CUDA graph and replayed (--no-graph: launched eagerly).
+    Mapping under torchrun shards the window by keyframe: every rank steps its
+    own frames and one NCCL all-reduce sums the parameter gradients (fixed
+    8-frame window: strong scaling)."""
     import numpy as np
     import torch
 
     import synth
-    from paper_2403_16095_b300 import Gaussians, Rasterizer, autotune_tile
+    from paper_2403_16095_b300 import Gaussians, Rasterizer, autotune
     from paper_2403_16095_b300 import _abi as A
     from paper_2403_16095_b300.build import build
+    from paper_2403_16095_b300.shard import ShardedWindow, allreduce_gaussian_grads
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
     build()
     w = synth.workload(a.workload)
     sc, cams, poses = w["scene"], w["cams"], w["poses"]
@@ -491,56 +521,98 @@ def run_batch(a):
     g = Gaussians(*(torch.from_numpy(pert[k]).to(dev) for k in names))
     # the mapping weights of Sec. 4 (Replica): omega_1 colour 0.7, omega_3 geo 0.25,
     # omega_4 align 0.25, omega_6 var 0.15 (SSIM and L_iso are off the rasterizer)
-    loss = dict(w_color=0.7, w_depth=0.25, w_unc=0.15, w_align=0.25, target_color=tcol, target_depth=tdep)
-    tile, tune = a.tile, None
-    if a.workload == "uneven":
-        tile, tune = autotune_tile(cams, g, Tt, tdep, mode=A.GS_MODE_FULL, loss=loss)
-    r = Rasterizer(cams, g.n, tile=tile, mode=A.GS_MODE_FULL)
-    r.render(g, Tt, tdep)
-    r.set_capacity(int(r.read_status()[1] * 1.25) + 4096)
+    loss_w = dict(w_color=0.7, w_depth=0.25, w_unc=0.15, w_align=0.25)
+    loss = dict(loss_w, target_color=tcol, target_depth=tdep)
+    sched_of = {"tile": A.GS_SCHED_TILE, "persistent": A.GS_SCHED_PERSISTENT}
+    tile, batch, sched, tune = a.tile, a.batch, sched_of.get(a.sched, A.GS_SCHED_TILE), None
+    if a.workload == "uneven" and a.sched == "auto":
+        (tile, batch, sched), times = autotune(cams, g, Tt, tdep, mode=A.GS_MODE_FULL, loss=loss)
+        tune = {f"tile{t}/batch{b}/{'persistent' if s_ else 'per-tile'}": ms for (t, b, s_), ms in times.items()}
+    elif a.sched == "auto":
+        sched = A.GS_SCHED_TILE
     grads = {k: torch.empty_like(getattr(g, k)) for k in names}
+    if a.workload == "mapping":
+        sw = ShardedWindow(cams, g.n, Tt, tcol, tdep, rank=rank, world=ws, tile=tile, loss_weights=loss_w,
+                           batch=batch, sched=sched)
+        sw.prepare(g)
+        r, my_cams, my_T, my_loss, my_dep = sw.rast, sw.cams, sw.T_cw, sw.loss, sw.target_depth
+    else:
+        r = Rasterizer(cams, g.n, tile=tile, mode=A.GS_MODE_FULL, batch=batch, sched=sched)
+        r.render(g, Tt, tdep)
+        r.set_capacity(int(r.read_status()[1] * 1.25) + 4096)
+        my_cams, my_T, my_loss, my_dep = cams, Tt, loss, tdep
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     # separate projection and binning calls: on multi-frame batches the count
     # kernel (8 records per thread) beats counting inside the projection
     stages = ("project", "bin", "forward", "backward")
 
-    def step():
+    def eager_step():
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
         ev[0].record()
-        r.project(g, Tt)
+        r.project(g, my_T)
         ev[1].record()
         r.bin()
         ev[2].record()
-        r.forward(tdep)
+        r.forward(my_dep)
         ev[3].record()
-        r.backward(obs_depth=tdep, loss=loss, g=g, T_cw=Tt, grads=grads)
+        r.backward(obs_depth=my_dep, loss=my_loss, g=g, T_cw=my_T, grads=grads)
         ev[4].record()
         return ev
 
     for _ in range(a.warmup):
         flush.zero_()
-        step()
+        eager_step()
     torch.cuda.synchronize()
     assert r.read_status()[0] == 0
-    clocks = ClockSampler(local)
-    torch.cuda.synchronize()
-    clocks.start()
+    # per-stage times and the work counts from eager steps (outside the timed line)
     per = {s_: [] for s_ in stages}
-    tot = []
     contrib = []
-    for _ in range(a.steps):
+    for _ in range(min(a.steps, 5)):
         flush.zero_()
-        ev = step()
+        ev = eager_step()
         ev[-1].synchronize()
         for i, s_ in enumerate(stages):
             per[s_].append(ev[i].elapsed_time(ev[i + 1]))
-        tot.append(ev[0].elapsed_time(ev[-1]))
         contrib.append(int(r.img["n_contrib"].sum()))
+    eager_ms = statistics.mean(sum(per[s_][k] for s_ in stages) for k in range(len(per["project"])))
+    graph = None if a.no_graph else r.capture_step(g, my_T, my_dep, my_loss, grads)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    tot = []
+    for _ in range(a.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        if graph is not None:
+            graph.replay()
+        else:
+            eager_step()
+        if ws > 1:
+            allreduce_gaussian_grads(grads, names)
+        e1.record()
+        e1.synchronize()
+        tot.append(e0.elapsed_time(e1))
+    barrier()
     clk = clocks.stop()
     if r.read_status()[0] != 0:
         raise RuntimeError("device status set during the timed region")
     total_ms = sum(tot)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t)
     value = F * a.steps / (total_ms / 1e3)
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
     peaks = _peaks()
     mhz = peaks.get("sm_max_mhz", 2032.0)
     fp32_peak, _ = _fp32_peak(dev, mhz)
@@ -550,26 +622,49 @@ def run_batch(a):
     n_pix = sum(int(c.width) * int(c.height) for c in cams)
     metric = {"mapping": "mapping keyframe-iterations/sec (fwd+FULL bwd), 8x640x480 window, 1M Gaussians",
               "uneven": "frames/sec (fwd+FULL bwd), 16 mixed-resolution frames in one batch, 2M Gaussians"}[a.workload]
-    line = {"metric": metric, "value": value, "unit": "frames/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
-            "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+    cpu = None
+    if not a.no_cpu_baseline:
+        # the oracle's FULL gradient of one frame of the batch (the first 640x480 one)
+        f0 = next(f for f, c in enumerate(cams) if int(c.width) == 640)
+        off = sum(int(c.width) * int(c.height) for c in cams[:f0])
+        hw = int(cams[f0].width) * int(cams[f0].height)
+        tc0 = tcol[3 * off: 3 * (off + hw)].view(3, int(cams[f0].height), int(cams[f0].width)).cpu().numpy()
+        td0 = tdep[off: off + hw].view(int(cams[f0].height), int(cams[f0].width)).cpu().numpy()
+        sc_p = synth.Scene(*(pert[k] for k in names))
+        rate, cores = _oracle_frame_grad_rate(sc_p, cams[f0], np.asarray(poses[f0], np.float64), tc0, td0, loss_w)
+        cpu = {"value": rate, "unit": "frames/s", "cores": cores, "kind": "oracle",
+               "sample": f"the FP64 oracle's forward + analytic FULL gradient of frame {f0} (640x480) of the batch, "
+                         f"{g.n // 1000}k Gaussians, one frame"}
+    sched_name = "persistent" if sched == A.GS_SCHED_PERSISTENT else "per-tile"
+    line = {"metric": metric, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+            "scaling": "strong" if a.workload == "mapping" else "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{a.workload}-{F}frames-{g.n // 1000}k", "frames": F, "pixels": n_pix,
-                       "gaussians": int(g.n), "tile": tile, "autotune_ms": tune,
-                       "l2": "flushed between steps (512 MB write, untimed)",
-                       "stage_ms": {s_: statistics.mean(v) for s_, v in per.items()},
+                       "gaussians": int(g.n), "tile": tile, "batch": batch or 512, "sched": sched_name,
+                       "launch": "CUDA graph replay" if graph is not None else "eager",
+                       "parallelism": f"keyframe shards x{ws}" if a.workload == "mapping" else "single batch",
+                       "autotune_ms": tune, "l2": "flushed between steps (512 MB write, untimed)",
+                       "stage_ms_eager": {s_: statistics.mean(v) for s_, v in per.items()},
+                       "eager_ms_per_step": eager_ms,
                        "pairs": int(r.read_status()[1]), "contributions": E},
             "roofline": {"kernel": f"k_render_bwd<{tile},FULL> + k_project_bwd", "bound": "alu",
                          "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                          "traffic": None, "flop_per_contribution": BWD_FULL_FLOP_PER_CONTRIB,
                          "avg_launch_ms": bwd_ms},
             # projection, 5 binning kernels, forward, FULL backward, projection adjoint
-            "cpu_baseline": None, "gpu_launches": 9 * a.steps, "clocks": clk}
+            "cpu_baseline": cpu, "gpu_launches": 9 * a.steps, "clocks": clk}
     print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
 
 
 def run_precision(a):
-    """Tracking at 1200x680 on 5M Gaussians in 16-bit storage (BF16 attributes,
-    per-chunk fixed-point means), 30 iterations per frame in a CUDA graph."""
+    """Tracking at 1200x680 on 5M Gaussians, 30 iterations per frame in a CUDA
+    graph, over the workload's 100 seeded frames (--steps 100 covers them all),
+    with the Gaussians in 16-bit storage (BF16 attributes, per-chunk fixed-point
+    means; --storage 16bit) or in plain FP32 (--storage fp32), so that the two
+    forms are measured on the same GPU at the same shape."""
     import numpy as np
     import torch
 
@@ -585,51 +680,87 @@ def run_precision(a):
     sc, cam, poses = w["scene"], w["cams"][0], w["poses"]
     names = ("means", "log_scales", "quats", "opacity_logit", "colors", "nu")
     g32 = Gaussians(*(torch.from_numpy(np.ascontiguousarray(getattr(sc, k), np.float32)).to(dev) for k in names))
-    pk = pack_bf16(g32, spatial=True)
+    packed = a.storage == "16bit"
+    gt = pack_bf16(g32, spatial=True) if packed else g32
     frames = list(range(a.warmup + a.steps))
+    n_pose = len(poses)
+    # targets: the FP32 field rendered at the true poses (device-resident inputs)
     r0 = Rasterizer([cam], g32.n, tile=a.tile, mode=A.GS_MODE_FWD)
     tcol, tdep = {}, {}
-    for f in frames:
-        r0.render(g32, torch.from_numpy(np.asarray(poses[f % len(poses)], np.float32)).to(dev).reshape(-1))
+    for f in sorted(set(f % n_pose for f in frames)):
+        r0.render(g32, torch.from_numpy(np.asarray(poses[f], np.float32)).to(dev).reshape(-1))
         tcol[f], tdep[f] = r0.img["color"].clone(), r0.img["depth"].clone()
-    del r0, g32
-    starts = {f: torch.from_numpy(synth.jitter_pose(poses[f % len(poses)], seed=1005 * 100 + f)).to(dev)
-              for f in frames}
-    tr = Tracker(pk, cam, tile=a.tile, iters=ITERS, graph=True, timing=True, timing_every=TIMING_EVERY)
+    del r0
+    starts = {f: torch.from_numpy(synth.jitter_pose(poses[f], seed=1005 * 100 + f)).to(dev)
+              for f in sorted(set(f % n_pose for f in frames))}
+    tr = Tracker(gt, cam, tile=a.tile, iters=ITERS, graph=True, timing=True, timing_every=TIMING_EVERY)
     tr.prepare(tcol[0], tdep[0], starts[0], headroom=1.6)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     for f in frames[:a.warmup]:
         flush.zero_()
-        tr.set_frame(tcol[f], tdep[f], starts[f])
+        tr.set_frame(tcol[f % n_pose], tdep[f % n_pose], starts[f % n_pose])
         tr.run()
     torch.cuda.synchronize()
+    r_cnt = Rasterizer([cam], g32.n, tile=a.tile, mode=A.GS_MODE_FWD)
     clocks = ClockSampler(local)
     clocks.start()
-    tot, bwd = [], []
-    for f in frames[a.warmup:]:
+    tot, bwd, contrib = [], [], []
+    for k, f in enumerate(frames[a.warmup:]):
         flush.zero_()
+        fp = f % n_pose
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        tr.set_frame(tcol[f], tdep[f], starts[f])
+        tr.set_frame(tcol[fp], tdep[fp], starts[fp])
         tr.run()
         e1.record()
         e1.synchronize()
         tot.append(e0.elapsed_time(e1))
         bwd.extend(tr.backward_ms())
+        if tr.rast.read_status()[0] != 0:
+            raise RuntimeError("device status set during the timed region")
+        if k % 10 == 0:  # blended entries at the final pose, outside the timed region
+            r_cnt.render(gt, tr.T_cw)
+            contrib.append(int(r_cnt.img["n_contrib"].sum()))
     clk = clocks.stop()
-    if tr.rast.read_status()[0] != 0:
-        raise RuntimeError("device status set during the timed region")
     total_ms = sum(tot)
-    line = {"metric": "tracking iters/sec (fwd+pose-bwd) at 1200x680/5M Gaussians, 16-bit storage",
+    peaks = _peaks()
+    mhz = peaks.get("sm_max_mhz", 2032.0)
+    fp32_peak, n_sm = _fp32_peak(dev, mhz)
+    E = statistics.mean(contrib)
+    flop = FWD_FLOP_PER_CONTRIB + BWD_FLOP_PER_CONTRIB
+    launch_ms = statistics.mean(bwd)
+    dense = g32.n >= 800 * tr.rast.n_tiles
+    achieved = E * flop / (launch_ms * 1e-3) / 1e12
+    roof = {"kernel": f"k_render_fused_pose<{a.tile}, {4 if dense else 3}>", "bound": "alu", "achieved": achieved,
+            "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+            "peak_source": f"{n_sm} SMs (device query) x 128 FP32 lanes x 2 x {mhz:.0f} MHz (max SM clock)",
+            "flop_per_contribution": flop, "contributions_per_launch": E, "avg_launch_ms": launch_ms,
+            "launches": len(bwd)}
+    cpu = None
+    if not a.no_cpu_baseline:
+        import oracle
+        field = (oracle.unpack_bf16(gt.anchors.cpu().numpy(), gt.packed.cpu().numpy().view(np.uint16)) if packed
+                 else synth.Scene(*(np.asarray(getattr(sc, k), np.float32) for k in names)))
+        tc0 = tcol[0].view(3, cam.height, cam.width).cpu().numpy()
+        td0 = tdep[0].view(cam.height, cam.width).cpu().numpy()
+        n_it = a.cpu_iters or 1
+        secs, cores = cpu_oracle_iterations(field, cam, poses, [synth.jitter_pose(poses[0], seed=1005 * 100)], n_it,
+                                            (tc0, td0))
+        cpu = {"value": n_it / secs, "unit": "iters/s", "cores": cores, "kind": "oracle",
+               "sample": f"{n_it} FP64 oracle tracking iteration(s) (forward + analytic pose gradient + Adam) on "
+                         f"frame 0, 1200x680, 5M Gaussians ({'decoded 16-bit' if packed else 'FP32'} field)"}
+    form = "16-bit storage" if packed else "FP32 storage"
+    line = {"metric": f"tracking iters/sec (fwd+pose-bwd) at 1200x680/5M Gaussians, {form}",
             "value": ITERS * a.steps / (total_ms / 1e3), "unit": "iters/s", "n_gpus": 1, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16 storage, f32 compute", "data": "synthetic",
-            "config": {"workload": "precision-1200x680-5M-room", "gaussians": int(pk.n), "tile": a.tile,
-                       "iters_per_frame": ITERS, "l2": "flushed between steps (512 MB write, untimed)",
-                       "bwd_ms_avg": statistics.mean(bwd), "ms_per_iteration": total_ms / (a.steps * ITERS),
+            "vs_baseline": None, "dtype": "bf16 storage, f32 compute" if packed else "f32", "data": "synthetic",
+            "config": {"workload": f"precision-1200x680-5M-room-{a.storage}", "gaussians": int(g32.n),
+                       "tile": a.tile, "iters_per_frame": ITERS, "frames": len(set(f % n_pose for f in frames[a.warmup:])),
+                       "l2": "flushed between steps (512 MB write, untimed)",
+                       "ms_per_iteration": total_ms / (a.steps * ITERS),
                        "pairs_per_iteration": int(tr.rast.read_status()[1])},
-            "cpu_baseline": None, "gpu_launches": tr.kernel_launches_per_iteration() * ITERS * a.steps,
-            "clocks": clk}
+            "roofline": roof, "cpu_baseline": cpu,
+            "gpu_launches": tr.kernel_launches_per_iteration() * ITERS * a.steps, "clocks": clk}
     print(json.dumps(line), flush=True)
 
 

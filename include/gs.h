@@ -61,7 +61,7 @@ extern "C" {
 #endif
 
 #define GS_MAX_FRAMES 64
-#define GS_ABI_VERSION 8
+#define GS_ABI_VERSION 9
 
 typedef struct CUstream_st *gs_stream; /* a cudaStream_t; NULL = legacy default stream */
 
@@ -94,6 +94,8 @@ typedef struct {
     const float *nu;            /* [n]    per-Gaussian uncertainty (Eq. 13)     */
 } gs_gaussians;
 
+enum { GS_SCHED_TILE = 0, GS_SCHED_PERSISTENT = 1 };
+
 typedef struct {
     int tile;        /* tile edge in pixels: 8, 16 or 32                         */
     int mode;        /* GS_MODE_FWD / GS_MODE_POSE / GS_MODE_FULL                 */
@@ -101,6 +103,17 @@ typedef struct {
                         field of view (1.3 typical); <= 0 disables the clamp       */
     float nu_cull;   /* > 0: Gaussians with nu > nu_cull are culled (Sec. 3.2);
                         <= 0: off                                                  */
+    int batch;       /* list entries gs_render_fwd and the FULL-mode gs_render_bwd
+                        stage in shared memory per batch at 16x16 and 32x32 tiles:
+                        256 or 512 (0 = 512); 8x8 tiles stage 64. Speed only: the
+                        results do not depend on it                                */
+    int sched;       /* GS_SCHED_TILE: one CTA per tile, heaviest tiles first;
+                        GS_SCHED_PERSISTENT: gs_render_fwd and the FULL-mode
+                        gs_render_bwd run as many CTAs as fit on the GPU, each
+                        pulling (frame, tile) items in launch order from the device
+                        work queue tiles->queue (required then). Speed only; the
+                        POSE-mode backward and the tracking pass always run one CTA
+                        per tile                                                   */
 } gs_opts;
 
 /* Projected records (output of gs_project), device, caller-allocated.
@@ -135,6 +148,13 @@ typedef struct {
                              bucket unspecified). gs_bin_tiles writes it;
                              gs_render_fwd / gs_render_bwd then start the
                              heaviest tiles first. Results do not depend on it. */
+    uint32_t *queue;      /* NULL, or [2] device counters of the persistent
+                             blend kernels (opts->sched = GS_SCHED_PERSISTENT):
+                             zero-filled by the caller before first use; every
+                             persistent launch leaves them at zero again. A
+                             persistent launch owns them until it completes, so
+                             two launches sharing one queue must be ordered on
+                             one stream. No kernel waits on another CTA.        */
 } gs_tiles;
 
 /* Rendered channels (Eq. 3-10), device, FP32 except n_last. A NULL member is not
@@ -289,7 +309,9 @@ gs_status gs_project_bin_bf16(const gs_gaussians_bf16 *g, int n_frames, const gs
  * until exit. Limits: tiles->capacity <= GS_NOALLOC_MAX_PAIRS, else
  * GS_ERR_INVALID_ARG with a message. It allocates nothing. Its first call on a
  * device (with that device current) looks up the array's address; make that
- * first call before any stream capture. All calls share the array: calls that
+ * first call before any stream capture. After the device's context is
+ * destroyed (cudaDeviceReset), the next call is a first call again: it finds a
+ * new context current and looks the address up anew. All calls share the array: calls that
  * overlap on the GPU race; sequential calls are independent (every scratch word
  * is written before it is read). Outputs and errors as gs_bin_tiles.          */
 #define GS_NOALLOC_MAX_PAIRS (1 << 19)

@@ -14,7 +14,7 @@ import importlib
 _EXPORTS = {
     "GsError": "_abi", "Gaussians": "_abi", "PackedGaussians": "_abi", "pack_bf16": "_abi",
     "GaussianRasterize": "raster", "Rasterizer": "raster", "Tracker": "raster", "rasterize": "raster",
-    "autotune_tile": "raster",
+    "autotune_tile": "raster", "autotune": "raster",
 }
 
 __all__ = sorted(_EXPORTS)

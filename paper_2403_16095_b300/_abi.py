@@ -23,6 +23,7 @@ GS_REC_FLOATS = 16
 GS_JAC_FLOATS = 36
 GS_POSE_STATE_DOUBLES = 28
 GS_MODE_FWD, GS_MODE_POSE, GS_MODE_FULL = 0, 1, 2
+GS_SCHED_TILE, GS_SCHED_PERSISTENT = 0, 1
 GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_UNSUPPORTED = range(6)
 STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CAPACITY", 3: "GS_ERR_CUDA",
                 4: "GS_ERR_TIMEOUT", 5: "GS_ERR_UNSUPPORTED"}
@@ -50,7 +51,8 @@ class gs_gaussians(C.Structure):
 
 
 class gs_opts(C.Structure):
-    _fields_ = [("tile", C.c_int), ("mode", C.c_int), ("jclamp", C.c_float), ("nu_cull", C.c_float)]
+    _fields_ = [("tile", C.c_int), ("mode", C.c_int), ("jclamp", C.c_float), ("nu_cull", C.c_float),
+                ("batch", C.c_int), ("sched", C.c_int)]
 
 
 class gs_projected(C.Structure):
@@ -60,7 +62,7 @@ class gs_projected(C.Structure):
 
 class gs_tiles(C.Structure):
     _fields_ = [("capacity", C.c_int), ("n_tiles", C.c_int), ("values", _vp), ("keys", _vp), ("ranges", _vp),
-                ("order", _vp)]
+                ("order", _vp), ("queue", _vp)]
 
 
 class gs_image(C.Structure):
@@ -101,7 +103,7 @@ EXPORTS = ("gs_abi_version", "gs_last_error", "gs_project", "gs_bin_tiles_worksp
            "gs_pack_bf16", "gs_nu_accumulate", "gs_nu_finalize", "gs_pose_grad_reduce", "gs_pose_adam_step",
            "gs_project_bin", "gs_project_bin_bf16")
 GS_NOALLOC_MAX_PAIRS = 1 << 19
-ABI_VERSION = 8  # GS_ABI_VERSION of the gs.h these structures mirror
+ABI_VERSION = 9  # GS_ABI_VERSION of the gs.h these structures mirror
 
 
 def _load():
@@ -373,11 +375,12 @@ def _image(img: dict) -> gs_image:
 
 def gs_render_fwd(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tensor, values: torch.Tensor,
                   ranges: torch.Tensor, obs_depth: Optional[torch.Tensor], out: dict, status: torch.Tensor,
-                  stream=None, order: Optional[torch.Tensor] = None) -> None:
+                  stream=None, order: Optional[torch.Tensor] = None, queue: Optional[torch.Tensor] = None) -> None:
     F = len(cams)
     proj = gs_projected(n_gaussians, F, _ptr(rec, torch.float32, "rec"), 1, None)  # touched unused
     tiles = gs_tiles(values.numel(), ranges.numel() // 2, _ptr(values, torch.int32), None,
-                     _ptr(ranges, torch.int32), _ptr(order, torch.int32, "order", ranges.numel() // 2))
+                     _ptr(ranges, torch.int32), _ptr(order, torch.int32, "order", ranges.numel() // 2),
+                     _ptr(queue, torch.int32, "queue", 2))
     _check(lib.gs_render_fwd(C.byref(proj), C.byref(tiles), F, cameras(cams),
                              _ptr(obs_depth, torch.float32, "obs_depth"), C.byref(opts), C.byref(_image(out)),
                              _ptr(status, torch.int32, "status", 4), _stream(stream)))
@@ -395,12 +398,14 @@ def gs_render_bwd(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tensor, pose
                   values: torch.Tensor, ranges: torch.Tensor, T_cw: Optional[torch.Tensor], g: Optional[Gaussians],
                   obs_depth: Optional[torch.Tensor], fwd: dict, dL: Optional[dict], loss: Optional[dict],
                   grads: Optional[dict], pose_partials: torch.Tensor, pose_grad: Optional[torch.Tensor],
-                  status: torch.Tensor, ws: torch.Tensor, stream=None, order: Optional[torch.Tensor] = None) -> None:
+                  status: torch.Tensor, ws: torch.Tensor, stream=None, order: Optional[torch.Tensor] = None,
+                  queue: Optional[torch.Tensor] = None) -> None:
     F = len(cams)
     proj = gs_projected(n_gaussians, F, _ptr(rec, torch.float32, "rec"), 1,
                         _ptr(pose_jac, torch.float32, "pose_jac"))
     tiles = gs_tiles(values.numel(), ranges.numel() // 2, _ptr(values, torch.int32), None,
-                     _ptr(ranges, torch.int32), _ptr(order, torch.int32, "order", ranges.numel() // 2))
+                     _ptr(ranges, torch.int32), _ptr(order, torch.int32, "order", ranges.numel() // 2),
+                     _ptr(queue, torch.int32, "queue", 2))
     gl = None
     if loss is not None:
         gl = gs_loss(float(loss.get("w_color", 0.0)), float(loss.get("w_depth", 0.0)), float(loss.get("w_unc", 0.0)),

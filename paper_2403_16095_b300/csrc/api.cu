@@ -62,6 +62,20 @@ gs_status check_opts(const gs_opts *o) {
     if (!o) return fail(GS_ERR_INVALID_ARG, "opts is NULL");
     if (o->mode != GS_MODE_FWD && o->mode != GS_MODE_POSE && o->mode != GS_MODE_FULL)
         return fail(GS_ERR_INVALID_ARG, "mode=%d unknown", o->mode);
+    if (o->batch != 0 && o->batch != 256 && o->batch != 512)
+        return fail(GS_ERR_INVALID_ARG, "batch=%d not in {0, 256, 512}", o->batch);
+    if (o->sched != GS_SCHED_TILE && o->sched != GS_SCHED_PERSISTENT)
+        return fail(GS_ERR_INVALID_ARG, "sched=%d unknown", o->sched);
+    return GS_OK;
+}
+
+// The work queue of a persistent launch (NULL: one CTA per tile).
+gs_status sched_queue(const gs_opts *o, const gs_tiles *t, unsigned **queue) {
+    *queue = nullptr;
+    if (o->sched != GS_SCHED_PERSISTENT) return GS_OK;
+    if (!t->queue || !aligned(t->queue, 4))
+        return fail(GS_ERR_INVALID_ARG, "GS_SCHED_PERSISTENT needs tiles.queue (2 x uint32, zero-filled once)");
+    *queue = t->queue;
     return GS_OK;
 }
 
@@ -310,8 +324,10 @@ gs_status gs_render_fwd(const gs_projected *proj, const gs_tiles *tiles, int n_f
         return fail(GS_ERR_INVALID_ARG, "dom_pos and dom_weight go together");
     gs::ImagePtrs ip{out->color, out->depth, out->alpha, out->unc, out->nu_map, out->median, out->T_final, out->n_last,
                      out->n_contrib, out->median_pos, out->dom_pos, out->dom_weight};
+    unsigned *queue = nullptr;
+    GS_TRY(sched_queue(opts, tiles, &queue));
     return cuda_status(gs::launch_render_fwd(proj->rec, tiles->values, tiles->ranges, tiles->order, ft, obs_depth, ip,
-                                             status, stream),
+                                             status, opts->batch, queue, stream),
                        "gs_render_fwd");
 }
 
@@ -385,7 +401,7 @@ gs_status gs_render_bwd(const gs_projected *proj, const gs_tiles *tiles, int n_f
         return cuda_status(gs::launch_render_bwd(mode, proj->rec, proj->pose_jac, tiles->values, tiles->ranges,
                                                  tiles->order, ft,
                                                  obs_depth, ip, lp, nullptr, pose_partials, per_frame, pose_grad,
-                                                 counters, status, stream),
+                                                 counters, status, opts->batch, nullptr, stream),
                            "gs_render_bwd");
     }
     GS_TRY(check_gauss(g));
@@ -394,9 +410,11 @@ gs_status gs_render_bwd(const gs_projected *proj, const gs_tiles *tiles, int n_f
     float *grad2d = static_cast<float *>(ws);
     if ((e = cudaMemsetAsync(grad2d, 0, sizeof(float) * gs::kGrad2d * (size_t)M, stream)) != cudaSuccess)
         return cuda_status(e, "gs_render_bwd memset");
+    unsigned *queue = nullptr;
+    GS_TRY(sched_queue(opts, tiles, &queue));
     if ((e = gs::launch_render_bwd(mode, proj->rec, nullptr, tiles->values, tiles->ranges, tiles->order, ft, obs_depth,
-                                   ip, lp,
-                                   grad2d, pose_partials, per_frame, nullptr, nullptr, status, stream)) != cudaSuccess)
+                                   ip, lp, grad2d, pose_partials, per_frame, nullptr, nullptr, status, opts->batch,
+                                   queue, stream)) != cudaSuccess)
         return cuda_status(e, "gs_render_bwd");
     return cuda_status(gs::launch_project_bwd(gauss_ptrs(g), N, ft, T_cw, opts->jclamp, proj->rec, grad2d, *grads,
                                               pose_partials, per_frame, pose_grad, counters, status, stream),

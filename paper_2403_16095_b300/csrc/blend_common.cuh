@@ -72,4 +72,30 @@ __device__ __forceinline__ bool warp_block_may_hit(const float4 &a, const float4
     return !(qmin > kQMax + 1e-3f);  // NaN-safe: keep on doubt
 }
 
+// acc[c] += th[r] * J[6r + c] for the 6x6 pose Jacobian J of one record
+// (row-major [theta = mean2d.x, mean2d.y, A, B, C, z][xi = rho, phi], nine
+// float4 in shared memory), in element order. Each pair of neighbouring
+// columns (2m, 2m + 1) lies in one row, so the pairs are contracted with the
+// packed two-lane FP32 FMA of sm_100+ (fma.rn.f32x2): 18 instructions instead
+// of 36, each lane rounded exactly as fmaf, so the sums are the same bits.
+__device__ __forceinline__ void fma_x2(float &d0, float &d1, float a, float b0, float b1) {
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %2};\n\t"
+        "mov.b64 rb, {%3, %4};\n\t"
+        "mov.b64 rd, {%0, %1};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rd;\n\t"
+        "mov.b64 {%0, %1}, rd;\n\t}"
+        : "+f"(d0), "+f"(d1)
+        : "f"(a), "f"(b0), "f"(b1));
+}
+__device__ __forceinline__ void pose_contract(float (&acc)[6], const float (&th)[6], const float4 *J) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        const float4 jq = J[q];
+        const int e = 4 * q;  // elements e .. e + 3: two column pairs, each within row e / 6 resp. (e + 2) / 6
+        fma_x2(acc[e % 6], acc[(e + 1) % 6], th[e / 6], jq.x, jq.y);
+        fma_x2(acc[(e + 2) % 6], acc[(e + 3) % 6], th[(e + 2) / 6], jq.z, jq.w);
+    }
+}
+
 }  // namespace gs

@@ -120,15 +120,20 @@ cudaError_t launch_bin_tiles(const float *rec, const int *touched, int n_records
 // zeroes the tile counters and the binning's scalars (ws) ahead of a counting projection
 cudaError_t launch_bin_clear(uint32_t *ranges, const FrameTable &ft, int capacity, void *ws, cudaStream_t s);
 // render_fwd.cu
+// batch: list entries staged per batch at 16x16 and 32x32 tiles (256 or 512;
+// other values take 512); queue: NULL for one CTA per tile, else the two
+// counters of the persistent form (work_queue.cuh)
 cudaError_t launch_render_fwd(const float *rec, const uint32_t *values, const uint32_t *ranges, const uint32_t *order,
                               const FrameTable &ft, const float *obs_depth, const ImagePtrs &out,
-                              const int32_t *status, cudaStream_t s);
+                              const int32_t *status, int batch, unsigned *queue, cudaStream_t s);
 // render_bwd.cu
+// batch / queue as for launch_render_fwd, FULL mode only (POSE mode stages
+// 256 entries per batch and runs one CTA per tile)
 cudaError_t launch_render_bwd(int mode, const float *rec, const float *jac, const uint32_t *values,
                               const uint32_t *ranges, const uint32_t *order, const FrameTable &ft, const float *obs_depth,
                               const ImagePtrs &fwd, const LossParams &lp, float *grad2d, float *pose_partials,
                               int per_frame, double *pose_grad, unsigned *counters, const int32_t *status,
-                              cudaStream_t s);
+                              int batch, unsigned *queue, cudaStream_t s);
 // pack.cu
 size_t spatial_order_workspace_bytes(int n);
 cudaError_t launch_spatial_order(const float *means, int n, uint32_t *perm, void *ws, const int32_t *status,

@@ -10,9 +10,12 @@
 // below, which every GPU that loads libgs holds until the process exits.
 //
 // Set-up: the first call on each device (with that device current) looks up
-// the array's device address with cudaGetSymbolAddress and caches it; in host
-// code the array's name is only a host-side stand-in, never a device address.
-// Make that first call before any stream capture. All calls share the array
+// the array's device address with cudaGetSymbolAddress and caches it with the
+// device's current CUDA context; in host code the array's name is only a
+// host-side stand-in, never a device address. Make that first call before any
+// stream capture. A call that finds another context current (the old one was
+// destroyed, e.g. by cudaDeviceReset, and the module loaded again) looks the
+// address up again: it is again a first call. All calls share the array
 // and it keeps the last call's contents: the binning writes every scratch word
 // it reads later in the same call and clears its counters itself, so nothing
 // leaks from one call to the next; calls that overlap on the GPU (different
@@ -33,6 +36,26 @@ static __device__ __align__(256) unsigned char g_bin_scratch[kScratchBytes];
 
 std::mutex g_mu;
 void *g_scratch_addr[kMaxDevices] = {};
+void *g_scratch_ctx[kMaxDevices] = {};  // the context the cached address belongs to
+
+// The current CUDA context (cuCtxGetCurrent, resolved through the runtime's
+// driver entry points so that libgs links no driver library), or NULL.
+void *current_context() {
+    using Fn = int (*)(void **);
+    static Fn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {  // under g_mu
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<Fn>(p);
+    }
+    void *ctx = nullptr;
+    if (fn && fn(&ctx) != 0) ctx = nullptr;
+    return ctx;
+}
 
 gs_status na_fail(gs_status st, const char *msg) {
     char buf[256];
@@ -48,11 +71,13 @@ gs_status scratch_address(void **out) {
     if (e != cudaSuccess) return na_fail(GS_ERR_CUDA, cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return na_fail(GS_ERR_UNSUPPORTED, "device ordinal >= 64");
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
+    void *ctx = current_context();
+    if (!g_scratch_addr[dev] || ctx != g_scratch_ctx[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_bin_scratch);
         if (e != cudaSuccess || !p) return na_fail(GS_ERR_CUDA, cudaGetErrorString(e));
         g_scratch_addr[dev] = p;
+        g_scratch_ctx[dev] = current_context();  // the lookup may have made the context current
     }
     *out = g_scratch_addr[dev];
     return GS_OK;

@@ -17,12 +17,15 @@
 // tile reduces them in FP64 by warp shuffles and a fixed block tree into one
 // partial per tile (deterministic, no atomics).
 // FULL mode: the eleven per-entry gradients are reduced across the warp (only
-// when some lane contributed) and lane 0 adds them to the record's accumulators.
+// when some lane contributed) and lane 0 adds them to the record's accumulators;
+// it also has a persistent form (resident CTAs pulling tiles from a device work
+// queue) and a choice of 256 or 512 staged entries per batch.
 #include <atomic>
 
 #include "gs_internal.cuh"
 #include "blend_common.cuh"
 #include "dfloat.cuh"
+#include "work_queue.cuh"
 
 namespace gs {
 namespace {
@@ -34,14 +37,14 @@ __device__ __forceinline__ float sgnf(float v) { return v > 0.f ? 1.f : (v < 0.f
 // The last CTA of a frame reuses the same bytes for the pose reduction.
 constexpr int kFullBatch = 512;
 
-template <int TILE, int MODE>
+template <int TILE, int MODE, int FULL_BATCH = kFullBatch>
 struct BwdSmem {
     static constexpr int NT = TILE * TILE;
     static constexpr bool POSE = MODE == GS_MODE_POSE;
-    // FULL mode stages 512 entries per batch (68 B each): half the CTA barriers
-    // of 256, which bound the kernel's warps (they wait for the tile's busiest
-    // warp at every batch)
-    static constexpr int BATCH = NT < 256 ? NT : (POSE ? 256 : kFullBatch);
+    // FULL mode stages 512 entries per batch by default (68 B each): half the
+    // CTA barriers of 256, which bound the kernel's warps (they wait for the
+    // tile's busiest warp at every batch); 256 is the other choice offered
+    static constexpr int BATCH = NT < 256 ? NT : (POSE ? 256 : FULL_BATCH);
     static constexpr size_t kEntry = 4 * sizeof(float4) + sizeof(uint32_t) + (POSE ? 9 * sizeof(float4) : 0);
     static constexpr size_t kStage = BATCH * kEntry;
     static constexpr size_t kRed = POSE ? sizeof(df) * kRedSlots * 6 : 0;
@@ -58,23 +61,33 @@ struct BwdSmem {
 constexpr int kDirectLanes = 20;
 
 // CD: the loss touches only colour and depth (the tracking loss), so the
-// opacity, U and nu terms of every contribution are compiled out. FULL mode at
-// 16x16 is held to 48 registers (5 CTAs per SM, no spills): the kernel is bound
-// by instruction issue and the per-entry warp reductions, and the fifth CTA
-// hides their latency (2.70 -> 2.60 ms on an 8-frame 640x480 window).
-template <int TILE, int MODE, bool CD>
-__global__ void __launch_bounds__(TILE *TILE, (TILE == 16 && MODE == GS_MODE_FULL) ? 5 : 1)
-    k_render_bwd(const float4 *__restrict__ rec, const float4 *__restrict__ jac, const uint32_t *__restrict__ values,
-                 const uint2 *__restrict__ ranges, const uint32_t *__restrict__ order, FrameTable ft,
-                 const float *__restrict__ obs_depth, ImagePtrs fwd,
-                 LossParams lp, float *__restrict__ grad2d, float *__restrict__ pose_partials, int per_frame,
-                 double *__restrict__ pose_grad, unsigned *__restrict__ counters, const int32_t *__restrict__ status) {
-    using SM = BwdSmem<TILE, MODE>;
+// opacity, U and nu terms of every contribution are compiled out.
+template <int TILE>
+struct BwdShared {  // the static shared state of a backward CTA
+    static constexpr int NWARP = TILE * TILE / 32 > 0 ? TILE * TILE / 32 : 1;
+    uint32_t wmax[NWARP];
+    df wdf[NWARP][6];
+    int flag;
+    int item[2];  // persistent form: the work-queue slots
+};
+
+// The backward of one tile. The per-tile CTA kernel and the persistent kernel
+// below run this same code, so their gradients agree up to the order of the
+// FULL-mode atomic additions.
+template <int TILE, int MODE, bool CD, int FULL_BATCH>
+__device__ __forceinline__ void bwd_tile(const int gtile, const float4 *__restrict__ rec,
+                                         const float4 *__restrict__ jac, const uint32_t *__restrict__ values,
+                                         const uint2 *__restrict__ ranges, const FrameTable &ft,
+                                         const float *__restrict__ obs_depth, const ImagePtrs &fwd,
+                                         const LossParams &lp, float *__restrict__ grad2d,
+                                         float *__restrict__ pose_partials, int per_frame,
+                                         double *__restrict__ pose_grad, unsigned *__restrict__ counters,
+                                         unsigned char *s_dyn, BwdShared<TILE> &sh) {
+    using SM = BwdSmem<TILE, MODE, FULL_BATCH>;
     constexpr int NT = SM::NT;
     constexpr bool POSE = SM::POSE;
     constexpr int BATCH = SM::BATCH;
     constexpr int NWARP = NT / 32 > 0 ? NT / 32 : 1;
-    extern __shared__ __align__(16) unsigned char s_dyn[];
     float4 *s_a = reinterpret_cast<float4 *>(s_dyn);
     float4 *s_b = s_a + BATCH;
     float4 *s_c = s_b + BATCH;
@@ -82,12 +95,8 @@ __global__ void __launch_bounds__(TILE *TILE, (TILE == 16 && MODE == GS_MODE_FUL
     float4 *s_j = reinterpret_cast<float4 *>(s_r + BATCH);                   // POSE only
     uint32_t *s_idx = reinterpret_cast<uint32_t *>(s_j + (POSE ? 9 * BATCH : 0));
     df(*s_red)[6] = reinterpret_cast<df(*)[6]>(s_dyn);                       // tail only
-    __shared__ uint32_t s_wmax[NWARP];
-    __shared__ df s_wdf[NWARP][6];
-    __shared__ int s_flag;
-    if (status[0] != 0) return;
+    uint32_t *s_wmax = sh.wmax;
 
-    const int gtile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;  // heaviest tiles first
     const int f = frame_of_tile(ft, gtile);
     const FrameDesc &fd = ft.f[f];
     const int lt = gtile - fd.tile_off;
@@ -232,16 +241,7 @@ __global__ void __launch_bounds__(TILE *TILE, (TILE == 16 && MODE == GS_MODE_FUL
             if (POSE) {
                 if (act) {
                     const float th[6] = {v[G_MX], v[G_MY], v[G_CA], v[G_CB], v[G_CC], v[G_Z]};
-                    const float4 *J = &s_j[k * 9];
-#pragma unroll
-                    for (int q = 0; q < 9; ++q) {
-                        const float4 jq = J[q];
-                        const int e = 4 * q;
-                        acc[(e + 0) % 6] = fmaf(th[(e + 0) / 6], jq.x, acc[(e + 0) % 6]);
-                        acc[(e + 1) % 6] = fmaf(th[(e + 1) / 6], jq.y, acc[(e + 1) % 6]);
-                        acc[(e + 2) % 6] = fmaf(th[(e + 2) / 6], jq.z, acc[(e + 2) % 6]);
-                        acc[(e + 3) % 6] = fmaf(th[(e + 3) / 6], jq.w, acc[(e + 3) % 6]);
-                    }
+                    pose_contract(acc, th, &s_j[k * 9]);
                 }
             } else {
                 const unsigned am = __ballot_sync(0xffffffffu, act);
@@ -287,51 +287,120 @@ __global__ void __launch_bounds__(TILE *TILE, (TILE == 16 && MODE == GS_MODE_FUL
         // per-tile partial (double-float, fixed tree), then the last tile of the
         // frame reduces all of the frame's partials into the FP64 pose gradient
         float *part_f = pose_partials + (size_t)f * per_frame * 12;
-        cta_pose_partial(acc, part_f + (size_t)lt * 12, s_wdf);
+        cta_pose_partial(acc, part_f + (size_t)lt * 12, sh.wdf);
         if (pose_grad)
             last_cta_pose_reduce(part_f, per_frame, fd.tiles_x * fd.tiles_y, counters + f, pose_grad + 6 * f, s_red,
-                                 &s_flag);
+                                 &sh.flag);
     }
 }
 
-// Raises the dynamic shared-memory limit of one kernel instance once per
-// device (a host-side attribute; the first call happens outside any capture).
-template <int TILE, int MODE, bool CD>
-cudaError_t launch_variant(const float4 *rec, const float4 *jac, const uint32_t *values, const uint2 *ranges,
-                           const uint32_t *order, const FrameTable &ft, const float *obs_depth, const ImagePtrs &fwd, const LossParams &lp,
-                           float *grad2d, float *pp, int per_frame, double *pg, unsigned *cnt, const int32_t *status,
-                           cudaStream_t s) {
-    // raise the dynamic shared-memory limit once per device (a host-side
-    // attribute; the first call happens outside any stream capture)
+// One CTA per tile, heaviest tiles first when the launch order is given.
+// FULL mode at 16x16 is held to 48 registers (5 CTAs per SM, no spills): the
+// kernel is bound by instruction issue and the per-entry warp reductions, and
+// the fifth CTA hides their latency (2.70 -> 2.60 ms on an 8-frame 640x480
+// window).
+template <int TILE, int MODE, bool CD, int FULL_BATCH>
+__global__ void __launch_bounds__(TILE *TILE, (TILE == 16 && MODE == GS_MODE_FULL) ? 5 : 1)
+    k_render_bwd(const float4 *__restrict__ rec, const float4 *__restrict__ jac, const uint32_t *__restrict__ values,
+                 const uint2 *__restrict__ ranges, const uint32_t *__restrict__ order, FrameTable ft,
+                 const float *__restrict__ obs_depth, ImagePtrs fwd,
+                 LossParams lp, float *__restrict__ grad2d, float *__restrict__ pose_partials, int per_frame,
+                 double *__restrict__ pose_grad, unsigned *__restrict__ counters, const int32_t *__restrict__ status) {
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    __shared__ BwdShared<TILE> sh;
+    if (status[0] != 0) return;
+    const int gtile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
+    bwd_tile<TILE, MODE, CD, FULL_BATCH>(gtile, rec, jac, values, ranges, ft, obs_depth, fwd, lp, grad2d,
+                                         pose_partials, per_frame, pose_grad, counters, s_dyn, sh);
+}
+
+// Persistent form of the FULL-mode backward: as many CTAs as fit on the GPU,
+// each pulling the next (frame, tile) item in launch order from the device
+// work queue (work_queue.cuh). FULL mode only: its per-record accumulators take
+// atomic adds in any order, so no tile waits for another.
+template <int TILE, bool CD, int FULL_BATCH>
+__global__ void __launch_bounds__(TILE *TILE, TILE == 16 ? 5 : 1)
+    k_render_bwd_persist(const float4 *__restrict__ rec, const uint32_t *__restrict__ values,
+                         const uint2 *__restrict__ ranges, const uint32_t *__restrict__ order, FrameTable ft,
+                         const float *__restrict__ obs_depth, ImagePtrs fwd, LossParams lp,
+                         float *__restrict__ grad2d, const int32_t *__restrict__ status, unsigned *__restrict__ queue) {
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    __shared__ BwdShared<TILE> sh;
+    if (status[0] != 0) return;
+    for (int it = 0;; ++it) {
+        const int item = queue_next(queue, sh.item, it);
+        if (item >= ft.total_tiles) break;
+        const int gtile = order ? (int)order[item] : item;
+        bwd_tile<TILE, GS_MODE_FULL, CD, FULL_BATCH>(gtile, rec, nullptr, values, ranges, ft, obs_depth, fwd, lp,
+                                                     grad2d, nullptr, 0, nullptr, nullptr, s_dyn, sh);
+    }
+    queue_exit(queue);
+}
+
+// Raises the dynamic shared-memory limit of one kernel once per device (a
+// host-side attribute; the first call happens outside any stream capture).
+template <auto KERNEL>
+cudaError_t set_smem_once(size_t smem) {
     static std::atomic<uint64_t> done{0};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    constexpr size_t smem = BwdSmem<TILE, MODE>::bytes;
     if (dev >= 64 || !((done.load() >> dev) & 1)) {
-        e = cudaFuncSetAttribute(k_render_bwd<TILE, MODE, CD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         if (dev < 64) done.fetch_or(1ull << dev);
     }
-    k_render_bwd<TILE, MODE, CD><<<ft.total_tiles, TILE * TILE, smem, s>>>(rec, jac, values, ranges, order, ft, obs_depth, fwd,
-                                                                           lp, grad2d, pp, per_frame, pg, cnt, status);
+    return cudaSuccess;
+}
+
+template <int TILE, int MODE, bool CD, int FULL_BATCH>
+cudaError_t launch_variant(const float4 *rec, const float4 *jac, const uint32_t *values, const uint2 *ranges,
+                           const uint32_t *order, const FrameTable &ft, const float *obs_depth, const ImagePtrs &fwd, const LossParams &lp,
+                           float *grad2d, float *pp, int per_frame, double *pg, unsigned *cnt, const int32_t *status,
+                           unsigned *queue, cudaStream_t s) {
+    constexpr size_t smem = BwdSmem<TILE, MODE, FULL_BATCH>::bytes;
+    cudaError_t e;
+    if (MODE == GS_MODE_FULL && queue) {
+        constexpr auto kern = k_render_bwd_persist<TILE, CD, FULL_BATCH>;
+        if ((e = set_smem_once<kern>(smem)) != cudaSuccess) return e;
+        int grid = 0;
+        if ((e = persistent_grid<kern>(TILE * TILE, smem, ft.total_tiles, &grid)) != cudaSuccess) return e;
+        kern<<<grid, TILE * TILE, smem, s>>>(rec, values, ranges, order, ft, obs_depth, fwd, lp, grad2d, status, queue);
+        return cudaGetLastError();
+    }
+    constexpr auto kern = k_render_bwd<TILE, MODE, CD, FULL_BATCH>;
+    if ((e = set_smem_once<kern>(smem)) != cudaSuccess) return e;
+    kern<<<ft.total_tiles, TILE * TILE, smem, s>>>(rec, jac, values, ranges, order, ft, obs_depth, fwd, lp, grad2d, pp,
+                                                   per_frame, pg, cnt, status);
     return cudaGetLastError();
+}
+
+template <int TILE, int FULL_BATCH>
+cudaError_t launch_batch(int mode, bool cd, const float4 *rec, const float4 *jac, const uint32_t *values,
+                         const uint2 *ranges, const uint32_t *order, const FrameTable &ft, const float *obs_depth,
+                         const ImagePtrs &fwd, const LossParams &lp, float *grad2d, float *pp, int per_frame,
+                         double *pg, unsigned *cnt, const int32_t *status, unsigned *queue, cudaStream_t s) {
+#define GS_BWD_ARGS rec, jac, values, ranges, order, ft, obs_depth, fwd, lp, grad2d, pp, per_frame, pg, cnt, status, queue, s
+    if (mode == GS_MODE_POSE)  // the POSE backward stages 256 entries (with their Jacobians) per batch
+        return cd ? launch_variant<TILE, GS_MODE_POSE, true, kFullBatch>(GS_BWD_ARGS)
+                  : launch_variant<TILE, GS_MODE_POSE, false, kFullBatch>(GS_BWD_ARGS);
+    return cd ? launch_variant<TILE, GS_MODE_FULL, true, FULL_BATCH>(GS_BWD_ARGS)
+              : launch_variant<TILE, GS_MODE_FULL, false, FULL_BATCH>(GS_BWD_ARGS);
+#undef GS_BWD_ARGS
 }
 
 template <int TILE>
 cudaError_t launch_tile(int mode, const float4 *rec, const float4 *jac, const uint32_t *values, const uint2 *ranges,
                         const uint32_t *order, const FrameTable &ft, const float *obs_depth, const ImagePtrs &fwd, const LossParams &lp,
                         float *grad2d, float *pp, int per_frame, double *pg, unsigned *cnt, const int32_t *status,
-                        cudaStream_t s) {
+                        int batch, unsigned *queue, cudaStream_t s) {
     const bool cd = lp.fused ? (lp.w_unc == 0.f && lp.w_nu == 0.f && lp.w_align == 0.f)
                              : (!lp.g_alpha && !lp.g_unc && !lp.g_nu && !lp.g_median);
-#define GS_BWD_ARGS rec, jac, values, ranges, order, ft, obs_depth, fwd, lp, grad2d, pp, per_frame, pg, cnt, status, s
-    if (mode == GS_MODE_POSE)
-        return cd ? launch_variant<TILE, GS_MODE_POSE, true>(GS_BWD_ARGS)
-                  : launch_variant<TILE, GS_MODE_POSE, false>(GS_BWD_ARGS);
-    return cd ? launch_variant<TILE, GS_MODE_FULL, true>(GS_BWD_ARGS)
-              : launch_variant<TILE, GS_MODE_FULL, false>(GS_BWD_ARGS);
-#undef GS_BWD_ARGS
+    if (mode == GS_MODE_FULL && TILE >= 16 && batch == 256)
+        return launch_batch<TILE, 256>(mode, cd, rec, jac, values, ranges, order, ft, obs_depth, fwd, lp, grad2d, pp,
+                                       per_frame, pg, cnt, status, queue, s);
+    return launch_batch<TILE, kFullBatch>(mode, cd, rec, jac, values, ranges, order, ft, obs_depth, fwd, lp, grad2d,
+                                          pp, per_frame, pg, cnt, status, queue, s);
 }
 
 }  // namespace
@@ -340,17 +409,19 @@ cudaError_t launch_render_bwd(int mode, const float *rec, const float *jac, cons
                               const uint32_t *ranges, const uint32_t *order, const FrameTable &ft, const float *obs_depth,
                               const ImagePtrs &fwd, const LossParams &lp, float *grad2d, float *pose_partials,
                               int per_frame, double *pose_grad, unsigned *counters, const int32_t *status,
-                              cudaStream_t s) {
+                              int batch, unsigned *queue, cudaStream_t s) {
     if (ft.total_tiles == 0) return cudaSuccess;
     const float4 *r4 = reinterpret_cast<const float4 *>(rec);
     const float4 *j4 = reinterpret_cast<const float4 *>(jac);
     const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
+#define GS_BWD_ARGS mode, r4, j4, values, rg, order, ft, obs_depth, fwd, lp, grad2d, pose_partials, per_frame, pose_grad, counters, status, batch, queue, s
     switch (ft.tile) {
-        case 8: return launch_tile<8>(mode, r4, j4, values, rg, order, ft, obs_depth, fwd, lp, grad2d, pose_partials, per_frame, pose_grad, counters, status, s);
-        case 16: return launch_tile<16>(mode, r4, j4, values, rg, order, ft, obs_depth, fwd, lp, grad2d, pose_partials, per_frame, pose_grad, counters, status, s);
-        case 32: return launch_tile<32>(mode, r4, j4, values, rg, order, ft, obs_depth, fwd, lp, grad2d, pose_partials, per_frame, pose_grad, counters, status, s);
+        case 8: return launch_tile<8>(GS_BWD_ARGS);
+        case 16: return launch_tile<16>(GS_BWD_ARGS);
+        case 32: return launch_tile<32>(GS_BWD_ARGS);
         default: return cudaErrorInvalidValue;
     }
+#undef GS_BWD_ARGS
 }
 
 }  // namespace gs

@@ -241,16 +241,7 @@ __global__ void __launch_bounds__(TILE *TILE, MINB)
                     const float th[6] = {dpow * (a.z * dx + a.w * dy), dpow * (a.w * dx + b.x * dy),
                                          -0.5f * dpow * dx * dx,       -dpow * dx * dy,
                                          -0.5f * dpow * dy * dy,       w * gD};
-                    const float4 *J = &s_j[k * 9];
-#pragma unroll
-                    for (int q = 0; q < 9; ++q) {
-                        const float4 jq = J[q];
-                        const int e = 4 * q;
-                        acc[(e + 0) % 6] = fmaf(th[(e + 0) / 6], jq.x, acc[(e + 0) % 6]);
-                        acc[(e + 1) % 6] = fmaf(th[(e + 1) / 6], jq.y, acc[(e + 1) % 6]);
-                        acc[(e + 2) % 6] = fmaf(th[(e + 2) / 6], jq.z, acc[(e + 2) % 6]);
-                        acc[(e + 3) % 6] = fmaf(th[(e + 3) / 6], jq.w, acc[(e + 3) % 6]);
-                    }
+                    pose_contract(acc, th, &s_j[k * 9]);
                 }
             }
         }

@@ -1,11 +1,14 @@
 // Front-to-back alpha blending of the depth-sorted tile lists (CG-SLAM Eq. 3-10).
 //
-// One CTA per tile (TILE x TILE pixels, one thread per pixel). Each warp owns an
-// 8x4 pixel block so that the warp-uniform rectangle test against a Gaussian's
-// pixel rect skips most non-overlapping list entries without divergence. The
-// tile's list is staged in shared memory in batches of up to 256 records; a
-// pixel stops when the next entry would take T below 1e-4, a warp skips a batch
-// once all of its pixels are done, and the CTA exits once every pixel is done.
+// One CTA per tile (TILE x TILE pixels, one thread per pixel), or, in the
+// persistent form, one resident CTA per slot of the GPU pulling tiles from a
+// device work queue. Each warp owns an 8x4 pixel block so that the
+// warp-uniform rectangle test against a Gaussian's pixel rect skips most
+// non-overlapping list entries without divergence. The tile's list is staged
+// in shared memory in batches (256 or 512 records at 16x16 and 32x32 tiles,
+// the whole CTA's 64 at 8x8); a pixel stops when the next entry would take T
+// below 1e-4, a warp skips a batch once all of its pixels are done, and the
+// tile ends once every pixel is done.
 //
 // The per-pixel arithmetic (q, G, alpha, T) is the same function as in the
 // backward pass, written with explicitly rounded operations, so both passes take
@@ -18,25 +21,22 @@
 // Separate instantiations, so each caller pays only for what it reads.
 #include "gs_internal.cuh"
 #include "blend_common.cuh"
+#include "work_queue.cuh"
 
 namespace gs {
 namespace {
 
-constexpr int kFwdBatch = 512;  // entries staged per batch at 16x16 and larger tiles (512: half the
-                                // CTA barriers of 256; mapping forward 1.20 -> 1.05 ms)
+constexpr int kFwdBatch = 512;  // default entries staged per batch at 16x16 and larger tiles (512: half
+                                // the CTA barriers of 256; mapping forward 1.20 -> 1.05 ms)
 
-template <int TILE, bool DOM, bool LITE>
-__global__ void __launch_bounds__(TILE *TILE, 1024 / (TILE * TILE))
-    k_render_fwd(const float4 *__restrict__ rec, const uint32_t *__restrict__ values,
-                 const uint2 *__restrict__ ranges, const uint32_t *__restrict__ order, FrameTable ft,
-                 const float *__restrict__ obs_depth, ImagePtrs out, const int32_t *__restrict__ status) {
+// The blend of one tile (one thread per pixel). The per-tile CTA kernel and the
+// persistent kernel below run this same code, so their images are identical.
+template <int TILE, bool DOM, bool LITE, int BATCH>
+__device__ __forceinline__ void fwd_tile(const int gtile, const float4 *__restrict__ rec,
+                                         const uint32_t *__restrict__ values, const uint2 *__restrict__ ranges,
+                                         const FrameTable &ft, const float *__restrict__ obs_depth,
+                                         const ImagePtrs &out, float4 *s_a, float4 *s_b, float4 *s_c, int4 *s_r) {
     constexpr int NT = TILE * TILE;
-    constexpr int BATCH = NT < 256 ? NT : kFwdBatch;
-    __shared__ float4 s_a[BATCH], s_b[BATCH], s_c[BATCH];
-    __shared__ int4 s_r[BATCH];
-    if (status[0] != 0) return;
-
-    const int gtile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;  // heaviest tiles first
     const int f = frame_of_tile(ft, gtile);
     const FrameDesc &fd = ft.f[f];
     const int lt = gtile - fd.tile_off;
@@ -139,35 +139,95 @@ __global__ void __launch_bounds__(TILE *TILE, 1024 / (TILE * TILE))
     }
 }
 
+// One CTA per tile, heaviest tiles first when the launch order is given.
+template <int TILE, bool DOM, bool LITE, int BATCH>
+__global__ void __launch_bounds__(TILE *TILE, 1024 / (TILE * TILE))
+    k_render_fwd(const float4 *__restrict__ rec, const uint32_t *__restrict__ values,
+                 const uint2 *__restrict__ ranges, const uint32_t *__restrict__ order, FrameTable ft,
+                 const float *__restrict__ obs_depth, ImagePtrs out, const int32_t *__restrict__ status) {
+    __shared__ float4 s_a[BATCH], s_b[BATCH], s_c[BATCH];
+    __shared__ int4 s_r[BATCH];
+    if (status[0] != 0) return;
+    const int gtile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
+    fwd_tile<TILE, DOM, LITE, BATCH>(gtile, rec, values, ranges, ft, obs_depth, out, s_a, s_b, s_c, s_r);
+}
+
+// Persistent form: as many CTAs as fit on the GPU at once, each pulling the
+// next (frame, tile) item -- in launch order, heaviest first -- from a device
+// counter until the batch is exhausted (work_queue.cuh).
+template <int TILE, bool DOM, bool LITE, int BATCH>
+__global__ void __launch_bounds__(TILE *TILE, 1024 / (TILE * TILE))
+    k_render_fwd_persist(const float4 *__restrict__ rec, const uint32_t *__restrict__ values,
+                         const uint2 *__restrict__ ranges, const uint32_t *__restrict__ order, FrameTable ft,
+                         const float *__restrict__ obs_depth, ImagePtrs out, const int32_t *__restrict__ status,
+                         unsigned *__restrict__ queue) {
+    __shared__ float4 s_a[BATCH], s_b[BATCH], s_c[BATCH];
+    __shared__ int4 s_r[BATCH];
+    __shared__ int s_item[2];
+    if (status[0] != 0) return;
+    for (int it = 0;; ++it) {
+        const int item = queue_next(queue, s_item, it);
+        if (item >= ft.total_tiles) break;
+        const int gtile = order ? (int)order[item] : item;
+        fwd_tile<TILE, DOM, LITE, BATCH>(gtile, rec, values, ranges, ft, obs_depth, out, s_a, s_b, s_c, s_r);
+    }
+    queue_exit(queue);
+}
+
+template <int TILE, bool DOM, bool LITE, int BATCH>
+cudaError_t launch_variant(const float4 *r4, const uint32_t *values, const uint2 *rg, const uint32_t *order,
+                           const FrameTable &ft, const float *obs_depth, const ImagePtrs &out, const int32_t *status,
+                           unsigned *queue, cudaStream_t s) {
+    if (!queue) {
+        k_render_fwd<TILE, DOM, LITE, BATCH><<<ft.total_tiles, TILE * TILE, 0, s>>>(r4, values, rg, order, ft,
+                                                                                    obs_depth, out, status);
+        return cudaGetLastError();
+    }
+    int grid = 0;
+    cudaError_t e = persistent_grid<k_render_fwd_persist<TILE, DOM, LITE, BATCH>>(TILE * TILE, 0, ft.total_tiles,
+                                                                                   &grid);
+    if (e != cudaSuccess) return e;
+    k_render_fwd_persist<TILE, DOM, LITE, BATCH><<<grid, TILE * TILE, 0, s>>>(r4, values, rg, order, ft, obs_depth,
+                                                                              out, status, queue);
+    return cudaGetLastError();
+}
+
+template <int TILE, int BATCH>
+cudaError_t launch_batch(const float4 *r4, const uint32_t *values, const uint2 *rg, const uint32_t *order,
+                         const FrameTable &ft, const float *obs_depth, const ImagePtrs &out, const int32_t *status,
+                         unsigned *queue, cudaStream_t s) {
+    const bool lite = !out.alpha && !out.unc && !out.median && !out.median_pos && !out.n_contrib;
+    if (out.dom_pos)
+        return launch_variant<TILE, true, false, BATCH>(r4, values, rg, order, ft, obs_depth, out, status, queue, s);
+    if (lite)
+        return launch_variant<TILE, false, true, BATCH>(r4, values, rg, order, ft, obs_depth, out, status, queue, s);
+    return launch_variant<TILE, false, false, BATCH>(r4, values, rg, order, ft, obs_depth, out, status, queue, s);
+}
+
 template <int TILE>
 cudaError_t launch_tile(const float4 *r4, const uint32_t *values, const uint2 *rg, const uint32_t *order,
                         const FrameTable &ft, const float *obs_depth, const ImagePtrs &out, const int32_t *status,
-                        cudaStream_t s) {
-    const bool lite = !out.alpha && !out.unc && !out.median && !out.median_pos && !out.n_contrib;
-    if (out.dom_pos)
-        k_render_fwd<TILE, true, false><<<ft.total_tiles, TILE * TILE, 0, s>>>(r4, values, rg, order, ft, obs_depth,
-                                                                                out, status);
-    else if (lite)
-        k_render_fwd<TILE, false, true><<<ft.total_tiles, TILE * TILE, 0, s>>>(r4, values, rg, order, ft, obs_depth,
-                                                                                out, status);
-    else
-        k_render_fwd<TILE, false, false><<<ft.total_tiles, TILE * TILE, 0, s>>>(r4, values, rg, order, ft, obs_depth,
-                                                                                 out, status);
-    return cudaGetLastError();
+                        int batch, unsigned *queue, cudaStream_t s) {
+    constexpr int NT = TILE * TILE;
+    if (NT < 256)  // a batch is the whole CTA's worth of entries at 8x8
+        return launch_batch<TILE, (NT < 256 ? NT : 256)>(r4, values, rg, order, ft, obs_depth, out, status, queue, s);
+    if (batch == 256)
+        return launch_batch<TILE, 256>(r4, values, rg, order, ft, obs_depth, out, status, queue, s);
+    return launch_batch<TILE, kFwdBatch>(r4, values, rg, order, ft, obs_depth, out, status, queue, s);
 }
 
 }  // namespace
 
 cudaError_t launch_render_fwd(const float *rec, const uint32_t *values, const uint32_t *ranges, const uint32_t *order,
                               const FrameTable &ft, const float *obs_depth, const ImagePtrs &out,
-                              const int32_t *status, cudaStream_t s) {
+                              const int32_t *status, int batch, unsigned *queue, cudaStream_t s) {
     if (ft.total_tiles == 0) return cudaSuccess;
     const float4 *r4 = reinterpret_cast<const float4 *>(rec);
     const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
     switch (ft.tile) {
-        case 8: return launch_tile<8>(r4, values, rg, order, ft, obs_depth, out, status, s);
-        case 16: return launch_tile<16>(r4, values, rg, order, ft, obs_depth, out, status, s);
-        case 32: return launch_tile<32>(r4, values, rg, order, ft, obs_depth, out, status, s);
+        case 8: return launch_tile<8>(r4, values, rg, order, ft, obs_depth, out, status, batch, queue, s);
+        case 16: return launch_tile<16>(r4, values, rg, order, ft, obs_depth, out, status, batch, queue, s);
+        case 32: return launch_tile<32>(r4, values, rg, order, ft, obs_depth, out, status, batch, queue, s);
         default: return cudaErrorInvalidValue;
     }
 }

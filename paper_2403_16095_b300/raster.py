@@ -31,19 +31,24 @@ class Rasterizer:
 
     def __init__(self, cams: Sequence, n_gaussians: int, tile: int = 16, mode: int = A.GS_MODE_POSE,
                  capacity: Optional[int] = None, jclamp: float = 1.3, nu_cull: float = 0.0,
-                 keep_keys: bool = False, dominant: bool = False, channels: str = "all", device=None):
+                 keep_keys: bool = False, dominant: bool = False, channels: str = "all", device=None,
+                 batch: int = 0, sched: int = A.GS_SCHED_TILE):
         """channels: "all" renders every channel; "track" only what the tracking
         loss and its POSE backward read (colour, depth, nu map, T_final, n_last),
-        which selects the lighter forward kernel."""
+        which selects the lighter forward kernel. batch (256 or 512; 0 = 512)
+        and sched (GS_SCHED_TILE or GS_SCHED_PERSISTENT) choose how the forward
+        and the FULL backward stage and schedule tiles; they change speed only."""
         self.cams = list(cams)
         self.F = len(self.cams)
         self.N = int(n_gaussians)
         self.M = self.F * self.N
         self.tile = tile
         self.mode = mode
-        self.opts = A.gs_opts(tile, mode, jclamp, nu_cull)
+        self.opts = A.gs_opts(tile, mode, jclamp, nu_cull, batch, sched)
         self.device = torch.device(device or "cuda")
         dev = self.device
+        # the persistent kernels' work queue: zero-filled once, left at zero by every launch
+        self.queue = torch.zeros(2, dtype=torch.int32, device=dev) if sched == A.GS_SCHED_PERSISTENT else None
         self.rec = torch.empty(self.M * A.GS_REC_FLOATS, dtype=torch.float32, device=dev)
         self.touched = torch.empty(self.M, dtype=torch.int32, device=dev)
         self.jac = (torch.empty(self.M * A.GS_JAC_FLOATS, dtype=torch.float32, device=dev)
@@ -121,7 +126,7 @@ class Rasterizer:
 
     def forward(self, obs_depth: Optional[torch.Tensor] = None, stream=None) -> None:
         A.gs_render_fwd(self.N, self.cams, self.opts, self.rec, self.values, self.ranges, obs_depth, self.img,
-                        self.status, stream, order=self.order)
+                        self.status, stream, order=self.order, queue=self.queue)
 
     def backward(self, *, obs_depth=None, loss: Optional[dict] = None, dL: Optional[dict] = None,
                  g: Optional[Gaussians] = None, T_cw: Optional[torch.Tensor] = None, grads: Optional[dict] = None,
@@ -130,7 +135,8 @@ class Rasterizer:
         ``pose_grad`` (otherwise call reduce_pose())."""
         A.gs_render_bwd(self.N, self.cams, self.opts, self.rec, self.jac, self.values, self.ranges, T_cw, g,
                         obs_depth, self.img, dL, loss, grads, self.pose_partials,
-                        self.pose_grad if fused_pose else None, self.status, self.bwd_ws, stream, order=self.order)
+                        self.pose_grad if fused_pose else None, self.status, self.bwd_ws, stream, order=self.order,
+                        queue=self.queue)
 
     def fwd_bwd_pose(self, loss: dict, images: bool = False, fused_pose: bool = True, stream=None,
                      adam_state=None, adam=None, T_cw=None) -> None:
@@ -192,6 +198,36 @@ class Rasterizer:
             self.set_capacity(int(need * 1.25) + 1024)
         raise A.GsError(A.GS_ERR_CAPACITY, "pair capacity still exceeded")
 
+    def step(self, g, T_cw: torch.Tensor, obs_depth=None, loss: Optional[dict] = None,
+             grads: Optional[dict] = None, stream=None) -> None:
+        """One batch step, enqueued without any host sync: project, bin,
+        forward and, unless in FWD mode, the backward with the fused ``loss``
+        (FULL mode: parameter gradients into ``grads``, overwritten)."""
+        self.project(g, T_cw, stream)
+        self.bin(stream)
+        self.forward(obs_depth, stream)
+        if self.mode == A.GS_MODE_FULL:
+            self.backward(obs_depth=obs_depth, loss=loss, g=g, T_cw=T_cw, grads=grads, stream=stream)
+        elif self.mode == A.GS_MODE_POSE:
+            self.backward(obs_depth=obs_depth, loss=loss, stream=stream)
+
+    def capture_step(self, g, T_cw: torch.Tensor, obs_depth=None, loss: Optional[dict] = None,
+                     grads: Optional[dict] = None) -> "torch.cuda.CUDAGraph":
+        """step() captured once in a CUDA graph on a side stream (after one
+        eager run, which also raises the kernels' one-time attributes). The
+        graph reads and writes the same tensors every replay: update their
+        contents in place, then graph.replay(). Read the status word after a
+        replay: a pair overflow needs set_capacity() and a new capture."""
+        s = torch.cuda.Stream(device=self.device)
+        s.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(s):
+            self.step(g, T_cw, obs_depth, loss, grads, s)
+        s.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=s):
+            self.step(g, T_cw, obs_depth, loss, grads, s)
+        return graph
+
     # --------------------------------------------------------------- views
     def frame_images(self, f: int) -> dict:
         """Per-frame views: color [3,H,W], the others [H,W]."""
@@ -211,52 +247,62 @@ class Rasterizer:
 
 
 # ===================================================================== autotuner
-_TILE_CACHE: dict = {}
+_TUNE_CACHE: dict = {}
+
+
+def autotune(cams: Sequence, g, T_cw: torch.Tensor, obs_depth=None, mode: int = A.GS_MODE_FULL,
+             loss: Optional[dict] = None, tiles=(8, 16, 32), batches=(256, 512),
+             scheds=(A.GS_SCHED_TILE, A.GS_SCHED_PERSISTENT), reps: int = 3, jclamp: float = 1.3,
+             nu_cull: float = 0.0):
+    """Picks the tile size (8, 16 or 32 pixels), the per-CTA staging batch of
+    the blend kernels (256 or 512 list entries; 8x8 tiles always stage 64) and
+    the schedule (one CTA per tile, or persistent CTAs pulling tiles from a
+    device queue) of a frame batch, by timing one whole step (Rasterizer.step:
+    project, bin, forward and, unless mode is FWD, the backward with the fused
+    ``loss``) with CUDA events, ``reps`` times per candidate after one untimed
+    run. Images and gradients do not depend on any of the three (same per-pixel
+    lists and arithmetic), so the choice changes speed only. Results are cached
+    per (resolutions, N, mode). Returns ((tile, batch, sched), {(tile, batch,
+    sched): ms})."""
+    key = (tuple((int(c.width), int(c.height)) for c in cams), int(g.n), int(mode), tuple(tiles), tuple(batches),
+           tuple(scheds))
+    if key in _TUNE_CACHE:
+        return _TUNE_CACHE[key]
+    full = mode == A.GS_MODE_FULL
+    grads = {k: torch.empty_like(getattr(g, k)) for k in
+             ("means", "log_scales", "quats", "opacity_logit", "colors", "nu")} if full else None
+    times = {}
+    cap = None
+    for t in tiles:
+        for b in (batches if t >= 16 else batches[:1]):  # 8x8 tiles stage 64 whatever the batch
+            for sc in scheds:
+                r = Rasterizer(cams, g.n, tile=t, mode=mode, jclamp=jclamp, nu_cull=nu_cull, batch=b, sched=sc)
+                r.render(g, T_cw, obs_depth)
+                r.set_capacity(int(r.read_status()[1] * 1.25) + 4096)
+                r.step(g, T_cw, obs_depth, loss, grads)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    r.step(g, T_cw, obs_depth, loss, grads)
+                e1.record()
+                e1.synchronize()
+                if r.read_status()[0] != 0:
+                    raise A.GsError(r.read_status()[0], f"autotune tile {t} batch {b} sched {sc}")
+                times[(t, b, sc)] = e0.elapsed_time(e1) / reps
+                del r
+    best = min(times, key=times.get)
+    _TUNE_CACHE[key] = (best, times)
+    return best, times
 
 
 def autotune_tile(cams: Sequence, g, T_cw: torch.Tensor, obs_depth=None, mode: int = A.GS_MODE_FULL,
                   loss: Optional[dict] = None, candidates=(8, 16, 32), reps: int = 3, jclamp: float = 1.3,
                   nu_cull: float = 0.0):
-    """Picks the tile size (8, 16 or 32 pixels) of a frame batch by timing one
-    whole iteration (project, bin, forward and, unless mode is FWD, the backward
-    with the fused ``loss``) with CUDA events, ``reps`` times per candidate after
-    one untimed run. The rendered images and gradients do not depend on the tile
-    size (same per-pixel lists and arithmetic), so the choice changes speed only.
-    Results are cached per (resolutions, N, mode). Returns (best tile, {tile: ms})."""
-    key = (tuple((int(c.width), int(c.height)) for c in cams), int(g.n), int(mode))
-    if key in _TILE_CACHE:
-        return _TILE_CACHE[key]
-    full = mode == A.GS_MODE_FULL
-    grads = {k: torch.empty_like(getattr(g, k)) for k in
-             ("means", "log_scales", "quats", "opacity_logit", "colors", "nu")} if full else None
-    times = {}
-    for t in candidates:
-        r = Rasterizer(cams, g.n, tile=t, mode=mode, jclamp=jclamp, nu_cull=nu_cull)
-        r.render(g, T_cw, obs_depth)
-        r.set_capacity(int(r.read_status()[1] * 1.25) + 4096)
-
-        def one():
-            r.project(g, T_cw)
-            r.bin()
-            r.forward(obs_depth)
-            if mode != A.GS_MODE_FWD:
-                r.backward(obs_depth=obs_depth, loss=loss, g=g if full else None, T_cw=T_cw if full else None,
-                           grads=grads)
-
-        one()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            one()
-        e1.record()
-        e1.synchronize()
-        if r.read_status()[0] != 0:
-            raise A.GsError(r.read_status()[0], f"autotune tile {t}")
-        times[t] = e0.elapsed_time(e1) / reps
-        del r
-    best = min(times, key=times.get)
-    _TILE_CACHE[key] = (best, times)
-    return best, times
+    """autotune() over the tile size alone (batch 512, one CTA per tile).
+    Returns (best tile, {tile: ms})."""
+    best, times = autotune(cams, g, T_cw, obs_depth, mode, loss, tiles=candidates, batches=(512,),
+                           scheds=(A.GS_SCHED_TILE,), reps=reps, jclamp=jclamp, nu_cull=nu_cull)
+    return best[0], {k[0]: v for k, v in times.items()}
 
 
 # ===================================================================== autograd

@@ -32,7 +32,45 @@ def rec_fields(r):
                 color=f[:, 8:11], radius=f[:, 11], rect=rect, valid=rect[:, 0] <= rect[:, 2])
 
 
-def decision_margin(ora, pix_mask=None):
-    """Per-pixel minimum of the oracle's normalised decision margins."""
-    m = ora["margins"].min(axis=0)
-    return m if pix_mask is None else m[pix_mask]
+# One image tolerance and one decision margin for every GPU-vs-oracle image
+# comparison (the derivation is in the design notes, "FP32/FP64 decision flips"):
+#   IMG_TOL          absolute, on every rendered channel: colour, depth, opacity,
+#                    U, nu map, T_final, median depth;
+#   DECISION_MARGIN  relative oracle margin of a threshold decision below which
+#                    FP32 and FP64 may decide differently: q vs 9, alpha vs 1/255,
+#                    T' vs 1e-4, opacity*G vs 0.99, T vs 0.5 (median), and the lead
+#                    of the largest blend weight (dominant entry, Eq. 13). FP32
+#                    carries T through up to a few hundred multiplications (~n 2^-24
+#                    relative) and q through a cancelling sum of three terms;
+#   ORDER_MARGIN     relative depth gap of neighbouring list entries below which the
+#                    FP32 z order may differ from the FP64 one.
+IMG_TOL = 1e-4
+DECISION_MARGIN = 1e-4
+ORDER_MARGIN = 1e-5
+CHANNELS = ("color", "depth", "alpha", "unc", "nu_map", "T_final", "median")
+
+
+def at_decision_margin(ora):
+    """Per pixel (or sample): True where some oracle decision sits within the
+    margins above, i.e. where FP32 may legitimately take another branch."""
+    m = ora["margins"]
+    return (m[[0, 1, 2, 3, 5]].min(axis=0) < DECISION_MARGIN) | (m[4] < ORDER_MARGIN)
+
+
+def image_mismatch(im, ora, channels=CHANNELS, pix=None):
+    """Per pixel: some channel differs from the oracle by more than IMG_TOL.
+    im: GPU images ([3,H,W] colour, [H,W] others); ora: oracle images, full
+    ([..,H,W]) or sampled at the flat pixel indices ``pix`` ([..,n])."""
+    bad = None
+    for k in channels:
+        if k not in im or k not in ora:
+            continue
+        got = np.asarray(im[k])
+        want = ora[k]
+        if pix is not None:
+            got = got.reshape(3, -1)[:, pix] if k == "color" else got.reshape(-1)[pix]
+        e = np.abs(got - want)
+        if k == "color":
+            e = e.max(0)
+        bad = e > IMG_TOL if bad is None else bad | (e > IMG_TOL)
+    return bad

@@ -42,7 +42,7 @@ def test_header_compiles_as_plain_c(tmp_path):
 
 
 def test_pure_host_queries(A):
-    assert A.lib.gs_abi_version() == A.ABI_VERSION == 8
+    assert A.lib.gs_abi_version() == A.ABI_VERSION == 9
     assert A.gs_bin_tiles_workspace_size(1000, 5000) >= 5000 * (8 + 8)
     assert A.gs_bin_tiles_workspace_size(10, 0) == 0
     cams = [type("C", (), dict(width=640, height=480, fx=600, fy=600, cx=320, cy=240, znear=0.2))()]
@@ -93,3 +93,24 @@ def test_argument_errors_are_synchronous(A):
     assert st == A.GS_ERR_INVALID_ARG and "workspace" in A.last_error()
     st = lib.gs_pose_grad_reduce(None, 1, 1, None, None, None)
     assert st == A.GS_ERR_INVALID_ARG
+
+
+def test_schedule_and_batch_options_are_checked(A):
+    """gs_opts.batch must be 0, 256 or 512 and gs_opts.sched a known schedule;
+    the persistent schedule needs the caller's work queue. All rejected before
+    any launch."""
+    lib = A.lib
+    cam = (A.gs_camera * 1)(A.gs_camera(64, 48, 50.0, 50.0, 32.0, 24.0, 0.2))
+    p = C.c_void_p(256)
+    p0 = A.gs_projected(0, 1, p, p, None)
+    img = A.gs_image(p, p, None, None, None, None, p, p)
+    st32 = C.c_void_p(256)
+    for bad, word in ((A.gs_opts(16, A.GS_MODE_FWD, 1.3, 0.0, 300, 0), "batch"),
+                      (A.gs_opts(16, A.GS_MODE_FWD, 1.3, 0.0, 0, 7), "sched")):
+        tiles = A.gs_tiles(10, 12, p, None, p)
+        st = lib.gs_render_fwd(C.byref(p0), C.byref(tiles), 1, cam, None, C.byref(bad), C.byref(img), st32, None)
+        assert st == A.GS_ERR_INVALID_ARG and word in A.last_error()
+    persist = A.gs_opts(16, A.GS_MODE_FWD, 1.3, 0.0, 256, A.GS_SCHED_PERSISTENT)
+    tiles = A.gs_tiles(10, 12, p, None, p)  # no queue
+    st = lib.gs_render_fwd(C.byref(p0), C.byref(tiles), 1, cam, None, C.byref(persist), C.byref(img), st32, None)
+    assert st == A.GS_ERR_INVALID_ARG and "queue" in A.last_error()

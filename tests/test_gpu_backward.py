@@ -18,7 +18,7 @@ import torch
 
 import oracle
 import synth
-from tests.gpu_util import PARAMS, f32_scene, poses_gpu, to_gpu_gaussians
+from tests.gpu_util import DECISION_MARGIN, f32_scene, image_mismatch, PARAMS, poses_gpu, to_gpu_gaussians
 
 pytestmark = pytest.mark.gpu
 
@@ -272,14 +272,12 @@ def test_degenerate_gaussians_match_oracle():
     r, grads = _run(A.GS_MODE_FULL, sc, cam, T, tc[0], td[0], W_ALL)
     ora = oracle.render(f32_scene(sc), cam, T, obs_depth=td[0])
     im = {k: v.cpu().numpy() for k, v in r.frame_images(0).items()}
-    bad = np.abs(im["color"] - ora["color"]).max(0) > 1e-4
-    for k in ("depth", "alpha", "unc", "nu_map", "T_final"):
-        bad |= np.abs(im[k] - ora[k]) > 1e-4
+    bad = image_mismatch(im, ora, ("color", "depth", "alpha", "unc", "nu_map", "T_final"))
     # a differing pixel must sit at an FP32-vs-FP64 decision flip (the depth-gap
     # margin, channel 4, is left out: equal depths are ordered by index on both
     # sides, and the ten Gaussians outside the image share z = 2)
     flip = ora["margins"][[0, 1, 2, 3, 5]].min(axis=0)
-    assert np.all(flip[bad] < 1e-4) and int(bad.sum()) <= 3, int(bad.sum())
+    assert np.all(flip[bad] < DECISION_MARGIN) and int(bad.sum()) <= 3, int(bad.sum())
     og = oracle.grad(f32_scene(sc), cam, T, _spec(W_ALL, tc[0], td[0]))
     for k in PARAMS:
         got = grads[k].cpu().numpy()

@@ -3,7 +3,7 @@ oracle: the dominated-pixel map of every keyframe, the per-Gaussian sums and
 counts over a 4-keyframe window, the division and the tau = 0.025 opacity rule.
 
 A pixel whose two largest blend weights are within FP32 rounding of each other
-(oracle lead < 1e-5), or which sits at another FP32/FP64 decision margin, may
+(oracle lead below the decision margin), or which sits at another FP32/FP64 decision margin, may
 pick a different dominant Gaussian in FP32; such pixels are counted and the
 Gaussians they feed are excluded from the per-Gaussian comparison."""
 import math
@@ -14,7 +14,7 @@ import torch
 
 import oracle
 import synth
-from tests.gpu_util import f32_scene, poses_gpu, to_gpu_gaussians
+from tests.gpu_util import DECISION_MARGIN, at_decision_margin, f32_scene, poses_gpu, to_gpu_gaussians
 
 pytestmark = pytest.mark.gpu
 
@@ -51,9 +51,9 @@ def _run(sc, cam, Ts, Ds, frames):
 
 def _flip_pixels(ora_img, gpu_dom):
     lead = ora_img["dom_margin"]
-    marg = ora_img["margins"].min(axis=0)
     diff = gpu_dom != ora_img["dominant"]
-    assert np.all((lead[diff] < 1e-5) | (marg[diff] < 1e-5)), "dominant differs away from a decision margin"
+    assert np.all((lead[diff] < DECISION_MARGIN) | at_decision_margin(ora_img)[diff]), \
+        "dominant differs away from a decision margin"
     return diff
 
 

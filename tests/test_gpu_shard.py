@@ -1,0 +1,103 @@
+"""The frame-sharded mapping window on the GPU (multi-GPU layout of Eq. 21's
+keyframe window): two gloo ranks, each a separate process driving the real
+FULL backward (libgs kernels) on its own keyframes of the 8-frame, 640x480,
+1M-Gaussian window, then one all-reduce of the parameter gradients. Both
+processes share the one GPU here; their kernels never wait on each other (the
+only exchange is the host-side gloo collective between whole steps). The sum
+must equal the single-launch 8-frame gradient up to FP32 summation order (within
+a few times the single launch's own run-to-run spread, which its atomic sums in
+arrival order give it), and each frame's pose gradient must be its owner's."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch
+import torch.multiprocessing as mp
+
+import synth
+from tests.gpu_util import PARAMS, to_gpu_gaussians
+
+pytestmark = pytest.mark.gpu
+
+
+def _window():
+    w = synth.workload("mapping")
+    sc, cams, poses = w["scene"], w["cams"], w["poses"]
+    tc, td = synth.random_targets(cams[0], 1003 + 70, n_frames=len(cams), depth_range=(0.5, 6.0))
+    return sc, cams, np.asarray(poses, np.float32), tc, td
+
+
+def _run(rank, world):
+    from paper_2403_16095_b300.shard import ShardedWindow
+    sc, cams, poses, tc, td = _window()
+    g = to_gpu_gaussians(sc)
+    T = torch.from_numpy(poses).cuda()
+    sw = ShardedWindow(cams, sc.n, T, torch.from_numpy(tc).cuda(), torch.from_numpy(td).cuda(), rank=rank,
+                       world=world)
+    sw.prepare(g)
+    grads = {k: torch.empty_like(getattr(g, k)) for k in PARAMS}
+    sw.step(g, grads)
+    torch.cuda.synchronize()
+    assert sw.status()[0] == 0
+    return ({k: v.cpu().numpy() for k, v in grads.items()},
+            {f: v.cpu().numpy() for f, v in sw.pose_grads().items()}, sw.frames)
+
+
+def _rank_main(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        torch.cuda.set_device(0)
+        q.put((rank,) + _run(rank, world))
+    finally:
+        dist.destroy_process_group()
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def test_two_rank_sharded_window_equals_single_launch():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=600) for _ in procs]
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    want, want_pose, frames = _run(0, 1)
+    assert frames == list(range(8))
+    # the single launch's own run-to-run spread: FP32 atomic sums in arrival order
+    again, again_pose, _ = _run(0, 1)
+    spread = {k: (np.abs(again[k] - want[k]).max() / np.abs(want[k]).max(),
+                  np.linalg.norm(again[k].astype(np.float64) - want[k]) / np.linalg.norm(want[k]))
+              for k in PARAMS if np.any(want[k])}
+    owners = {}
+    for rank, g, poses, mine in res:
+        assert mine == list(range(rank, 8, 2))
+        for f in mine:
+            owners[f] = rank
+            rel = np.abs(poses[f] - want_pose[f]).max() / np.abs(want_pose[f]).max()
+            assert rel < 1e-6, (f, rel)
+        for k in PARAMS:
+            if not np.any(want[k]):  # no loss term reaches this parameter (nu here): exactly zero
+                assert not np.any(g[k]), k
+                continue
+            d = g[k].astype(np.float64) - want[k]
+            scale = np.abs(want[k]).max()
+            e_max = np.abs(d).max() / scale
+            e_norm = np.linalg.norm(d) / np.linalg.norm(want[k])
+            print(f"rank {rank} {k}: max {e_max:.2e} of scale, norm {e_norm:.2e} "
+                  f"(single launch run to run: {spread[k][0]:.2e}, {spread[k][1]:.2e})")
+            # within a few times the order noise of the single launch itself
+            assert e_max < max(4 * spread[k][0], 1e-5) and e_norm < max(4 * spread[k][1], 1e-6), (k, e_max, e_norm)
+    assert sorted(owners) == list(range(8))
+    for k in PARAMS:  # both ranks hold the same summed gradients
+        assert np.array_equal(res[0][1][k], res[1][1][k])

@@ -9,7 +9,7 @@ import torch
 
 import oracle
 import synth
-from tests.gpu_util import f32_scene, poses_gpu, to_gpu_gaussians
+from tests.gpu_util import IMG_TOL, at_decision_margin, f32_scene, image_mismatch, poses_gpu, to_gpu_gaussians
 
 pytestmark = pytest.mark.gpu
 
@@ -95,14 +95,13 @@ def test_full_size_forward_matches_oracle(track_full):
     torch.cuda.synchronize()
     im = {k: v.cpu().numpy() for k, v in r.frame_images(0).items()}
     ora = oracle.render(f32_scene(sc), cam, T, obs_depth=td)
-    bad = np.zeros(td.shape, bool)
-    for k in ("color", "depth", "alpha", "unc", "nu_map", "T_final"):
-        e = np.abs(im[k] - ora[k])
-        bad |= (e.max(0) if k == "color" else e) > 1e-4 * (1 + (k == "unc") * np.abs(ora["unc"]))
+    # every channel, U included, within IMG_TOL absolute (U reaches ~4 m^2 here;
+    # its FP32 error away from decision margins measured 1e-5)
+    bad = image_mismatch(im, ora)
     frac = bad.mean()
-    print("pixels beyond 1e-4:", int(bad.sum()), "of", bad.size)
+    print("pixels beyond", IMG_TOL, ":", int(bad.sum()), "of", bad.size)
     assert frac < 2e-3
-    assert np.all(ora["margins"].min(0)[bad] < 1e-4)
+    assert np.all(at_decision_margin(ora)[bad])
 
 
 def test_full_size_pose_gradient_matches_oracle(track_full):
