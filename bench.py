@@ -70,11 +70,12 @@ FWD_FLOP_PER_CONTRIB = 26
 # workload, from one ncu capture of the current kernel
 # (profiles/k_render_fused_pose_track-640x480-300k.md, cold cache); None once
 # the kernel changes.
-FUSED_DRAM_BYTES_PER_LAUNCH = 16.350208e6 + 0
-# DRAM bytes (read + write) of one whole tracking iteration (the 6 kernels),
-# from one ncu capture with the caches carried over between kernels; None
-# until captured for the current build.
-DRAM_BYTES_PER_ITERATION = None
+FUSED_DRAM_BYTES_PER_LAUNCH = 16.348160e6 + 0
+# DRAM bytes (read + write) of one whole tracking iteration (its 6 kernels),
+# from one ncu capture with the caches carried over between kernels
+# (profiles/dram_iteration_track-640x480-300k.md); None once a kernel of the
+# iteration changes.
+DRAM_BYTES_PER_ITERATION = 0.513792e6 + 2.860544e6
 FP32_LANES_PER_SM = 128
 
 
