@@ -76,6 +76,9 @@ FUSED_DRAM_BYTES_PER_LAUNCH = 16.348160e6 + 0
 # (profiles/dram_iteration_track-640x480-300k.md); None once a kernel of the
 # iteration changes.
 DRAM_BYTES_PER_ITERATION = 0.513792e6 + 2.860544e6
+# DRAM bytes of one k_render_fused_pose<16, 4> launch at 1200x680 on the 5M
+# Gaussians in 16-bit storage (ncu, cold cache); None for other builds.
+PREC16_FUSED_DRAM_BYTES_PER_LAUNCH = 104.520192e6 + 2.896640e6
 FP32_LANES_PER_SM = 128
 
 
@@ -732,8 +735,10 @@ def run_precision(a):
     launch_ms = statistics.mean(bwd)
     dense = g32.n >= 800 * tr.rast.n_tiles
     achieved = E * flop / (launch_ms * 1e-3) / 1e12
+    traffic = PREC16_FUSED_DRAM_BYTES_PER_LAUNCH if (packed and dense and a.tile == 16) else None
     roof = {"kernel": f"k_render_fused_pose<{a.tile}, {4 if dense else 3}>", "bound": "alu", "achieved": achieved,
-            "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+            "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch, cold cache",
             "peak_source": f"{n_sm} SMs (device query) x 128 FP32 lanes x 2 x {mhz:.0f} MHz (max SM clock)",
             "flop_per_contribution": flop, "contributions_per_launch": E, "avg_launch_ms": launch_ms,
             "launches": len(bwd)}
