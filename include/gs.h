@@ -365,9 +365,11 @@ gs_status gs_render_bwd(const gs_projected *proj, const gs_tiles *tiles, int n_f
  * depth, nu_map, T_final and n_last to have them written as well (its other
  * members are ignored). pose_partials, pose_grad and ws as for gs_render_bwd
  * in POSE mode (ws: gs_render_bwd_workspace_size(records, GS_MODE_POSE)).
- * If adam_state is not NULL (then pose_grad, adam and T_cw are required), the
- * CTA that reduces frame f's pose gradient also applies gs_pose_adam_step to
- * frame f (same arithmetic), rewriting T_cw for the next iteration.          */
+ * Two launches: the pass writes one pose partial per tile; if pose_grad is not
+ * NULL, a chained launch then sums each frame's partials into pose_grad, bit
+ * for bit as gs_pose_grad_reduce, and, if adam_state is not NULL (then adam
+ * and T_cw are required), applies gs_pose_adam_step to every frame (same
+ * arithmetic), rewriting T_cw for the next iteration.                        */
 gs_status gs_render_fwd_bwd_pose(const gs_projected *proj, const gs_tiles *tiles, int n_frames,
                                  const gs_camera *cams, const gs_loss *loss, const gs_opts *opts,
                                  gs_image *out, float *pose_partials, double *pose_grad,

@@ -455,7 +455,6 @@ gs_status gs_render_fwd_bwd_pose(const gs_projected *proj, const gs_tiles *tiles
     const size_t need = bwd_ws_bytes(M, GS_MODE_POSE);
     if (!ws || ws_bytes < need || !aligned(ws, 256))
         return fail(GS_ERR_INVALID_ARG, "workspace %zu bytes < %zu needed (256-aligned)", ws_bytes, need);
-    unsigned *counters = reinterpret_cast<unsigned *>(static_cast<char *>(ws) + grad2d_bytes(M, GS_MODE_POSE));
     cudaError_t e;
     for (int f = 0; f < n_frames; ++f) {
         const int used = ft.f[f].tiles_x * ft.f[f].tiles_y;
@@ -466,10 +465,14 @@ gs_status gs_render_fwd_bwd_pose(const gs_projected *proj, const gs_tiles *tiles
         }
     }
     const gs_adam ad = adam ? *adam : gs_adam{};
-    return cuda_status(gs::launch_render_fused_pose(proj->rec, proj->pose_jac, tiles->values, tiles->ranges,
-                                                    tiles->order, ft, ip, lp, pose_partials, per_frame, pose_grad,
-                                                    counters, adam_state, ad, T_cw, status, M, stream),
-                       "gs_render_fwd_bwd_pose");
+    // the pass writes one pose partial per tile; the frame's fixed-order sum
+    // (and the Adam step) follow as one small chained launch
+    e = gs::launch_render_fused_pose(proj->rec, proj->pose_jac, tiles->values, tiles->ranges, tiles->order, ft, ip,
+                                     lp, pose_partials, per_frame, status, M, stream);
+    if (e != cudaSuccess || !pose_grad) return cuda_status(e, "gs_render_fwd_bwd_pose");
+    return cuda_status(gs::launch_pose_reduce_adam(pose_partials, n_frames, per_frame, pose_grad, adam_state, ad, T_cw,
+                                                   status, stream),
+                       "gs_render_fwd_bwd_pose (pose reduction)");
 }
 
 gs_status gs_nu_accumulate(const gs_projected *proj, const gs_tiles *tiles, int n_frames, const gs_camera *cams,

@@ -71,32 +71,67 @@ constexpr int kRedSlots = 256;
 
 // Fixed-order sum of K pose partials into six FP64 values. Slot s in [0, 256)
 // accumulates partials j = s, s + 256, ... in increasing j, then a fixed binary
-// tree combines the slots. The order depends only on K -- not on the number of
-// threads running it -- so every caller gets bit-identical results. Loads
-// bypass L1 (the partials may have been written by other CTAs of the same
-// launch). Needs blockDim.x >= 6 and a shared buffer of 256 x 6 double-floats.
+// tree combines the slots (slot s takes slot s + stride, stride 128 down to 1).
+// The order depends only on K -- not on the number of threads running it -- so
+// every caller gets bit-identical results. Loads bypass L1 (the partials may
+// have been written by other CTAs of the same launch) and are issued four
+// partials at a time, so a slot waits for one L2 round trip per four partials
+// instead of one per partial; the adds keep their order. The tree runs through
+// shared memory down to 32 slots, then in warp 0 by shuffles (same pairs, same
+// operand order). Needs blockDim.x >= 32 and a shared buffer of 256 x 6
+// double-floats.
 __device__ __forceinline__ void reduce_pose_partials(const float *p, int K, double *out6, df (*s_red)[6]) {
+    constexpr int kAhead = 4;
     for (int s = threadIdx.x; s < kRedSlots; s += blockDim.x) {
         df acc[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) acc[k] = {0.f, 0.f};
-        for (int j = s; j < K; j += kRedSlots)
+        for (int j = s; j < K; j += kAhead * kRedSlots) {
+            float2 v[kAhead][6];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                const float2 v = __ldcg(reinterpret_cast<const float2 *>(p) + (size_t)j * 6 + k);
-                acc[k] = df_add(acc[k], df{v.x, v.y});
+            for (int r = 0; r < kAhead; ++r) {
+                const int jj = j + r * kRedSlots;
+#pragma unroll
+                for (int k = 0; k < 6; ++k)
+                    v[r][k] = jj < K ? __ldcg(reinterpret_cast<const float2 *>(p) + (size_t)jj * 6 + k)
+                                     : make_float2(0.f, 0.f);
             }
+#pragma unroll
+            for (int r = 0; r < kAhead; ++r)
+                if (j + r * kRedSlots < K)
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) acc[k] = df_add(acc[k], df{v[r][k].x, v[r][k].y});
+        }
 #pragma unroll
         for (int k = 0; k < 6; ++k) s_red[s][k] = acc[k];
     }
     __syncthreads();
-    for (int stride = kRedSlots / 2; stride > 0; stride >>= 1) {
+    for (int stride = kRedSlots / 2; stride >= 32; stride >>= 1) {
         for (int s = threadIdx.x; s < stride; s += blockDim.x)
 #pragma unroll
             for (int k = 0; k < 6; ++k) s_red[s][k] = df_add(s_red[s][k], s_red[s + stride][k]);
         __syncthreads();
     }
-    if (threadIdx.x < 6) out6[threadIdx.x] = (double)s_red[0][threadIdx.x].hi + (double)s_red[0][threadIdx.x].lo;
+    if (threadIdx.x < 32) {
+        df h[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) h[k] = s_red[threadIdx.x][k];
+#pragma unroll
+        for (int stride = 16; stride > 0; stride >>= 1)
+#pragma unroll
+            for (int k = 0; k < 6; ++k)
+                h[k] = df_add(h[k], df{__shfl_down_sync(0xffffffffu, h[k].hi, stride),
+                                       __shfl_down_sync(0xffffffffu, h[k].lo, stride)});
+        // lane 0 holds the tree's root; hand it to lanes 0-5, one component each
+        double r = 0.0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float hi = __shfl_sync(0xffffffffu, h[k].hi, 0), lo = __shfl_sync(0xffffffffu, h[k].lo, 0);
+            if (threadIdx.x == k) r = (double)hi + (double)lo;
+        }
+        if (threadIdx.x < 6) out6[threadIdx.x] = r;
+    }
+    __syncthreads();
 }
 
 // Per-CTA double-float sum of six per-thread FP32 values (fixed tree); thread 0

@@ -141,11 +141,11 @@ cudaError_t launch_spatial_order(const float *means, int n, uint32_t *perm, void
 cudaError_t launch_pack_bf16(const GaussPtrs &g, int n, const uint32_t *perm, float *anchors, uint16_t *packed,
                              const int32_t *status, cudaStream_t s);
 // render_fused.cu
+// writes one pose partial per tile; launch_pose_reduce_adam then sums them
 cudaError_t launch_render_fused_pose(const float *rec, const float *jac, const uint32_t *values,
                                      const uint32_t *ranges, const uint32_t *order, const FrameTable &ft,
                                      const ImagePtrs &out, const LossParams &lp, float *pose_partials, int per_frame,
-                                     double *pose_grad, unsigned *counters, double *adam_state, const gs_adam &adam,
-                                     float *T_cw, const int32_t *status, int n_records, cudaStream_t s);
+                                     const int32_t *status, int n_records, cudaStream_t s);
 // nu.cu
 cudaError_t launch_nu_accumulate(const float *rec, const uint32_t *values, const FrameTable &ft, int n_gaussians,
                                  const float *obs_depth, const int32_t *dom_pos, const float *dom_weight,
@@ -159,5 +159,9 @@ cudaError_t launch_pose_reduce(const float *partials, int n_frames, int per_fram
                                const int32_t *status, cudaStream_t s);
 cudaError_t launch_pose_adam(double *state, const double *grad, float *T_cw, int n_frames, gs_adam adam,
                              const int32_t *status, cudaStream_t s);
+// pose reduction (+ Adam step when adam_state is not NULL), chained after the tracking pass
+cudaError_t launch_pose_reduce_adam(const float *partials, int n_frames, int per_frame, double *pose_grad,
+                                    double *adam_state, const gs_adam &adam, float *T_cw, const int32_t *status,
+                                    cudaStream_t s);
 
 }  // namespace gs

@@ -39,7 +39,35 @@ __global__ void __launch_bounds__(32)
     pose_adam_warp(state + (size_t)f * GS_POSE_STATE_DOUBLES, grad + (size_t)f * 6, T_cw + (size_t)f * 12, ad);
 }
 
+// The frame's pose reduction and, with adam_state, its Adam step, as one small
+// launch chained after the tracking pass (programmatic dependent launch): one
+// CTA per frame waits for the pass to complete, sums the frame's per-tile
+// partials in the fixed order of reduce_pose_partials (the bits of
+// gs_pose_grad_reduce) and applies the pose update in warp 0. No CTA of the
+// pass fences or takes an arrival ticket.
+__global__ void __launch_bounds__(kRedThreads)
+    k_pose_reduce_adam(const float *__restrict__ partials, int per_frame, double *__restrict__ pose_grad,
+                       double *__restrict__ adam_state, gs_adam ad, float *__restrict__ T_cw,
+                       const int32_t *__restrict__ status) {
+    dep_wait();
+    __shared__ df s_red[kRedSlots][6];
+    if (status[0] != 0) return;
+    const int f = blockIdx.x;
+    reduce_pose_partials(partials + (size_t)f * per_frame * 12, per_frame, pose_grad + (size_t)f * 6, s_red);
+    if (adam_state && threadIdx.x < 32)
+        pose_adam_warp(adam_state + (size_t)f * GS_POSE_STATE_DOUBLES, pose_grad + (size_t)f * 6, T_cw + (size_t)f * 12,
+                       ad);
+}
+
 }  // namespace
+
+cudaError_t launch_pose_reduce_adam(const float *partials, int n_frames, int per_frame, double *pose_grad,
+                                    double *adam_state, const gs_adam &adam, float *T_cw, const int32_t *status,
+                                    cudaStream_t s) {
+    if (n_frames == 0) return cudaSuccess;
+    return launch_chained(k_pose_reduce_adam, dim3(n_frames), dim3(kRedThreads), 0, s, partials, per_frame, pose_grad,
+                          adam_state, adam, T_cw, status);
+}
 
 cudaError_t launch_pose_reduce(const float *partials, int n_frames, int per_frame, double *out,
                                const int32_t *status, cudaStream_t s) {

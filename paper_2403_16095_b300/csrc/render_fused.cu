@@ -13,15 +13,15 @@
 //     for the forward stay in shared memory for the backward when the batch
 //     boundaries coincide, i.e. whenever the walk fits in one batch;
 //   - one launch and one tail of idle SMs;
-//   - optionally the Adam launch: the CTA that reduces a frame's pose gradient
-//     also applies the pose update (the same warp routine as
-//     gs_pose_adam_step).
+//   - the pose reduction's arrival ticket and memory fence in every CTA: the
+//     per-tile partials are summed (and the Adam step applied) by one small
+//     launch chained after this one (launch_pose_reduce_adam), which measured
+//     ~2 us per tracking iteration faster than a last-CTA tail in this kernel.
 // The per-pixel arithmetic is the same as in the two kernels (same helpers,
 // same order), so images and pose gradients are bit-identical to them.
 #include "gs_internal.cuh"
 #include "blend_common.cuh"
 #include "dfloat.cuh"
-#include "pose_adam.cuh"
 
 #include <atomic>
 
@@ -36,9 +36,7 @@ template <int TILE>
 struct FusedSmem {
     static constexpr int NT = TILE * TILE;
     static constexpr int BATCH = NT < 256 ? NT : 256;
-    static constexpr size_t kStage = (size_t)BATCH * 13 * sizeof(float4);  // record (4) + Jacobian (9)
-    static constexpr size_t kRed = sizeof(df) * kRedSlots * 6;
-    static constexpr size_t bytes = kStage > kRed ? kStage : kRed;
+    static constexpr size_t bytes = (size_t)BATCH * 13 * sizeof(float4);  // record (4) + Jacobian (9)
 };
 
 // Two builds per tile size: MINB = 3 (80 registers, 3 CTAs per SM at tile 16)
@@ -53,9 +51,7 @@ __global__ void __launch_bounds__(TILE *TILE, MINB)
     k_render_fused_pose(const float4 *__restrict__ rec, const float4 *__restrict__ jac,
                         const uint32_t *__restrict__ values, const uint2 *__restrict__ ranges,
                         const uint32_t *__restrict__ order, FrameTable ft, ImagePtrs out, LossParams lp,
-                        float *__restrict__ pose_partials, int per_frame, double *__restrict__ pose_grad,
-                        unsigned *__restrict__ counters, double *__restrict__ adam_state, gs_adam adam,
-                        float *__restrict__ T_cw, const int32_t *__restrict__ status) {
+                        float *__restrict__ pose_partials, int per_frame, const int32_t *__restrict__ status) {
     dep_wait();
     using SM = FusedSmem<TILE>;
     constexpr int NT = SM::NT;
@@ -67,17 +63,20 @@ __global__ void __launch_bounds__(TILE *TILE, MINB)
     float4 *s_c = s_b + BATCH;
     int4 *s_r = reinterpret_cast<int4 *>(s_c + BATCH);
     float4 *s_j = reinterpret_cast<float4 *>(s_r + BATCH);
-    df(*s_red)[6] = reinterpret_cast<df(*)[6]>(s_dyn);  // tail only
     __shared__ uint32_t s_wmax[NWARP];
     __shared__ df s_wdf[NWARP][6];
-    __shared__ int s_flag;
     // the forward's warp-cull ballot of every 32-entry group of the list (first
     // kCullGroups groups): the backward walks the same entries with the same
     // warp and reuses them instead of evaluating warp_block_may_hit again
     __shared__ uint32_t s_cull[NWARP][kCullGroups];
+    // the tile (heaviest first) and its list range are loaded alongside the
+    // status word instead of after it; the index is clamped because, with the
+    // status set, an earlier kernel of the iteration may have left `order`
+    // unwritten
+    const int gtile = order ? (int)min(order[blockIdx.x], (uint32_t)(ft.total_tiles - 1)) : (int)blockIdx.x;
+    const uint2 range = ranges[gtile];
     if (status[0] != 0) return;
 
-    const int gtile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;  // heaviest tiles first
     const int f = frame_of_tile(ft, gtile);
     const FrameDesc &fd = ft.f[f];
     const int lt = gtile - fd.tile_off;
@@ -91,7 +90,6 @@ __global__ void __launch_bounds__(TILE *TILE, MINB)
     const size_t pix = (size_t)fd.pix_off + (size_t)py * fd.W + px;
     const int HW = fd.W * fd.H;
     const size_t cbase = 3 * (size_t)fd.pix_off + (size_t)py * fd.W + px;
-    const uint2 range = ranges[gtile];
 
     // stages list entries [lo, hi) of the tile into shared memory
     auto stage = [&](int lo, int hi) {
@@ -246,28 +244,17 @@ __global__ void __launch_bounds__(TILE *TILE, MINB)
             }
         }
     }
-    // per-tile partial (double-float, fixed tree), then the last tile of the
-    // frame reduces all of the frame's partials into the FP64 pose gradient
+    // per-tile partial (double-float, fixed tree); the frame's partials are
+    // summed by the chained reduction launch
     float *part_f = pose_partials + (size_t)f * per_frame * 12;
-    __syncthreads();  // the tail may reuse the staging bytes
+    __syncthreads();
     cta_pose_partial(acc, part_f + (size_t)lt * 12, s_wdf);
-    if (pose_grad) {
-        last_cta_pose_reduce(part_f, per_frame, fd.tiles_x * fd.tiles_y, counters + f, pose_grad + 6 * f, s_red,
-                             &s_flag);
-        if (adam_state && s_flag) {  // this CTA holds the frame's pose gradient
-            __syncthreads();
-            if (warp == 0)
-                pose_adam_warp(adam_state + (size_t)f * GS_POSE_STATE_DOUBLES, pose_grad + 6 * f, T_cw + 12 * f,
-                               adam);
-        }
-    }
 }
 
 template <int TILE>
 cudaError_t launch_tile(const float4 *rec, const float4 *jac, const uint32_t *values, const uint2 *ranges,
                         const uint32_t *order, const FrameTable &ft, const ImagePtrs &out, const LossParams &lp,
-                        float *pp, int per_frame, double *pg, unsigned *cnt, double *adam_state, const gs_adam &adam,
-                        float *T_cw, const int32_t *status, bool dense, cudaStream_t s) {
+                        float *pp, int per_frame, const int32_t *status, bool dense, cudaStream_t s) {
     // raise the dynamic shared-memory limit once per device (a host-side
     // attribute; the first call happens outside any stream capture)
     static std::atomic<uint64_t> done{0};
@@ -287,7 +274,7 @@ cudaError_t launch_tile(const float4 *rec, const float4 *jac, const uint32_t *va
     }
     auto kernel = dense ? k_render_fused_pose<TILE, kMinbDense> : k_render_fused_pose<TILE, kMinb>;
     return launch_chained(kernel, dim3(ft.total_tiles), dim3(TILE * TILE), smem, s, rec, jac, values, ranges, order, ft,
-                          out, lp, pp, per_frame, pg, cnt, adam_state, adam, T_cw, status);
+                          out, lp, pp, per_frame, status);
 }
 
 }  // namespace
@@ -295,17 +282,16 @@ cudaError_t launch_tile(const float4 *rec, const float4 *jac, const uint32_t *va
 cudaError_t launch_render_fused_pose(const float *rec, const float *jac, const uint32_t *values,
                                      const uint32_t *ranges, const uint32_t *order, const FrameTable &ft,
                                      const ImagePtrs &out, const LossParams &lp, float *pose_partials, int per_frame,
-                                     double *pose_grad, unsigned *counters, double *adam_state, const gs_adam &adam,
-                                     float *T_cw, const int32_t *status, int n_records, cudaStream_t s) {
+                                     const int32_t *status, int n_records, cudaStream_t s) {
     if (ft.total_tiles == 0) return cudaSuccess;
     const float4 *r4 = reinterpret_cast<const float4 *>(rec);
     const float4 *j4 = reinterpret_cast<const float4 *>(jac);
     const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
     const bool dense = (long long)n_records >= (long long)kDenseRecordsPerTile * ft.total_tiles;
     switch (ft.tile) {
-        case 8: return launch_tile<8>(r4, j4, values, rg, order, ft, out, lp, pose_partials, per_frame, pose_grad, counters, adam_state, adam, T_cw, status, dense, s);
-        case 16: return launch_tile<16>(r4, j4, values, rg, order, ft, out, lp, pose_partials, per_frame, pose_grad, counters, adam_state, adam, T_cw, status, dense, s);
-        case 32: return launch_tile<32>(r4, j4, values, rg, order, ft, out, lp, pose_partials, per_frame, pose_grad, counters, adam_state, adam, T_cw, status, dense, s);
+        case 8: return launch_tile<8>(r4, j4, values, rg, order, ft, out, lp, pose_partials, per_frame, status, dense, s);
+        case 16: return launch_tile<16>(r4, j4, values, rg, order, ft, out, lp, pose_partials, per_frame, status, dense, s);
+        case 32: return launch_tile<32>(r4, j4, values, rg, order, ft, out, lp, pose_partials, per_frame, status, dense, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -438,10 +438,11 @@ class Tracker:
     def kernel_launches_per_iteration(self) -> int:
         """libgs kernels one iteration launches: the tile-counter clear, the
         projection (which also counts the pairs), the tile scan, fill and
-        per-tile sort; then either the tracking pass (forward, backward, pose
-        reduction and Adam step in one launch) or the forward, the backward
-        (with the pose reduction) and the Adam step. No memsets."""
-        return 5 + (1 if self.fused else 3)
+        per-tile sort; then either the tracking pass (forward and backward in
+        one launch) and the pose reduction with the Adam step (one chained
+        launch), or the forward, the backward (with the pose reduction) and
+        the Adam step. No memsets."""
+        return 5 + (2 if self.fused else 3)
 
     def _capture(self):
         """Capture all ``iters`` iterations of a frame in one CUDA graph."""
