@@ -70,15 +70,15 @@ FWD_FLOP_PER_CONTRIB = 26
 # workload, from one ncu capture of the current kernel
 # (profiles/k_render_fused_pose_track-640x480-300k.md, cold cache); None once
 # the kernel changes.
-FUSED_DRAM_BYTES_PER_LAUNCH = 16.348160e6 + 0
-# DRAM bytes (read + write) of one whole tracking iteration (its 6 kernels),
+FUSED_DRAM_BYTES_PER_LAUNCH = 16.321536e6 + 0
+# DRAM bytes (read + write) of one whole tracking iteration (its 7 kernels),
 # from one ncu capture with the caches carried over between kernels
 # (profiles/dram_iteration_track-640x480-300k.md); None once a kernel of the
 # iteration changes.
-DRAM_BYTES_PER_ITERATION = 0.513792e6 + 2.860544e6
+DRAM_BYTES_PER_ITERATION = 0.549888e6 + 2.811136e6
 # DRAM bytes of one k_render_fused_pose<16, 4> launch at 1200x680 on the 5M
 # Gaussians in 16-bit storage (ncu, cold cache); None for other builds.
-PREC16_FUSED_DRAM_BYTES_PER_LAUNCH = 104.520192e6 + 2.896640e6
+PREC16_FUSED_DRAM_BYTES_PER_LAUNCH = 105.175296e6 + 3.282944e6
 FP32_LANES_PER_SM = 128
 
 
