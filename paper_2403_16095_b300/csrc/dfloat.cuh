@@ -74,14 +74,15 @@ constexpr int kRedSlots = 256;
 // tree combines the slots (slot s takes slot s + stride, stride 128 down to 1).
 // The order depends only on K -- not on the number of threads running it -- so
 // every caller gets bit-identical results. Loads bypass L1 (the partials may
-// have been written by other CTAs of the same launch) and are issued four
-// partials at a time, so a slot waits for one L2 round trip per four partials
-// instead of one per partial; the adds keep their order. The tree runs through
+// have been written by other CTAs of the same launch) and are issued several
+// partials at a time, so a slot waits for one L2 round trip per kAhead
+// partials instead of one per partial (kAhead = 4 by default);
+// the adds keep their order, so kAhead changes no bits. The tree runs through
 // shared memory down to 32 slots, then in warp 0 by shuffles (same pairs, same
 // operand order). Needs blockDim.x >= 32 and a shared buffer of 256 x 6
 // double-floats.
+template <int kAhead = 4>
 __device__ __forceinline__ void reduce_pose_partials(const float *p, int K, double *out6, df (*s_red)[6]) {
-    constexpr int kAhead = 4;
     for (int s = threadIdx.x; s < kRedSlots; s += blockDim.x) {
         df acc[6];
 #pragma unroll

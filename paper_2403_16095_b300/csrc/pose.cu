@@ -53,10 +53,15 @@ __global__ void __launch_bounds__(kRedThreads)
     __shared__ df s_red[kRedSlots][6];
     if (status[0] != 0) return;
     const int f = blockIdx.x;
-    reduce_pose_partials(partials + (size_t)f * per_frame * 12, per_frame, pose_grad + (size_t)f * 6, s_red);
-    if (adam_state && threadIdx.x < 32)
-        pose_adam_warp(adam_state + (size_t)f * GS_POSE_STATE_DOUBLES, pose_grad + (size_t)f * 6, T_cw + (size_t)f * 12,
-                       ad);
+    double *st = adam_state ? adam_state + (size_t)f * GS_POSE_STATE_DOUBLES : nullptr;
+    // fetch the frame's Adam state (28 doubles, up to three 128-byte lines)
+    // into L1 while the partials are being summed
+    if (st && threadIdx.x < 3)
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(st + (threadIdx.x == 0 ? 0 : (threadIdx.x == 1 ? 14 : 27))));
+    // all partials of a slot in one round trip (K <= 8 x 256 per frame at 16x16
+    // tiles up to 2048x2048 pixels; longer frames take more rounds)
+    reduce_pose_partials<8>(partials + (size_t)f * per_frame * 12, per_frame, pose_grad + (size_t)f * 6, s_red);
+    if (st && threadIdx.x < 32) pose_adam_warp(st, pose_grad + (size_t)f * 6, T_cw + (size_t)f * 12, ad);
 }
 
 }  // namespace

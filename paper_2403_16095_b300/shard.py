@@ -55,6 +55,24 @@ def allreduce_gaussian_grads(grads: Dict[str, torch.Tensor], names: Optional[Seq
 PARAMS = ("means", "log_scales", "quats", "opacity_logit", "colors", "nu")
 
 
+def window_slice(cams, T_cw, target_color, target_depth, frames: Sequence[int]):
+    """The cameras, poses ([F*12]) and RGB-D targets of the listed frames of a
+    window, in that order. The window's images are planar and concatenated
+    frame after frame (colour [3][H_f][W_f] per frame), so frames of different
+    sizes are sliced by their pixel offsets."""
+    frames = list(frames)
+    T = T_cw.reshape(len(cams), 12)
+    sizes = [int(c.width) * int(c.height) for c in cams]
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    tc = target_color.reshape(-1)
+    td = target_depth.reshape(-1)
+    if not frames:
+        return [], T[:0].reshape(-1), tc[:0], td[:0]
+    return ([cams[f] for f in frames], T[frames].contiguous().reshape(-1),
+            torch.cat([tc[3 * offs[f]: 3 * offs[f + 1]] for f in frames]),
+            torch.cat([td[offs[f]: offs[f + 1]] for f in frames]))
+
+
 class ShardedWindow:
     """One rank's share of a keyframe window (Eq. 21): the frames
     ``frames_for_rank(len(cams), rank, world)`` of the window, rendered and
@@ -75,16 +93,8 @@ class ShardedWindow:
         from .raster import Rasterizer
         self.frames = frames_for_rank(len(cams), rank, world)
         self.rank, self.world, self.group = rank, world, group
-        self.cams = [cams[f] for f in self.frames]
-        T = T_cw.reshape(len(cams), 12)
-        self.T_cw = T[self.frames].contiguous().reshape(-1) if self.frames else T[:0].reshape(-1)
-        sizes = [int(c.width) * int(c.height) for c in cams]
-        offs = np.concatenate([[0], np.cumsum(sizes)])
-        tc = target_color.reshape(-1)
-        td = target_depth.reshape(-1)
-        self.target_color = (torch.cat([tc[3 * offs[f]: 3 * offs[f + 1]] for f in self.frames])
-                             if self.frames else tc[:0])
-        self.target_depth = (torch.cat([td[offs[f]: offs[f + 1]] for f in self.frames]) if self.frames else td[:0])
+        self.cams, self.T_cw, self.target_color, self.target_depth = window_slice(
+            cams, T_cw, target_color, target_depth, self.frames)
         w = dict(w_color=0.7, w_depth=0.25, w_unc=0.15, w_align=0.25) if loss_weights is None else dict(loss_weights)
         self.loss = dict(w, target_color=self.target_color, target_depth=self.target_depth)
         self.rast = (Rasterizer(self.cams, n_gaussians, tile=tile, mode=A.GS_MODE_FULL, capacity=capacity,

@@ -102,3 +102,36 @@ def test_two_rank_frame_sharded_sum_equals_single_process_sum():
     a, b = res[0][2], res[1][2]
     for k in PARAMS:
         assert np.array_equal(a[k], b[k])
+
+
+def test_window_slice_of_uneven_frames():
+    """A rank's share of a window of frames of different sizes: its cameras,
+    poses and the planar per-frame RGB-D targets, cut at each frame's pixel
+    offset, in the rank's frame order."""
+    from paper_2403_16095_b300.shard import window_slice
+    cams = [synth.Camera(w, h, 50.0, 50.0, w / 2, h / 2) for w, h in ((4, 3), (5, 2), (2, 2), (3, 3))]
+    sizes = [c.width * c.height for c in cams]
+    T = torch.arange(4 * 12, dtype=torch.float32).reshape(4, 3, 4)
+    tc = torch.cat([torch.full((3 * n,), float(f)) for f, n in enumerate(sizes)])
+    td = torch.cat([torch.full((n,), 10.0 + f) for f, n in enumerate(sizes)])
+    for frames in ([1, 3], [0, 2], [3], []):
+        c, Tr, tcr, tdr = window_slice(cams, T, tc, td, frames)
+        assert [x.width for x in c] == [cams[f].width for f in frames]
+        assert torch.equal(Tr, T[frames].reshape(-1) if frames else T[:0].reshape(-1))
+        assert torch.equal(tcr, torch.cat([torch.full((3 * sizes[f],), float(f)) for f in frames])
+                           if frames else tc[:0])
+        assert torch.equal(tdr, torch.cat([torch.full((sizes[f],), 10.0 + f) for f in frames]) if frames else td[:0])
+
+
+def test_rank_without_frames_contributes_zeros():
+    """With more ranks than keyframes, a rank that owns no frame builds no
+    rasterizer and its step writes zero gradients (then joins the all-reduce,
+    the identity in a single process)."""
+    from paper_2403_16095_b300.shard import ShardedWindow
+    cams = [synth.Camera(8, 6, 10.0, 10.0, 4.0, 3.0)] * 3
+    T = torch.zeros(3, 3, 4)
+    sw = ShardedWindow(cams, 5, T, torch.zeros(3 * 3 * 48), torch.zeros(3 * 48), rank=4, world=6)
+    assert sw.frames == [] and sw.rast is None and sw.pose_grads() == {} and sw.status() == (0, 0)
+    grads = {k: torch.ones(5, 3) for k in PARAMS}
+    sw.step(None, grads)
+    assert all(float(v.abs().sum()) == 0.0 for v in grads.values())
