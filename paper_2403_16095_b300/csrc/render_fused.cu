@@ -245,7 +245,9 @@ __global__ void __launch_bounds__(TILE *TILE, MINB)
         }
     }
     // per-tile partial (double-float, fixed tree); the frame's partials are
-    // summed by the chained reduction launch
+    // summed by the chained reduction launch. The barrier lets every warp
+    // finish its walk before the tile's sum (cta_pose_partial orders its own
+    // shared-memory exchange).
     float *part_f = pose_partials + (size_t)f * per_frame * 12;
     __syncthreads();
     cta_pose_partial(acc, part_f + (size_t)lt * 12, s_wdf);
