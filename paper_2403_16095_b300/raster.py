@@ -460,6 +460,38 @@ class Tracker:
         completed frame)."""
         return [e[0].elapsed_time(e[1]) for e in self.bwd_events if e is not None]
 
+    def stage_ms(self, target_color, target_depth, T_init) -> dict:
+        """Mean device time per iteration of each library call of a tracking
+        iteration, over one frame launched eagerly with CUDA events around every
+        call (the events break the kernel-to-kernel chaining of the graph, so
+        the stages add up to a little more than a graph-launched iteration):
+        "project_bin" (counter clear, projection with pair count, tile scan,
+        fill and sort) and "tracking_pass" (the pass, then the pose reduction
+        with the Adam step; fused=False: forward, backward and Adam)."""
+        self.set_frame(target_color, target_depth, T_init)
+        s = self.stream
+        s.wait_stream(torch.cuda.current_stream())
+        r = self.rast
+        marks = []
+        with torch.cuda.stream(s):
+            for _ in range(self.iters):
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                e[0].record(s)
+                r.project_bin(self.g, self.T_cw, s)
+                e[1].record(s)
+                if self.fused:
+                    r.fwd_bwd_pose(self.loss, stream=s, adam_state=self.state, adam=self.adam, T_cw=self.T_cw)
+                else:
+                    r.forward(self.target_depth, s)
+                    r.backward(obs_depth=self.target_depth, loss=self.loss, stream=s)
+                    A.gs_pose_adam_step(self.state, r.pose_grad, self.T_cw, 1, self.adam, r.status, s)
+                e[2].record(s)
+                marks.append(e)
+        s.synchronize()
+        n = len(marks)
+        return {"project_bin": sum(e[0].elapsed_time(e[1]) for e in marks) / n,
+                "tracking_pass": sum(e[1].elapsed_time(e[2]) for e in marks) / n}
+
     def set_frame(self, target_color: torch.Tensor, target_depth: torch.Tensor, T_init: torch.Tensor) -> None:
         self.target_color.copy_(target_color.reshape(-1), non_blocking=True)
         self.target_depth.copy_(target_depth.reshape(-1), non_blocking=True)
