@@ -429,8 +429,8 @@ def run_ours(a):
             "avg_launch_ms": bwd_avg_ms, "launches": len(bwd_ms),
             "launch_timing": f"CUDA events around the launch on iterations 0, {TIMING_EVERY}, ... of every timed frame"}
     bwd_share = bwd_avg_ms * ITERS * len(step_ms) / sum(step_ms)
-    # per-stage device time of an iteration, from one eager frame after the
-    # timed region (events around each library call)
+    # per-stage device time of an iteration, from one frame after the timed
+    # region, captured with an event node around each library call
     f_last = my_frames[a.warmup + a.steps - 1]
     stage_ms = tr.stage_ms(tcol[f_last], tdep[f_last], starts_t[f_last])
 
@@ -467,7 +467,7 @@ def run_ours(a):
                        "ms_per_iteration": total_ms / (a.steps * ITERS), "wall_s": wall,
                        "pairs_per_iteration": int(tr.rast.read_status()[1]),
                        "contributions_per_iteration": E, "bwd_share_of_step": bwd_share,
-                       "stage_ms_eager": stage_ms},
+                       "stage_ms": stage_ms},
             "roofline": roof, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "context": "paper: 7.89 ms x 15 tracking iterations on an RTX 4090 (Table 5, Replica office-0)"}
     print(json.dumps(line), flush=True)

@@ -462,20 +462,20 @@ class Tracker:
 
     def stage_ms(self, target_color, target_depth, T_init) -> dict:
         """Mean device time per iteration of each library call of a tracking
-        iteration, over one frame launched eagerly with CUDA events around every
-        call (the events break the kernel-to-kernel chaining of the graph, so
-        the stages add up to a little more than a graph-launched iteration):
+        iteration, over one frame captured in a CUDA graph with an event node
+        around every call (events break the kernel-to-kernel chaining, so the
+        stages add up to a little more than an iteration of the plain graph):
         "project_bin" (counter clear, projection with pair count, tile scan,
         fill and sort) and "tracking_pass" (the pass, then the pose reduction
         with the Adam step; fused=False: forward, backward and Adam)."""
+        marks = [[torch.cuda.Event(enable_timing=True, external=True) for _ in range(3)]
+                 for _ in range(self.iters)]
+        r, s = self.rast, self.stream
         self.set_frame(target_color, target_depth, T_init)
-        s = self.stream
         s.wait_stream(torch.cuda.current_stream())
-        r = self.rast
-        marks = []
-        with torch.cuda.stream(s):
-            for _ in range(self.iters):
-                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=s):
+            for e in marks:
                 e[0].record(s)
                 r.project_bin(self.g, self.T_cw, s)
                 e[1].record(s)
@@ -486,7 +486,10 @@ class Tracker:
                     r.backward(obs_depth=self.target_depth, loss=self.loss, stream=s)
                     A.gs_pose_adam_step(self.state, r.pose_grad, self.T_cw, 1, self.adam, r.status, s)
                 e[2].record(s)
-                marks.append(e)
+        self.set_frame(target_color, target_depth, T_init)
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            graph.replay()
         s.synchronize()
         n = len(marks)
         return {"project_bin": sum(e[0].elapsed_time(e[1]) for e in marks) / n,
