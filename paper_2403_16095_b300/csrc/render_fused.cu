@@ -181,11 +181,19 @@ __global__ void __launch_bounds__(TILE *TILE, MINB)
 
     // ---------------------------------------------------------- backward
     const uint32_t warp_last = __reduce_max_sync(0xffffffffu, my_last);
-    if (lane == 0) s_wmax[warp] = warp_last;
-    __syncthreads();
-    uint32_t block_last = range.x;
+    // A list of at most one batch is still staged whole (nothing is restaged
+    // below), so each warp walks back from its own last entry without waiting
+    // for the others' forwards. Longer lists restage batch by batch, with every
+    // warp, from the CTA's last entry.
+    const bool one_batch = range.y - range.x <= (uint32_t)BATCH;
+    uint32_t block_last = warp_last;
+    if (!one_batch) {
+        if (lane == 0) s_wmax[warp] = warp_last;
+        __syncthreads();
+        block_last = range.x;
 #pragma unroll
-    for (int w = 0; w < NWARP; ++w) block_last = max(block_last, s_wmax[w]);
+        for (int w = 0; w < NWARP; ++w) block_last = max(block_last, s_wmax[w]);
+    }
 
     float GS = 0.f;
     float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
