@@ -196,6 +196,57 @@ def test_fused_tracking_pass_dense_build_equals_forward_then_backward():
     assert float(res[1][1].abs().max()) > 0
 
 
+@pytest.mark.parametrize("n", [255, 256, 257, 511, 512, 513])
+def test_fused_tracking_pass_at_staging_batch_boundaries(n):
+    """Every tile list exactly n entries long, around one and two 256-entry
+    staging batches: n broad, faint Gaussians in front of a 64x48 camera, each
+    covering all 12 tiles and blended by the central pixels without saturating
+    them. A list of one batch is walked back by each warp on its own; a longer
+    one is restaged batch by batch. Both equal gs_render_fwd + gs_render_bwd
+    bit for bit (tracking channels and FP64 pose gradient)."""
+    from paper_2403_16095_b300 import Rasterizer
+    from paper_2403_16095_b300 import _abi as A
+    rng = np.random.default_rng(1400 + n)
+    z = rng.uniform(2.5, 3.5, n)
+    means = np.stack([rng.uniform(-0.05, 0.05, n) * z, rng.uniform(-0.05, 0.05, n) * z, z], 1)
+    q = rng.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    sc = synth.Scene(means.astype(np.float32), np.full((n, 3), math.log(0.8), np.float32), q.astype(np.float32),
+                     rng.normal(-4.6, 0.15, n).astype(np.float32), rng.uniform(0, 1, (n, 3)).astype(np.float32),
+                     rng.uniform(0, 0.1, n).astype(np.float32))
+    cam = synth.Camera(64, 48, 60.0, 60.0, 32.0, 24.0)
+    T = synth.jitter_pose(np.c_[np.eye(3), np.zeros(3)], seed=n)
+    g = to_gpu_gaussians(sc)
+    tc = torch.rand(3 * 64 * 48, device="cuda", generator=torch.Generator("cuda").manual_seed(n))
+    td = torch.rand(64 * 48, device="cuda", generator=torch.Generator("cuda").manual_seed(n + 1)) + 2.5
+    loss = dict(w_color=0.2, w_depth=1.0, unc_tau=0.025, target_color=tc, target_depth=td)
+    res = []
+    for fused in (False, True):
+        r = Rasterizer([cam], n, tile=16, mode=A.GS_MODE_POSE, channels="track")
+        r.render(g, poses_gpu(T), td)
+        lens = (r.ranges[1::2] - r.ranges[0::2]).cpu()
+        assert bool(torch.all(lens == n)), lens
+        for k in r.img:
+            r.img[k].fill_(-1 if r.img[k].dtype == torch.int32 else float("nan"))
+        r.pose_grad.zero_()
+        if fused:
+            r.fwd_bwd_pose(loss, images=True)
+        else:
+            r.forward(td)
+            r.backward(obs_depth=td, loss=loss)
+        torch.cuda.synchronize()
+        assert r.read_status()[0] == 0
+        res.append(({k: v.clone() for k, v in r.img.items()}, r.pose_grad.clone()))
+    for k in res[0][0]:
+        assert torch.equal(res[0][0][k], res[1][0][k]), k
+    assert torch.equal(res[0][1], res[1][1])
+    # the central pixel blends every entry of its tile (tile 6 of the 4x3
+    # grid), so its warps walk the whole list back
+    assert int(res[1][0]["n_last"][24 * 64 + 32]) == int(r.ranges[2 * 6 + 1])
+    assert float(res[1][0]["T_final"].min()) > 1e-3
+    assert float(res[1][1].abs().max()) > 0
+
+
 def test_tracker_fused_equals_unfused(room_small):
     from paper_2403_16095_b300 import Tracker
     sc, cam, poses = room_small
