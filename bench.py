@@ -70,15 +70,18 @@ FWD_FLOP_PER_CONTRIB = 26
 # workload, from one ncu capture of the current kernel
 # (profiles/k_render_fused_pose_track-640x480-300k.md, cold cache); None once
 # the kernel changes.
-FUSED_DRAM_BYTES_PER_LAUNCH = 16.321536e6 + 0
+FUSED_DRAM_BYTES_PER_LAUNCH = 16.32256e6 + 0
 # DRAM bytes (read + write) of one whole tracking iteration (its 7 kernels),
 # from one ncu capture with the caches carried over between kernels
 # (profiles/dram_iteration_track-640x480-300k.md); None once a kernel of the
 # iteration changes.
-DRAM_BYTES_PER_ITERATION = 0.549888e6 + 2.811136e6
+DRAM_BYTES_PER_ITERATION = 0.549120e6 + 2.989056e6
 # DRAM bytes of one k_render_fused_pose<16, 4> launch at 1200x680 on the 5M
-# Gaussians in 16-bit storage (ncu, cold cache); None for other builds.
-PREC16_FUSED_DRAM_BYTES_PER_LAUNCH = 105.175296e6 + 3.282944e6
+# Gaussians, 16-bit storage (records in Morton order) and FP32 storage
+# (generator's order), ncu, cold cache
+# (profiles/dram_fused_precision-1200x680-5M-room.md); None for other builds.
+PREC16_FUSED_DRAM_BYTES_PER_LAUNCH = 105.288192e6 + 3.363072e6
+PREC32_FUSED_DRAM_BYTES_PER_LAUNCH = 176.138752e6 + 6.345984e6
 FP32_LANES_PER_SM = 128
 
 
@@ -740,7 +743,8 @@ def run_precision(a):
     launch_ms = statistics.mean(bwd)
     dense = g32.n >= 800 * tr.rast.n_tiles
     achieved = E * flop / (launch_ms * 1e-3) / 1e12
-    traffic = PREC16_FUSED_DRAM_BYTES_PER_LAUNCH if (packed and dense and a.tile == 16) else None
+    traffic = ((PREC16_FUSED_DRAM_BYTES_PER_LAUNCH if packed else PREC32_FUSED_DRAM_BYTES_PER_LAUNCH)
+               if (dense and a.tile == 16) else None)
     roof = {"kernel": f"k_render_fused_pose<{a.tile}, {4 if dense else 3}>", "bound": "alu", "achieved": achieved,
             "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch, cold cache",
