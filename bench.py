@@ -127,7 +127,13 @@ def _args():
     p.add_argument("--no-graph", action="store_true", help="mapping/uneven: launch the step eagerly")
     p.add_argument("--storage", choices=("16bit", "fp32"), default="16bit",
                    help="precision: the Gaussians in 16-bit storage or in plain FP32")
-    return p.parse_args()
+    p.add_argument("--order", choices=("morton", "given"), default=None,
+                   help="the map in Morton order (gs_spatial_order, once before timing) or in the "
+                        "generator's order (default: given for track, morton otherwise)")
+    a = p.parse_args()
+    if a.order is None:
+        a.order = "given" if a.workload == "track" else "morton"
+    return a
 
 
 def _dist():
@@ -299,6 +305,8 @@ def run_ours(a):
     n_frames = len(gt)
     g = Gaussians(*(torch.from_numpy(np.ascontiguousarray(getattr(sc, k))).to(dev)
                     for k in ("means", "log_scales", "quats", "opacity_logit", "colors", "nu")))
+    if a.order == "morton":
+        g = morton_ordered(g, dev)
     my_frames = [(rank + k * ws) % n_frames for k in range(a.warmup + a.steps)]
     # targets: renders at the ground-truth poses of the frames this rank uses
     # (device-resident inputs of the timed region)
@@ -464,7 +472,7 @@ def run_ours(a):
     line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "width": 640, "height": 480, "gaussians": int(g.n),
+            "config": {"workload": WORKLOAD, "width": 640, "height": 480, "gaussians": int(g.n), "map_order": a.order,
                        "iters_per_frame": ITERS, "step": "one tracked frame (30 iterations)", "tile": a.tile,
                        "l2": "flushed between steps (512 MB write, untimed)", "parallelism": f"replicas x{ws}",
                        "ms_per_iteration": total_ms / (a.steps * ITERS), "wall_s": wall,
@@ -531,6 +539,8 @@ def run_batch(a):
     pert["means"] += rng.normal(0, 0.01, pert["means"].shape).astype(np.float32)
     pert["colors"] = np.clip(pert["colors"] + rng.normal(0, 0.05, pert["colors"].shape), 0, 1).astype(np.float32)
     g = Gaussians(*(torch.from_numpy(pert[k]).to(dev) for k in names))
+    if a.order == "morton":
+        g = morton_ordered(g, dev)
     # the mapping weights of Sec. 4 (Replica): omega_1 colour 0.7, omega_3 geo 0.25,
     # omega_4 align 0.25, omega_6 var 0.15 (SSIM and L_iso are off the rasterizer)
     loss_w = dict(w_color=0.7, w_depth=0.25, w_unc=0.15, w_align=0.25)
@@ -653,7 +663,8 @@ def run_batch(a):
             "scaling": "strong" if a.workload == "mapping" else "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{a.workload}-{F}frames-{g.n // 1000}k", "frames": F, "pixels": n_pix,
-                       "gaussians": int(g.n), "tile": tile, "batch": batch or 512, "sched": sched_name,
+                       "gaussians": int(g.n), "map_order": a.order, "tile": tile, "batch": batch or 512,
+                       "sched": sched_name,
                        "launch": "CUDA graph replay" if graph is not None else "eager",
                        "parallelism": f"keyframe shards x{ws}" if a.workload == "mapping" else "single batch",
                        "autotune_ms": tune, "l2": "flushed between steps (512 MB write, untimed)",
@@ -669,6 +680,23 @@ def run_batch(a):
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def morton_ordered(g, dev):
+    """A copy of the FP32 map g with its Gaussians in Morton order of their
+    means (gs_spatial_order), gathered once before any timed region."""
+    import torch
+    from paper_2403_16095_b300 import Gaussians
+    from paper_2403_16095_b300 import _abi as A
+    perm = torch.empty(g.n, dtype=torch.int32, device=dev)
+    ws_sort = torch.empty(max(1, A.gs_spatial_order_workspace_size(g.n)), dtype=torch.uint8, device=dev)
+    st = torch.zeros(4, dtype=torch.int32, device=dev)
+    A.gs_spatial_order(g.means, perm, ws_sort, st)
+    if int(st[0]) != 0:
+        raise RuntimeError("gs_spatial_order set the device status")
+    idx = perm.long()
+    names = ("means", "log_scales", "quats", "opacity_logit", "colors", "nu")
+    return Gaussians(*(getattr(g, k)[idx].contiguous() for k in names))
 
 
 def run_precision(a):
@@ -693,7 +721,13 @@ def run_precision(a):
     names = ("means", "log_scales", "quats", "opacity_logit", "colors", "nu")
     g32 = Gaussians(*(torch.from_numpy(np.ascontiguousarray(getattr(sc, k), np.float32)).to(dev) for k in names))
     packed = a.storage == "16bit"
-    gt = pack_bf16(g32, spatial=True) if packed else g32
+    morton = a.order == "morton"
+    if packed:
+        gt = pack_bf16(g32, spatial=morton)
+    elif morton:  # the same record order as the 16-bit form
+        gt = morton_ordered(g32, dev)
+    else:
+        gt = g32
     frames = list(range(a.warmup + a.steps))
     n_pose = len(poses)
     # targets: the FP32 field rendered at the true poses (device-resident inputs)
@@ -743,7 +777,8 @@ def run_precision(a):
     launch_ms = statistics.mean(bwd)
     dense = g32.n >= 800 * tr.rast.n_tiles
     achieved = E * flop / (launch_ms * 1e-3) / 1e12
-    traffic = ((PREC16_FUSED_DRAM_BYTES_PER_LAUNCH if packed else PREC32_FUSED_DRAM_BYTES_PER_LAUNCH)
+    traffic = ({("16bit", "morton"): PREC16_FUSED_DRAM_BYTES_PER_LAUNCH,
+                ("fp32", "given"): PREC32_FUSED_DRAM_BYTES_PER_LAUNCH}.get((a.storage, a.order))
                if (dense and a.tile == 16) else None)
     roof = {"kernel": f"k_render_fused_pose<{a.tile}, {4 if dense else 3}>", "bound": "alu", "achieved": achieved,
             "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
@@ -771,6 +806,7 @@ def run_precision(a):
             "vs_baseline": None, "dtype": "bf16 storage, f32 compute" if packed else "f32", "data": "synthetic",
             "config": {"workload": f"precision-1200x680-5M-room-{a.storage}", "gaussians": int(g32.n),
                        "tile": a.tile, "iters_per_frame": ITERS, "frames": len(set(f % n_pose for f in frames[a.warmup:])),
+                       "map_order": a.order,
                        "l2": "flushed between steps (512 MB write, untimed)",
                        "ms_per_iteration": total_ms / (a.steps * ITERS),
                        "pairs_per_iteration": int(tr.rast.read_status()[1])},
