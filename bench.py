@@ -77,11 +77,12 @@ FUSED_DRAM_BYTES_PER_LAUNCH = 16.32256e6 + 0
 # iteration changes.
 DRAM_BYTES_PER_ITERATION = 0.549120e6 + 2.989056e6
 # DRAM bytes of one k_render_fused_pose<16, 4> launch at 1200x680 on the 5M
-# Gaussians, 16-bit storage (records in Morton order) and FP32 storage
-# (generator's order), ncu, cold cache
+# Gaussians: 16-bit storage and FP32 storage with the map in Morton order, and
+# FP32 storage in the generator's order; ncu, cold cache
 # (profiles/dram_fused_precision-1200x680-5M-room.md); None for other builds.
 PREC16_FUSED_DRAM_BYTES_PER_LAUNCH = 105.288192e6 + 3.363072e6
-PREC32_FUSED_DRAM_BYTES_PER_LAUNCH = 176.138752e6 + 6.345984e6
+PREC32_FUSED_DRAM_BYTES_PER_LAUNCH = 105.395712e6 + 3.413248e6
+PREC32_GIVEN_ORDER_FUSED_DRAM_BYTES_PER_LAUNCH = 176.138752e6 + 6.345984e6
 FP32_LANES_PER_SM = 128
 
 
@@ -778,7 +779,8 @@ def run_precision(a):
     dense = g32.n >= 800 * tr.rast.n_tiles
     achieved = E * flop / (launch_ms * 1e-3) / 1e12
     traffic = ({("16bit", "morton"): PREC16_FUSED_DRAM_BYTES_PER_LAUNCH,
-                ("fp32", "given"): PREC32_FUSED_DRAM_BYTES_PER_LAUNCH}.get((a.storage, a.order))
+                ("fp32", "morton"): PREC32_FUSED_DRAM_BYTES_PER_LAUNCH,
+                ("fp32", "given"): PREC32_GIVEN_ORDER_FUSED_DRAM_BYTES_PER_LAUNCH}.get((a.storage, a.order))
                if (dense and a.tile == 16) else None)
     roof = {"kernel": f"k_render_fused_pose<{a.tile}, {4 if dense else 3}>", "bound": "alu", "achieved": achieved,
             "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
