@@ -14,14 +14,18 @@ constexpr float kAlphaMin = 1.f / 255.f; // entries below are skipped
 constexpr float kAlphaMax = 0.99f;      // alpha clamp
 constexpr float kQMax = 9.f;            // footprint: q <= 9 (3 sigma)
 
-// inclusive pixel rect test: x0 <= px <= x1 and y0 <= py <= y1
-__device__ __forceinline__ bool in_rect(int px, int py, int4 rc) {
-    return (unsigned)(px - rc.x) <= (unsigned)(rc.z - rc.x) && (unsigned)(py - rc.y) <= (unsigned)(rc.w - rc.y);
-}
-
 // a = (mx, my, A, B), b = (C, opacity, z, nu). Returns false if the Gaussian does
 // not contribute (q > 9 or alpha < 1/255); otherwise G = exp(-q/2),
 // sg = opacity * G and alpha = min(0.99, sg).
+//
+// A Gaussian is in a pixel's list iff the pixel lies in its rect and q <= 9.
+// The blend kernels test only q <= 9 on the entries of the pixel's tile list:
+// the rect contains the q <= 9 ellipse, since over a pixel offset (dx, dy)
+// q >= dx^2 / S_xx >= dx^2 / lambda_max for the dilated 2D covariance S (and
+// likewise in y), while the rect's half-width r = ceil(3 sqrt(lambda_max)).
+// In FP32 the two tests can disagree only where q is within ~1e-6 (relative)
+// of 9 and r within as much of 3 sqrt(S_xx), a threshold decision like the
+// FP32 footprint test itself.
 __device__ __forceinline__ bool eval_alpha(float pxc, float pyc, const float4 &a, const float4 &b, float &dx,
                                            float &dy, float &G, float &sg, float &alpha) {
     dx = __fsub_rn(pxc, a.x);
@@ -70,6 +74,33 @@ __device__ __forceinline__ bool warp_block_may_hit(const float4 &a, const float4
         qmin = fminf(qmin, q_slack(A, B, C, ex, ey));
     }
     return !(qmin > kQMax + 1e-3f);  // NaN-safe: keep on doubt
+}
+
+// Backward of one blended entry under the colour + depth loss (adjoint of
+// Eq. 3-6, walking the list back to front). On entry T is the transmittance
+// behind the entry and GS the sum of w_i (g . f_i) over the entries behind it;
+// on return T is the transmittance in front of it and GS includes it. th gets
+// the loss gradient of the entry's (mean2d.x, mean2d.y, A, B, C, z), w its
+// blend weight and dal dL/dalpha. Every operation is explicitly rounded, so
+// that the tracking pass and the separate backward produce the same bits.
+__device__ __forceinline__ void entry_grad_cd(float alpha, float sg, float dx, float dy, const float4 &a,
+                                              const float4 &b, const float4 &c, float gc0, float gc1, float gc2,
+                                              float gD, float &T, float &GS, float (&th)[6], float &w, float &dal) {
+    const float one_m = __fsub_rn(1.f, alpha);
+    const float inv = __fdividef(1.f, one_m);
+    T = __fmul_rn(T, inv);
+    w = __fmul_rn(alpha, T);
+    const float dot = __fmaf_rn(gD, b.z, __fmaf_rn(gc2, c.z, __fmaf_rn(gc1, c.y, __fmul_rn(gc0, c.x))));
+    dal = __fmaf_rn(T, dot, -__fmul_rn(inv, GS));
+    GS = __fmaf_rn(w, dot, GS);
+    const float dpow = sg >= kAlphaMax ? 0.f : __fmul_rn(dal, alpha);
+    const float hp = __fmul_rn(-0.5f, dpow);
+    th[0] = __fmul_rn(dpow, __fmaf_rn(a.z, dx, __fmul_rn(a.w, dy)));
+    th[1] = __fmul_rn(dpow, __fmaf_rn(a.w, dx, __fmul_rn(b.x, dy)));
+    th[2] = __fmul_rn(hp, __fmul_rn(dx, dx));
+    th[3] = __fmul_rn(-dpow, __fmul_rn(dx, dy));
+    th[4] = __fmul_rn(hp, __fmul_rn(dy, dy));
+    th[5] = __fmul_rn(w, gD);
 }
 
 // acc[c] += th[r] * J[6r + c] for the 6x6 pose Jacobian J of one record

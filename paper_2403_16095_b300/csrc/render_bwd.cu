@@ -47,8 +47,12 @@ struct BwdSmem {
     static constexpr int BATCH = NT < 256 ? NT : (POSE ? 256 : FULL_BATCH);
     static constexpr size_t kEntry = 4 * sizeof(float4) + sizeof(uint32_t) + (POSE ? 9 * sizeof(float4) : 0);
     static constexpr size_t kStage = BATCH * kEntry;
+    // FULL mode: each thread's rarely used loss terms (opacity, nu and median
+    // gradients, median position), kept here instead of in registers; at the
+    // 48-register cap of the 16x16 build this keeps the walk from spilling
+    static constexpr size_t kLoss = POSE ? 0 : NT * sizeof(float4);
     static constexpr size_t kRed = POSE ? sizeof(df) * kRedSlots * 6 : 0;
-    static constexpr size_t bytes = kStage > kRed ? kStage : kRed;
+    static constexpr size_t bytes = kStage + kLoss > kRed ? kStage + kLoss : kRed;
 };
 
 // FULL mode: an entry blended by at most kDirectLanes lanes of the warp is
@@ -94,6 +98,7 @@ __device__ __forceinline__ void bwd_tile(const int gtile, const float4 *__restri
     int4 *s_r = reinterpret_cast<int4 *>(s_c + BATCH);
     float4 *s_j = reinterpret_cast<float4 *>(s_r + BATCH);                   // POSE only
     uint32_t *s_idx = reinterpret_cast<uint32_t *>(s_j + (POSE ? 9 * BATCH : 0));
+    float4 *s_gx = reinterpret_cast<float4 *>(s_dyn + SM::kStage);           // FULL only
     df(*s_red)[6] = reinterpret_cast<df(*)[6]>(s_dyn);                       // tail only
     uint32_t *s_wmax = sh.wmax;
 
@@ -153,6 +158,7 @@ __device__ __forceinline__ void bwd_tile(const int gtile, const float4 *__restri
         }
         if (gM != 0.f) my_med = fwd.median_pos[pix];
     }
+    if (!POSE && !CD) s_gx[tid] = make_float4(gO, gN, gM, __int_as_float(my_med));
     if (CD) {  // the launcher picked this variant because these are zero
         gO = 0.f;
         gU = 0.f;
@@ -201,21 +207,38 @@ __device__ __forceinline__ void bwd_tile(const int gtile, const float4 *__restri
             mask &= ~(1u << bit);
             const int k = g0 + bit;
             const int j = bstart + k;
-            const int4 rc = s_r[k];
             const float4 a = s_a[k];
             const float4 b = s_b[k];
             float dx = 0.f, dy = 0.f, G = 0.f, sg = 0.f, alpha = 0.f;
-            bool act = (uint32_t)j < my_last && in_rect(px, py, rc);
+            bool act = (uint32_t)j < my_last;
             if (act) act = eval_alpha(pxc, pyc, a, b, dx, dy, G, sg, alpha);
             float v[11];
-            if (act) {
+            if (act && CD) {  // colour + depth only: the tracking pass's arithmetic, bit for bit
+                float th[6], w, dal;
+                entry_grad_cd(alpha, sg, dx, dy, a, b, s_c[k], gc0, gc1, gc2, gD, T, GS, th, w, dal);
+                v[G_MX] = th[0];
+                v[G_MY] = th[1];
+                v[G_CA] = th[2];
+                v[G_CB] = th[3];
+                v[G_CC] = th[4];
+                v[G_Z] = th[5];
+                if (!POSE) {
+                    v[G_OP] = sg >= kAlphaMax ? 0.f : dal * G;
+                    v[G_NU] = 0.f;  // nu is not in this loss
+                    v[G_R] = w * gc0;
+                    v[G_G] = w * gc1;
+                    v[G_B] = w * gc2;
+                }
+            } else if (act) {
                 const float one_m = __fsub_rn(1.f, alpha);
                 const float inv = __fdividef(1.f, one_m);
                 T = T * inv;  // transmittance in front of entry j
                 const float w = alpha * T;
                 const float4 c = s_c[k];
+                // (gO, gN, gM, median position): from shared memory in FULL mode
+                const float4 gx = POSE ? make_float4(gO, gN, gM, __int_as_float(my_med)) : s_gx[tid];
                 const float dz = b.z - Dp;
-                const float dot = gc0 * c.x + gc1 * c.y + gc2 * c.z + gD * b.z + gO + gU * dz * dz + gN * b.w;
+                const float dot = gc0 * c.x + gc1 * c.y + gc2 * c.z + gD * b.z + gx.x + gU * dz * dz + gx.y * b.w;
                 const float dal = T * dot - inv * GS;
                 GS = fmaf(w, dot, GS);
                 const bool clamped = sg >= kAlphaMax;
@@ -226,10 +249,10 @@ __device__ __forceinline__ void bwd_tile(const int gtile, const float4 *__restri
                 v[G_CB] = -dpow * dx * dy;
                 v[G_CC] = -0.5f * dpow * dy * dy;
                 v[G_Z] = w * (gD + 2.f * gU * dz);
-                if (!CD && j == my_med) v[G_Z] += gM;  // D_median = z of the median entry (Eq. 7)
+                if (j == __float_as_int(gx.w)) v[G_Z] += gx.z;  // D_median = z of the median entry (Eq. 7)
                 if (!POSE) {
                     v[G_OP] = clamped ? 0.f : dal * G;
-                    v[G_NU] = w * gN;
+                    v[G_NU] = w * gx.y;
                     v[G_R] = w * gc0;
                     v[G_G] = w * gc1;
                     v[G_B] = w * gc2;

@@ -129,8 +129,6 @@ __global__ void __launch_bounds__(TILE *TILE, MINB)
                     const int k = g0 + __ffs(mask) - 1;
                     mask &= mask - 1;
                     if (done) continue;
-                    const int4 rc = s_r[k];
-                    if (!in_rect(px, py, rc)) continue;
                     const float4 a = s_a[k];
                     const float4 b = s_b[k];
                     float dx, dy, G, sg, alpha;
@@ -227,26 +225,14 @@ __global__ void __launch_bounds__(TILE *TILE, MINB)
                 mask &= ~(1u << bit);
                 const int k = g0 + bit;
                 const int j = bstart + k;
-                const int4 rc = s_r[k];
                 const float4 a = s_a[k];
                 const float4 b = s_b[k];
                 float dx = 0.f, dy = 0.f, G = 0.f, sg = 0.f, alpha = 0.f;
-                bool act = (uint32_t)j < my_last && in_rect(px, py, rc);
+                bool act = (uint32_t)j < my_last;
                 if (act) act = eval_alpha(pxc, pyc, a, b, dx, dy, G, sg, alpha);
                 if (act) {
-                    const float one_m = __fsub_rn(1.f, alpha);
-                    const float inv = __fdividef(1.f, one_m);
-                    T = T * inv;  // transmittance in front of entry j
-                    const float w = alpha * T;
-                    const float4 c = s_c[k];
-                    const float dot = gc0 * c.x + gc1 * c.y + gc2 * c.z + gD * b.z;
-                    const float dal = T * dot - inv * GS;
-                    GS = fmaf(w, dot, GS);
-                    const bool clamped = sg >= kAlphaMax;
-                    const float dpow = clamped ? 0.f : dal * alpha;
-                    const float th[6] = {dpow * (a.z * dx + a.w * dy), dpow * (a.w * dx + b.x * dy),
-                                         -0.5f * dpow * dx * dx,       -dpow * dx * dy,
-                                         -0.5f * dpow * dy * dy,       w * gD};
+                    float th[6], w, dal;
+                    entry_grad_cd(alpha, sg, dx, dy, a, b, s_c[k], gc0, gc1, gc2, gD, T, GS, th, w, dal);
                     pose_contract(acc, th, &s_j[k * 9]);
                 }
             }

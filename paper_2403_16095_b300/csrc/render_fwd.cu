@@ -80,8 +80,6 @@ __device__ __forceinline__ void fwd_tile(const int gtile, const float4 *__restri
                     const int k = g0 + __ffs(mask) - 1;
                     mask &= mask - 1;
                     if (done) continue;
-                    const int4 rc = s_r[k];
-                    if (!in_rect(px, py, rc)) continue;
                     const float4 a = s_a[k];
                     const float4 b = s_b[k];
                     float dx, dy, G, sg, alpha;

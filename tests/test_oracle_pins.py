@@ -140,6 +140,38 @@ def test_projection_of_rotated_anisotropic_gaussian():
     np.testing.assert_allclose(pr["conic"][0], [inv[0, 0], inv[0, 1], inv[1, 1]], rtol=1e-12)
 
 
+def test_footprint_ellipse_lies_inside_the_pixel_rect():
+    """Footprint (Eq. 2 radius and rect): every pixel with q <= 9 lies in the
+    Gaussian's pixel rect, so a pixel's list is decided by q alone within the
+    tiles the rect covers. Checked by brute force over a margin of 3 pixels
+    around every rect, on anisotropic, rotated Gaussians, including ones whose
+    projection Jacobian is clamped at the image edge; q is evaluated both in
+    FP64 and in FP32 from the FP32-rounded centre and conic, as the kernels
+    do."""
+    scenes = [synth.tiny_scene(n=400, seed=1401)[0], synth.fd_scene(n=60, seed=1402, n_edge=8)[0]]
+    cams = [synth.Camera(128, 96, 100.0, 100.0, 64.0, 48.0), synth.Camera(64, 48, 60.0, 60.0, 32.0, 24.0)]
+    checked = 0
+    for sc, cam in zip(scenes, cams):
+        pr = oracle.project(sc, cam, _ident())
+        for g in np.flatnonzero(pr["valid"]):
+            x0, y0, x1, y1 = pr["rect"][g]
+            mx, my = pr["mean2d"][g]
+            A, B, C = pr["conic"][g]
+            xs = np.arange(max(0, x0 - 3), min(cam.width, x1 + 4))
+            ys = np.arange(max(0, y0 - 3), min(cam.height, y1 + 4))
+            px, py = np.meshgrid(xs, ys)
+            inside = (px >= x0) & (px <= x1) & (py >= y0) & (py <= y1)
+            dx, dy = px + 0.5 - mx, py + 0.5 - my
+            q64 = A * dx * dx + 2 * B * dx * dy + C * dy * dy
+            f = np.float32
+            dx32, dy32 = f(px + 0.5) - f(mx), f(py + 0.5) - f(my)
+            q32 = f(A) * dx32 * dx32 + f(2) * f(B) * dx32 * dy32 + f(C) * dy32 * dy32
+            assert not np.any((q64 <= 9.0) & ~inside), g
+            assert not np.any((q32 <= f(9.0)) & ~inside), g
+            checked += int(np.count_nonzero(q64 <= 9.0))
+    assert checked > 10_000
+
+
 # ----------------------------------------------------------- invariants (P4)
 @pytest.fixture(scope="module")
 def tiny():
