@@ -16,7 +16,9 @@ constexpr float kQMax = 9.f;            // footprint: q <= 9 (3 sigma)
 
 // a = (mx, my, A, B), b = (C, opacity, z, nu). Returns false if the Gaussian does
 // not contribute (q > 9 or alpha < 1/255); otherwise G = exp(-q/2),
-// sg = opacity * G and alpha = min(0.99, sg).
+// sg = opacity * G and alpha = min(0.99, sg). The exponential is taken for
+// every lane, with no exit at q > 9, so that a warp's lanes stay on one path
+// (a NaN q fails the q test whatever alpha becomes).
 //
 // A Gaussian is in a pixel's list iff the pixel lies in its rect and q <= 9.
 // The blend kernels test only q <= 9 on the entries of the pixel's tile list:
@@ -32,11 +34,10 @@ __device__ __forceinline__ bool eval_alpha(float pxc, float pyc, const float4 &a
     dy = __fsub_rn(pyc, a.y);
     const float cross = __fmul_rn(__fmul_rn(2.f, a.w), __fmul_rn(dx, dy));
     const float q = __fmaf_rn(__fmul_rn(a.z, dx), dx, __fmaf_rn(__fmul_rn(b.x, dy), dy, cross));
-    if (!(q <= kQMax)) return false;
     G = __expf(__fmul_rn(-0.5f, q));
     sg = __fmul_rn(b.y, G);
     alpha = fminf(kAlphaMax, sg);
-    return alpha >= kAlphaMin;
+    return (q <= kQMax) & (alpha >= kAlphaMin);
 }
 
 // Conservative test: can the Gaussian (a, b, rect rc) be blended by any pixel

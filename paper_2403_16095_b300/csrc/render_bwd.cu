@@ -210,8 +210,13 @@ __device__ __forceinline__ void bwd_tile(const int gtile, const float4 *__restri
             const float4 a = s_a[k];
             const float4 b = s_b[k];
             float dx = 0.f, dy = 0.f, G = 0.f, sg = 0.f, alpha = 0.f;
-            bool act = (uint32_t)j < my_last;
-            if (act) act = eval_alpha(pxc, pyc, a, b, dx, dy, G, sg, alpha);
+            bool act;
+            if (!POSE && !CD) {  // one path for all lanes up to the act test (measured faster here)
+                act = ((uint32_t)j < my_last) & eval_alpha(pxc, pyc, a, b, dx, dy, G, sg, alpha);
+            } else {  // branching spills less in these builds
+                act = (uint32_t)j < my_last;
+                if (act) act = eval_alpha(pxc, pyc, a, b, dx, dy, G, sg, alpha);
+            }
             float v[11];
             if (act && CD) {  // colour + depth only: the tracking pass's arithmetic, bit for bit
                 float th[6], w, dal;

@@ -128,22 +128,25 @@ __global__ void __launch_bounds__(TILE *TILE, MINB)
                 while (mask) {  // surviving entries, front to back
                     const int k = g0 + __ffs(mask) - 1;
                     mask &= mask - 1;
-                    if (done) continue;
                     const float4 a = s_a[k];
                     const float4 b = s_b[k];
-                    float dx, dy, G, sg, alpha;
-                    if (!eval_alpha(pxc, pyc, a, b, dx, dy, G, sg, alpha)) continue;
+                    const float4 c = s_c[k];  // loaded with a and b: off the blend's dependency chain
+                    // the tests are predicates, not exits: the lanes stay on one path
+                    float dx = 0.f, dy = 0.f, G = 0.f, sg = 0.f, alpha = 0.f;
+                    const bool ok = !done && eval_alpha(pxc, pyc, a, b, dx, dy, G, sg, alpha);
                     const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
-                    if (Tn < kTMin) { done = true; continue; }
-                    const float w = __fmul_rn(alpha, T);
-                    const float4 c = s_c[k];
-                    c0 = fmaf(w, c.x, c0);
-                    c1 = fmaf(w, c.y, c1);
-                    c2 = fmaf(w, c.z, c2);
-                    dep = fmaf(w, b.z, dep);
-                    nus = fmaf(w, b.w, nus);
-                    T = Tn;
-                    last = base + k + 1;
+                    const bool stop = ok && Tn < kTMin;  // stop before T would drop below 1e-4
+                    done = done || stop;
+                    if (ok && !stop) {
+                        const float w = __fmul_rn(alpha, T);
+                        c0 = fmaf(w, c.x, c0);
+                        c1 = fmaf(w, c.y, c1);
+                        c2 = fmaf(w, c.z, c2);
+                        dep = fmaf(w, b.z, dep);
+                        nus = fmaf(w, b.w, nus);
+                        T = Tn;
+                        last = base + k + 1;
+                    }
                 }
                 if (__all_sync(0xffffffffu, done)) break;
             }
@@ -227,12 +230,18 @@ __global__ void __launch_bounds__(TILE *TILE, MINB)
                 const int j = bstart + k;
                 const float4 a = s_a[k];
                 const float4 b = s_b[k];
+                const float4 c = s_c[k];
                 float dx = 0.f, dy = 0.f, G = 0.f, sg = 0.f, alpha = 0.f;
-                bool act = (uint32_t)j < my_last;
-                if (act) act = eval_alpha(pxc, pyc, a, b, dx, dy, G, sg, alpha);
+                bool act;
+                if (MINB == 3) {  // one path for all lanes up to the act test
+                    act = ((uint32_t)j < my_last) & eval_alpha(pxc, pyc, a, b, dx, dy, G, sg, alpha);
+                } else {  // the other builds: branching spills less
+                    act = (uint32_t)j < my_last;
+                    if (act) act = eval_alpha(pxc, pyc, a, b, dx, dy, G, sg, alpha);
+                }
                 if (act) {
                     float th[6], w, dal;
-                    entry_grad_cd(alpha, sg, dx, dy, a, b, s_c[k], gc0, gc1, gc2, gD, T, GS, th, w, dal);
+                    entry_grad_cd(alpha, sg, dx, dy, a, b, c, gc0, gc1, gc2, gD, T, GS, th, w, dal);
                     pose_contract(acc, th, &s_j[k * 9]);
                 }
             }
