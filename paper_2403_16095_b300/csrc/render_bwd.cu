@@ -37,7 +37,7 @@ __device__ __forceinline__ float sgnf(float v) { return v > 0.f ? 1.f : (v < 0.f
 // The last CTA of a frame reuses the same bytes for the pose reduction.
 constexpr int kFullBatch = 512;
 
-template <int TILE, int MODE, int FULL_BATCH = kFullBatch>
+template <int TILE, int MODE, int FULL_BATCH = kFullBatch, bool PERSIST = false>
 struct BwdSmem {
     static constexpr int NT = TILE * TILE;
     static constexpr bool POSE = MODE == GS_MODE_POSE;
@@ -47,10 +47,13 @@ struct BwdSmem {
     static constexpr int BATCH = NT < 256 ? NT : (POSE ? 256 : FULL_BATCH);
     static constexpr size_t kEntry = 4 * sizeof(float4) + sizeof(uint32_t) + (POSE ? 9 * sizeof(float4) : 0);
     static constexpr size_t kStage = BATCH * kEntry;
-    // FULL mode: each thread's rarely used loss terms (opacity, nu and median
-    // gradients, median position), kept here instead of in registers; at the
-    // 48-register cap of the 16x16 build this keeps the walk from spilling
-    static constexpr size_t kLoss = POSE ? 0 : NT * sizeof(float4);
+    // per-tile FULL mode: each thread's rarely used loss terms (opacity, nu and
+    // median gradients, median position), kept here instead of in registers;
+    // at the 48-register cap of the 16x16 build this keeps the walk from
+    // spilling. The persistent kernel keeps them in registers: with the slot
+    // (4 KB more per CTA) its backward measured 8.1-8.8 against 5.5 ms on the
+    // uneven batch.
+    static constexpr size_t kLoss = (POSE || PERSIST) ? 0 : NT * sizeof(float4);
     static constexpr size_t kRed = POSE ? sizeof(df) * kRedSlots * 6 : 0;
     static constexpr size_t bytes = kStage + kLoss > kRed ? kStage + kLoss : kRed;
 };
@@ -78,7 +81,7 @@ struct BwdShared {  // the static shared state of a backward CTA
 // The backward of one tile. The per-tile CTA kernel and the persistent kernel
 // below run this same code, so their gradients agree up to the order of the
 // FULL-mode atomic additions.
-template <int TILE, int MODE, bool CD, int FULL_BATCH>
+template <int TILE, int MODE, bool CD, int FULL_BATCH, bool PERSIST = false>
 __device__ __forceinline__ void bwd_tile(const int gtile, const float4 *__restrict__ rec,
                                          const float4 *__restrict__ jac, const uint32_t *__restrict__ values,
                                          const uint2 *__restrict__ ranges, const FrameTable &ft,
@@ -87,7 +90,7 @@ __device__ __forceinline__ void bwd_tile(const int gtile, const float4 *__restri
                                          float *__restrict__ pose_partials, int per_frame,
                                          double *__restrict__ pose_grad, unsigned *__restrict__ counters,
                                          unsigned char *s_dyn, BwdShared<TILE> &sh) {
-    using SM = BwdSmem<TILE, MODE, FULL_BATCH>;
+    using SM = BwdSmem<TILE, MODE, FULL_BATCH, PERSIST>;
     constexpr int NT = SM::NT;
     constexpr bool POSE = SM::POSE;
     constexpr int BATCH = SM::BATCH;
@@ -158,7 +161,8 @@ __device__ __forceinline__ void bwd_tile(const int gtile, const float4 *__restri
         }
         if (gM != 0.f) my_med = fwd.median_pos[pix];
     }
-    if (!POSE && !CD) s_gx[tid] = make_float4(gO, gN, gM, __int_as_float(my_med));
+    constexpr bool kLossSmem = SM::kLoss > 0 && !CD;  // see BwdSmem
+    if (kLossSmem) s_gx[tid] = make_float4(gO, gN, gM, __int_as_float(my_med));
     if (CD) {  // the launcher picked this variant because these are zero
         gO = 0.f;
         gU = 0.f;
@@ -240,8 +244,8 @@ __device__ __forceinline__ void bwd_tile(const int gtile, const float4 *__restri
                 T = T * inv;  // transmittance in front of entry j
                 const float w = alpha * T;
                 const float4 c = s_c[k];
-                // (gO, gN, gM, median position): from shared memory in FULL mode
-                const float4 gx = POSE ? make_float4(gO, gN, gM, __int_as_float(my_med)) : s_gx[tid];
+                // (gO, gN, gM, median position): from shared memory in the per-tile FULL kernel
+                const float4 gx = kLossSmem ? s_gx[tid] : make_float4(gO, gN, gM, __int_as_float(my_med));
                 const float dz = b.z - Dp;
                 const float dot = gc0 * c.x + gc1 * c.y + gc2 * c.z + gD * b.z + gx.x + gU * dz * dz + gx.y * b.w;
                 const float dal = T * dot - inv * GS;
@@ -359,8 +363,8 @@ __global__ void __launch_bounds__(TILE *TILE, TILE == 16 ? 5 : 1)
         const int item = queue_next(queue, sh.item, it);
         if (item >= ft.total_tiles) break;
         const int gtile = order ? (int)order[item] : item;
-        bwd_tile<TILE, GS_MODE_FULL, CD, FULL_BATCH>(gtile, rec, nullptr, values, ranges, ft, obs_depth, fwd, lp,
-                                                     grad2d, nullptr, 0, nullptr, nullptr, s_dyn, sh);
+        bwd_tile<TILE, GS_MODE_FULL, CD, FULL_BATCH, true>(gtile, rec, nullptr, values, ranges, ft, obs_depth, fwd, lp,
+                                                           grad2d, nullptr, 0, nullptr, nullptr, s_dyn, sh);
     }
     queue_exit(queue);
 }
@@ -389,11 +393,12 @@ cudaError_t launch_variant(const float4 *rec, const float4 *jac, const uint32_t 
     constexpr size_t smem = BwdSmem<TILE, MODE, FULL_BATCH>::bytes;
     cudaError_t e;
     if (MODE == GS_MODE_FULL && queue) {
+        constexpr size_t smem_p = BwdSmem<TILE, MODE, FULL_BATCH, true>::bytes;
         constexpr auto kern = k_render_bwd_persist<TILE, CD, FULL_BATCH>;
-        if ((e = set_smem_once<kern>(smem)) != cudaSuccess) return e;
+        if ((e = set_smem_once<kern>(smem_p)) != cudaSuccess) return e;
         int grid = 0;
-        if ((e = persistent_grid<kern>(TILE * TILE, smem, ft.total_tiles, &grid)) != cudaSuccess) return e;
-        kern<<<grid, TILE * TILE, smem, s>>>(rec, values, ranges, order, ft, obs_depth, fwd, lp, grad2d, status, queue);
+        if ((e = persistent_grid<kern>(TILE * TILE, smem_p, ft.total_tiles, &grid)) != cudaSuccess) return e;
+        kern<<<grid, TILE * TILE, smem_p, s>>>(rec, values, ranges, order, ft, obs_depth, fwd, lp, grad2d, status, queue);
         return cudaGetLastError();
     }
     constexpr auto kern = k_render_bwd<TILE, MODE, CD, FULL_BATCH>;
