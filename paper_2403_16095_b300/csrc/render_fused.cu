@@ -132,8 +132,9 @@ __global__ void __launch_bounds__(TILE *TILE, MINB)
                     const float4 b = s_b[k];
                     const float4 c = s_c[k];  // loaded with a and b: off the blend's dependency chain
                     // the tests are predicates, not exits: the lanes stay on one path
+                    // (saturated lanes evaluate alpha too, and discard it)
                     float dx = 0.f, dy = 0.f, G = 0.f, sg = 0.f, alpha = 0.f;
-                    const bool ok = !done && eval_alpha(pxc, pyc, a, b, dx, dy, G, sg, alpha);
+                    const bool ok = (!done) & eval_alpha(pxc, pyc, a, b, dx, dy, G, sg, alpha);
                     const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
                     const bool stop = ok && Tn < kTMin;  // stop before T would drop below 1e-4
                     done = done || stop;
