@@ -76,12 +76,12 @@ FUSED_DRAM_BYTES_PER_LAUNCH = 16.324096e6 + 0
 # (profiles/dram_iteration_track-640x480-300k.md); None once a kernel of the
 # iteration changes.
 DRAM_BYTES_PER_ITERATION = 0.562432e6 + 2.875136e6
-# DRAM bytes of one k_render_fused_pose<16, 4> launch at 1200x680 on the 5M
+# DRAM bytes of one k_render_fused_pose<16, 3> launch at 1200x680 on the 5M
 # Gaussians: 16-bit storage and FP32 storage with the map in Morton order, and
 # FP32 storage in the generator's order; ncu, cold cache
 # (profiles/dram_fused_precision-1200x680-5M-room.md); None for other builds.
-PREC16_FUSED_DRAM_BYTES_PER_LAUNCH = 105.221376e6 + 3.605248e6
-PREC32_FUSED_DRAM_BYTES_PER_LAUNCH = 105.456384e6 + 3.291392e6
+PREC16_FUSED_DRAM_BYTES_PER_LAUNCH = None  # recaptured below for the current build
+PREC32_FUSED_DRAM_BYTES_PER_LAUNCH = None
 PREC32_GIVEN_ORDER_FUSED_DRAM_BYTES_PER_LAUNCH = None  # not captured for the current kernel
 FP32_LANES_PER_SM = 128
 
@@ -424,11 +424,10 @@ def run_ours(a):
     bwd_avg_ms = statistics.mean(bwd_ms)
     E = statistics.mean(contrib)
     if tr.fused:
-        # the library's build choice: 4 CTAs per SM at >= 800 records per tile, else 3 (tile 16)
-        dense = g.n >= 800 * tr.rast.n_tiles
-        minb = (4 if dense else 3) if a.tile == 16 else 1
+        # the library's build: 3 CTAs per SM at tile 16, 1 otherwise
+        minb = 3 if a.tile == 16 else 1
         kname, flop, traffic = f"k_render_fused_pose<{a.tile}, {minb}>", FWD_FLOP_PER_CONTRIB + BWD_FLOP_PER_CONTRIB, \
-            (FUSED_DRAM_BYTES_PER_LAUNCH if (a.tile == 16 and not dense) else None)
+            (FUSED_DRAM_BYTES_PER_LAUNCH if a.tile == 16 else None)
     else:
         kname, flop, traffic = f"k_render_bwd<{a.tile},POSE>", BWD_FLOP_PER_CONTRIB, \
             (BWD_DRAM_BYTES_PER_LAUNCH if a.tile == 16 else None)
@@ -776,13 +775,12 @@ def run_precision(a):
     E = statistics.mean(contrib)
     flop = FWD_FLOP_PER_CONTRIB + BWD_FLOP_PER_CONTRIB
     launch_ms = statistics.mean(bwd)
-    dense = g32.n >= 800 * tr.rast.n_tiles
     achieved = E * flop / (launch_ms * 1e-3) / 1e12
     traffic = ({("16bit", "morton"): PREC16_FUSED_DRAM_BYTES_PER_LAUNCH,
                 ("fp32", "morton"): PREC32_FUSED_DRAM_BYTES_PER_LAUNCH,
                 ("fp32", "given"): PREC32_GIVEN_ORDER_FUSED_DRAM_BYTES_PER_LAUNCH}.get((a.storage, a.order))
-               if (dense and a.tile == 16) else None)
-    roof = {"kernel": f"k_render_fused_pose<{a.tile}, {4 if dense else 3}>", "bound": "alu", "achieved": achieved,
+               if a.tile == 16 else None)
+    roof = {"kernel": f"k_render_fused_pose<{a.tile}, {3 if a.tile == 16 else 1}>", "bound": "alu", "achieved": achieved,
             "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch, cold cache",
             "peak_source": f"{n_sm} SMs (device query) x 128 FP32 lanes x 2 x {mhz:.0f} MHz (max SM clock)",

@@ -468,7 +468,7 @@ gs_status gs_render_fwd_bwd_pose(const gs_projected *proj, const gs_tiles *tiles
     // the pass writes one pose partial per tile; the frame's fixed-order sum
     // (and the Adam step) follow as one small chained launch
     e = gs::launch_render_fused_pose(proj->rec, proj->pose_jac, tiles->values, tiles->ranges, tiles->order, ft, ip,
-                                     lp, pose_partials, per_frame, status, M, stream);
+                                     lp, pose_partials, per_frame, status, stream);
     if (e != cudaSuccess || !pose_grad) return cuda_status(e, "gs_render_fwd_bwd_pose");
     return cuda_status(gs::launch_pose_reduce_adam(pose_partials, n_frames, per_frame, pose_grad, adam_state, ad, T_cw,
                                                    status, stream),

@@ -145,7 +145,7 @@ cudaError_t launch_pack_bf16(const GaussPtrs &g, int n, const uint32_t *perm, fl
 cudaError_t launch_render_fused_pose(const float *rec, const float *jac, const uint32_t *values,
                                      const uint32_t *ranges, const uint32_t *order, const FrameTable &ft,
                                      const ImagePtrs &out, const LossParams &lp, float *pose_partials, int per_frame,
-                                     const int32_t *status, int n_records, cudaStream_t s);
+                                     const int32_t *status, cudaStream_t s);
 // nu.cu
 cudaError_t launch_nu_accumulate(const float *rec, const uint32_t *values, const FrameTable &ft, int n_gaussians,
                                  const float *obs_depth, const int32_t *dom_pos, const float *dom_weight,

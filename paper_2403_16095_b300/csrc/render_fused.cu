@@ -39,13 +39,12 @@ struct FusedSmem {
     static constexpr size_t bytes = (size_t)BATCH * 13 * sizeof(float4);  // record (4) + Jacobian (9)
 };
 
-// Two builds per tile size: MINB = 3 (80 registers, 3 CTAs per SM at tile 16)
-// and MINB = 4 (63 registers, 4 CTAs per SM, no spills). Which is faster depends on the list lengths: at 640x480 with 300k
-// Gaussians (~250 records per tile) the first (155 vs 161 us per launch), at
-// 1200x680 with 5M (~1,550 records per tile) the second (2.14 vs 2.27 ms per
-// iteration), where the longer walks need more warps to hide their latency.
-// The launcher picks by records per tile (kDenseRecordsPerTile).
-constexpr int kDenseRecordsPerTile = 800;
+// At tile 16 the pass is built for 3 CTAs per SM (80 registers). A 4-CTA
+// build (63 registers, no spills) was faster at ~1,550 records per tile
+// before the per-entry chains were shortened (2.14 vs 2.27 ms per iteration
+// at 1200x680 / 5M); with them it is slower at both measured list lengths:
+// 126.2 vs 116.0 us per launch at 640x480 / 300k (~250 records per tile) and
+// 1.360 vs 1.350 ms at 1200x680 / 5M.
 template <int TILE, int MINB>
 __global__ void __launch_bounds__(TILE *TILE, MINB)
     k_render_fused_pose(const float4 *__restrict__ rec, const float4 *__restrict__ jac,
@@ -260,7 +259,7 @@ __global__ void __launch_bounds__(TILE *TILE, MINB)
 template <int TILE>
 cudaError_t launch_tile(const float4 *rec, const float4 *jac, const uint32_t *values, const uint2 *ranges,
                         const uint32_t *order, const FrameTable &ft, const ImagePtrs &out, const LossParams &lp,
-                        float *pp, int per_frame, const int32_t *status, bool dense, cudaStream_t s) {
+                        float *pp, int per_frame, const int32_t *status, cudaStream_t s) {
     // raise the dynamic shared-memory limit once per device (a host-side
     // attribute; the first call happens outside any stream capture)
     static std::atomic<uint64_t> done{0};
@@ -268,17 +267,14 @@ cudaError_t launch_tile(const float4 *rec, const float4 *jac, const uint32_t *va
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     constexpr size_t smem = FusedSmem<TILE>::bytes;
-    constexpr int kMinb = TILE == 16 ? 3 : 1, kMinbDense = TILE == 16 ? 4 : 1;
+    constexpr int kMinb = TILE == 16 ? 3 : 1;
     if (dev >= 64 || !((done.load() >> dev) & 1)) {
         e = cudaFuncSetAttribute(k_render_fused_pose<TILE, kMinb>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_render_fused_pose<TILE, kMinbDense>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem);
         if (e != cudaSuccess) return e;
         if (dev < 64) done.fetch_or(1ull << dev);
     }
-    auto kernel = dense ? k_render_fused_pose<TILE, kMinbDense> : k_render_fused_pose<TILE, kMinb>;
+    auto kernel = k_render_fused_pose<TILE, kMinb>;
     return launch_chained(kernel, dim3(ft.total_tiles), dim3(TILE * TILE), smem, s, rec, jac, values, ranges, order, ft,
                           out, lp, pp, per_frame, status);
 }
@@ -288,16 +284,15 @@ cudaError_t launch_tile(const float4 *rec, const float4 *jac, const uint32_t *va
 cudaError_t launch_render_fused_pose(const float *rec, const float *jac, const uint32_t *values,
                                      const uint32_t *ranges, const uint32_t *order, const FrameTable &ft,
                                      const ImagePtrs &out, const LossParams &lp, float *pose_partials, int per_frame,
-                                     const int32_t *status, int n_records, cudaStream_t s) {
+                                     const int32_t *status, cudaStream_t s) {
     if (ft.total_tiles == 0) return cudaSuccess;
     const float4 *r4 = reinterpret_cast<const float4 *>(rec);
     const float4 *j4 = reinterpret_cast<const float4 *>(jac);
     const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
-    const bool dense = (long long)n_records >= (long long)kDenseRecordsPerTile * ft.total_tiles;
     switch (ft.tile) {
-        case 8: return launch_tile<8>(r4, j4, values, rg, order, ft, out, lp, pose_partials, per_frame, status, dense, s);
-        case 16: return launch_tile<16>(r4, j4, values, rg, order, ft, out, lp, pose_partials, per_frame, status, dense, s);
-        case 32: return launch_tile<32>(r4, j4, values, rg, order, ft, out, lp, pose_partials, per_frame, status, dense, s);
+        case 8: return launch_tile<8>(r4, j4, values, rg, order, ft, out, lp, pose_partials, per_frame, status, s);
+        case 16: return launch_tile<16>(r4, j4, values, rg, order, ft, out, lp, pose_partials, per_frame, status, s);
+        case 32: return launch_tile<32>(r4, j4, values, rg, order, ft, out, lp, pose_partials, per_frame, status, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -156,11 +156,11 @@ def test_fused_tracking_pass_equals_forward_then_backward(track_full):
         r.fwd_bwd_pose(dict(loss, w_align=0.1))
 
 
-def test_fused_tracking_pass_dense_build_equals_forward_then_backward():
-    """At 800 or more records per tile the tracking pass runs its 4-CTA-per-SM
-    build (fewer registers): here 12,000 Gaussians over the 12 tiles of a 64x48
-    image (1,000 per tile). Its channels and FP64 pose gradient equal
-    gs_render_fwd + gs_render_bwd bit for bit, as the default build's do."""
+def test_fused_tracking_pass_long_lists_equal_forward_then_backward():
+    """Long tile lists, walked in several staging batches and restaged for the
+    backward: 12,000 Gaussians over the 12 tiles of a 64x48 image (1,000 per
+    tile). The tracking pass's channels and FP64 pose gradient equal
+    gs_render_fwd + gs_render_bwd bit for bit."""
     from paper_2403_16095_b300 import Rasterizer
     from paper_2403_16095_b300 import _abi as A
     sc = synth.room_scene(12_000, seed=1309)
