@@ -70,18 +70,18 @@ FWD_FLOP_PER_CONTRIB = 26
 # workload, from one ncu capture of the current kernel
 # (profiles/k_render_fused_pose_track-640x480-300k.md, cold cache); None once
 # the kernel changes.
-FUSED_DRAM_BYTES_PER_LAUNCH = 16.324096e6 + 0
+FUSED_DRAM_BYTES_PER_LAUNCH = 16.32128e6 + 0
 # DRAM bytes (read + write) of one whole tracking iteration (its 7 kernels),
 # from one ncu capture with the caches carried over between kernels
 # (profiles/dram_iteration_track-640x480-300k.md); None once a kernel of the
 # iteration changes.
-DRAM_BYTES_PER_ITERATION = 0.562432e6 + 2.875136e6
+DRAM_BYTES_PER_ITERATION = 0.545024e6 + 2.876672e6
 # DRAM bytes of one k_render_fused_pose<16, 3> launch at 1200x680 on the 5M
 # Gaussians: 16-bit storage and FP32 storage with the map in Morton order, and
 # FP32 storage in the generator's order; ncu, cold cache
 # (profiles/dram_fused_precision-1200x680-5M-room.md); None for other builds.
-PREC16_FUSED_DRAM_BYTES_PER_LAUNCH = None  # recaptured below for the current build
-PREC32_FUSED_DRAM_BYTES_PER_LAUNCH = None
+PREC16_FUSED_DRAM_BYTES_PER_LAUNCH = 104.30976e6 + 2.601984e6
+PREC32_FUSED_DRAM_BYTES_PER_LAUNCH = 104.235264e6 + 3.001088e6
 PREC32_GIVEN_ORDER_FUSED_DRAM_BYTES_PER_LAUNCH = None  # not captured for the current kernel
 FP32_LANES_PER_SM = 128
 
