@@ -79,12 +79,12 @@ __device__ __forceinline__ void fwd_tile(const int gtile, const float4 *__restri
                 while (mask) {  // surviving entries, front to back
                     const int k = g0 + __ffs(mask) - 1;
                     mask &= mask - 1;
-                    if (done) continue;
                     const float4 a = s_a[k];
                     const float4 b = s_b[k];
                     const float4 c = s_c[k];  // loaded with a and b: off the blend's dependency chain
                     float dx, dy, G, sg, alpha;
-                    if (!eval_alpha(pxc, pyc, a, b, dx, dy, G, sg, alpha)) continue;
+                    // saturated lanes evaluate alpha too and discard it: no branch around the evaluation
+                    if (!((!done) & eval_alpha(pxc, pyc, a, b, dx, dy, G, sg, alpha))) continue;
                     const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
                     if (Tn < kTMin) { done = true; continue; }
                     const float w = __fmul_rn(alpha, T);
