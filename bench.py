@@ -10,8 +10,8 @@ reduction -> Adam step on the pose), captured as one CUDA graph per frame.
 
 A step is one tracked frame (30 iterations). The metric is tracking iterations
 per second: value = 30 * steps * ranks / (max over ranks of the summed device
-time of the steps). L2 (126 MB) is flushed between steps by writing a 512 MB
-buffer outside the timed region; within a frame the iterations run back to back
+time of the steps). L2 (126 MB) is flushed between steps by writing a buffer of
+twice its size outside the timed region; within a frame the iterations run back to back
 as tracking does.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -84,6 +84,15 @@ PREC16_FUSED_DRAM_BYTES_PER_LAUNCH = 104.30976e6 + 2.601984e6
 PREC32_FUSED_DRAM_BYTES_PER_LAUNCH = 104.235264e6 + 3.001088e6
 PREC32_GIVEN_ORDER_FUSED_DRAM_BYTES_PER_LAUNCH = None  # not captured for the current kernel
 FP32_LANES_PER_SM = 128
+
+
+def _l2_flush_buffer(dev):
+    """A device buffer of twice the L2 size (rounded up to a MiB); writing it
+    evicts every line of the previous step. Returns (buffer, MiB)."""
+    import torch
+    l2 = int(getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 0) or (126 << 20))
+    mib = -(-2 * l2 // (1 << 20))
+    return torch.empty(mib << 20, dtype=torch.uint8, device=dev), mib
 
 
 def _fp32_peak(dev, mhz):
@@ -327,7 +336,7 @@ def run_ours(a):
                  timing_every=TIMING_EVERY)
     f0 = my_frames[0]
     tr.prepare(tcol[f0], tdep[f0], starts_t[f0], headroom=1.6)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    flush, flush_mib = _l2_flush_buffer(dev)
 
     def barrier():
         if ws > 1:
@@ -409,7 +418,7 @@ def run_ours(a):
                "d2h_bytes_per_step": 12 * 8 + 4 * 4,
                "note": "per step: frame RGB-D + start pose host->device (pinned), 30 iterations, pose + status "
                        "device->host (pinned), through Tracker.submit/drain: the upload of frame k + 1 overlaps "
-                       "the tracking of frame k; the 512 MB L2 flush between frames is inside the timed region"}
+                       f"the tracking of frame k; the {flush_mib} MiB L2 flush between frames is inside the timed region"}
 
     if rank != 0:
         if ws > 1:
@@ -474,7 +483,7 @@ def run_ours(a):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "width": 640, "height": 480, "gaussians": int(g.n), "map_order": a.order,
                        "iters_per_frame": ITERS, "step": "one tracked frame (30 iterations)", "tile": a.tile,
-                       "l2": "flushed between steps (512 MB write, untimed)", "parallelism": f"replicas x{ws}",
+                       "l2": f"flushed between steps ({flush_mib} MiB write, twice the L2, untimed)", "parallelism": f"replicas x{ws}",
                        "ms_per_iteration": total_ms / (a.steps * ITERS), "wall_s": wall,
                        "pairs_per_iteration": int(tr.rast.read_status()[1]),
                        "contributions_per_iteration": E, "bwd_share_of_step": bwd_share,
@@ -563,7 +572,7 @@ def run_batch(a):
         r.render(g, Tt, tdep)
         r.set_capacity(int(r.read_status()[1] * 1.25) + 4096)
         my_cams, my_T, my_loss, my_dep = cams, Tt, loss, tdep
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    flush, flush_mib = _l2_flush_buffer(dev)
     # separate projection and binning calls: on multi-frame batches the count
     # kernel (8 records per thread) beats counting inside the projection
     stages = ("project", "bin", "forward", "backward")
@@ -667,7 +676,7 @@ def run_batch(a):
                        "sched": sched_name,
                        "launch": "CUDA graph replay" if graph is not None else "eager",
                        "parallelism": f"keyframe shards x{ws}" if a.workload == "mapping" else "single batch",
-                       "autotune_ms": tune, "l2": "flushed between steps (512 MB write, untimed)",
+                       "autotune_ms": tune, "l2": f"flushed between steps ({flush_mib} MiB write, twice the L2, untimed)",
                        "stage_ms_eager": {s_: statistics.mean(v) for s_, v in per.items()},
                        "eager_ms_per_step": eager_ms,
                        "pairs": int(r.read_status()[1]), "contributions": E},
@@ -741,7 +750,7 @@ def run_precision(a):
               for f in sorted(set(f % n_pose for f in frames))}
     tr = Tracker(gt, cam, tile=a.tile, iters=ITERS, graph=True, timing=True, timing_every=TIMING_EVERY)
     tr.prepare(tcol[0], tdep[0], starts[0], headroom=1.6)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    flush, flush_mib = _l2_flush_buffer(dev)
     for f in frames[:a.warmup]:
         flush.zero_()
         tr.set_frame(tcol[f % n_pose], tdep[f % n_pose], starts[f % n_pose])
@@ -807,7 +816,7 @@ def run_precision(a):
             "config": {"workload": f"precision-1200x680-5M-room-{a.storage}", "gaussians": int(g32.n),
                        "tile": a.tile, "iters_per_frame": ITERS, "frames": len(set(f % n_pose for f in frames[a.warmup:])),
                        "map_order": a.order,
-                       "l2": "flushed between steps (512 MB write, untimed)",
+                       "l2": f"flushed between steps ({flush_mib} MiB write, twice the L2, untimed)",
                        "ms_per_iteration": total_ms / (a.steps * ITERS),
                        "pairs_per_iteration": int(tr.rast.read_status()[1])},
             "roofline": roof, "cpu_baseline": cpu,
