@@ -320,7 +320,11 @@ gs_status gs_bin_tiles_noalloc(const gs_projected *proj, int n_frames, const gs_
 
 /* Eq. 3-10. One CTA per tile: the tile's sorted list is staged in shared memory
  * in batches and every pixel blends front to back (alpha test, stop rule,
- * median crossing of T = 0.5) until all of the tile's pixels are done.
+ * median crossing of T = 0.5) until all of the tile's pixels are done. A list
+ * entry is blended by the pixels with q <= 9 (and alpha >= 1/255): the pixel
+ * rect of the record contains that ellipse (q >= dx^2 / lambda_max and
+ * r >= 3 sqrt(lambda_max)), so the rect is not tested per pixel; in FP32 the
+ * two can differ only where q is within ~1e-6 of 9.
  *   obs_depth: device [.][H][W] sensor depth D for U (Eq. 10), or NULL (U not written). */
 gs_status gs_render_fwd(const gs_projected *proj, const gs_tiles *tiles, int n_frames,
                         const gs_camera *cams, const float *obs_depth, const gs_opts *opts,
