@@ -4,9 +4,17 @@ FULL backward (libgs kernels) on its own keyframes of the 8-frame, 640x480,
 1M-Gaussian window, then one all-reduce of the parameter gradients. Both
 processes share the one GPU here; their kernels never wait on each other (the
 only exchange is the host-side gloo collective between whole steps). The sum
-must equal the single-launch 8-frame gradient up to FP32 summation order (within
-a few times the single launch's own run-to-run spread, which its atomic sums in
-arrival order give it), and each frame's pose gradient must be its owner's."""
+must equal the single-launch 8-frame gradient up to FP32 summation order, and
+each frame's pose gradient must be its owner's.
+
+Tolerance. The ranks sum their own frames, then add the two partial sums; the
+single launch sums all eight frames in one order. Both are FP32 sums of the
+same per-frame terms, and the quaternion gradients cancel strongly across
+frames, so the two orders differ by more than the single launch's run-to-run
+spread (its atomics in arrival order): measured up to 2.6e-5 of the largest
+element and 5.8e-6 in norm. A frame dropped or counted twice would move the
+sum by about an eighth of its norm. The bounds below (5e-4 of the largest
+element, 1e-4 in norm) sit between the two."""
 import os
 import socket
 
@@ -96,8 +104,8 @@ def test_two_rank_sharded_window_equals_single_launch():
             e_norm = np.linalg.norm(d) / np.linalg.norm(want[k])
             print(f"rank {rank} {k}: max {e_max:.2e} of scale, norm {e_norm:.2e} "
                   f"(single launch run to run: {spread[k][0]:.2e}, {spread[k][1]:.2e})")
-            # within a few times the order noise of the single launch itself
-            assert e_max < max(4 * spread[k][0], 1e-5) and e_norm < max(4 * spread[k][1], 1e-6), (k, e_max, e_norm)
+            # FP32 summation order, far below one frame's share (module docstring)
+            assert e_max < 5e-4 and e_norm < 1e-4, (k, e_max, e_norm)
     assert sorted(owners) == list(range(8))
     for k in PARAMS:  # both ranks hold the same summed gradients
         assert np.array_equal(res[0][1][k], res[1][1][k])
