@@ -169,7 +169,7 @@ gs_status gs_project(const gs_gaussians *g, int n_frames, const gs_camera *cams,
     if (opts->mode == GS_MODE_POSE && g->n > 0 && n_frames > 0 && (!out->pose_jac || !aligned(out->pose_jac, 16)))
         return fail(GS_ERR_INVALID_ARG, "POSE mode needs a 16-byte aligned pose_jac");
     return cuda_status(gs::launch_project(gauss_ptrs(g), g->n, ft, T_cw, opts->jclamp, opts->nu_cull, opts->mode,
-                                          out->rec, out->tiles_touched, out->pose_jac, nullptr, status, stream),
+                                          out->rec, out->tiles_touched, out->pose_jac, gs::TileCtr{nullptr, 0}, status, stream),
                        "gs_project");
 }
 
@@ -189,7 +189,7 @@ gs_status gs_project_bf16(const gs_gaussians_bf16 *g, int n_frames, const gs_cam
     if (opts->mode == GS_MODE_POSE && g->n > 0 && n_frames > 0 && (!out->pose_jac || !aligned(out->pose_jac, 16)))
         return fail(GS_ERR_INVALID_ARG, "POSE mode needs a 16-byte aligned pose_jac");
     return cuda_status(gs::launch_project_bf16(g->anchors, g->packed, g->n, ft, T_cw, opts->jclamp, opts->nu_cull,
-                                               opts->mode, out->rec, out->tiles_touched, out->pose_jac, nullptr, status,
+                                               opts->mode, out->rec, out->tiles_touched, out->pose_jac, gs::TileCtr{nullptr, 0}, status,
                                                stream),
                        "gs_project_bf16");
 }
@@ -279,7 +279,8 @@ gs_status gs_project_bin(const gs_gaussians *g, int n_frames, const gs_camera *c
     GS_TRY(check_bin_call(out, n_frames, ft, tiles, status, ws, ws_bytes));
     GS_TRY(cuda_status(gs::launch_bin_clear(tiles->ranges, ft, tiles->capacity, ws, stream), "gs_project_bin (clear)"));
     GS_TRY(cuda_status(gs::launch_project(gauss_ptrs(g), g->n, ft, T_cw, opts->jclamp, opts->nu_cull, opts->mode,
-                                          out->rec, out->tiles_touched, out->pose_jac, tiles->ranges, status, stream),
+                                          out->rec, out->tiles_touched, out->pose_jac,
+                                          gs::tile_counters(tiles->ranges, ft, tiles->capacity, ws), status, stream),
                        "gs_project_bin (projection)"));
     return bin_after_counting_projection(out, n_frames, ft, tiles, status, ws, stream);
 }
@@ -304,8 +305,9 @@ gs_status gs_project_bin_bf16(const gs_gaussians_bf16 *g, int n_frames, const gs
     GS_TRY(cuda_status(gs::launch_bin_clear(tiles->ranges, ft, tiles->capacity, ws, stream),
                        "gs_project_bin_bf16 (clear)"));
     GS_TRY(cuda_status(gs::launch_project_bf16(g->anchors, g->packed, g->n, ft, T_cw, opts->jclamp, opts->nu_cull,
-                                               opts->mode, out->rec, out->tiles_touched, out->pose_jac, tiles->ranges,
-                                               status, stream),
+                                               opts->mode, out->rec, out->tiles_touched, out->pose_jac,
+                                               gs::tile_counters(tiles->ranges, ft, tiles->capacity, ws), status,
+                                               stream),
                        "gs_project_bin_bf16 (projection)"));
     return bin_after_counting_projection(out, n_frames, ft, tiles, status, ws, stream);
 }

@@ -3,22 +3,23 @@
 // (global tile id << 32 | float bits of depth) with the record index as the
 // final tie-break:
 //
-//   k_bin_clear   zeroes the tile counters (the `ranges` buffer doubles as
-//                 the counters) and the call's scalars.
+//   k_bin_clear   zeroes the tile counters (a line apart in the workspace for
+//                 calls of up to 4,096 tiles, else the end words of `ranges`;
+//                 tile_counters) and the call's scalars.
 //   k_tile_count  MSD digit = the tile id: one atomic increment per
 //                 (record, overlapped tile) into the tile's counter; pairs are
 //                 spread over the lanes of a warp so large footprints do not
 //                 serialise, and lanes on the same tile share one atomic
 //                 (pairs.cuh). gs_project_bin does this count in the
 //                 projection kernel instead and skips this pass.
-//   k_tile_scan   exclusive scan of the counters -> each tile's [start, start)
-//                 cursor, total pair count P and the capacity check; optionally
+//   k_tile_scan   exclusive scan of the counters -> each tile's final
+//                 [start, end) in `ranges`, the fill's cursor (= start), the
+//                 total pair count P and the capacity check; optionally
 //                 the launch order of the blend kernels: tiles by descending
 //                 list length (a counting sort on lengths / 4), so that the
 //                 longest tiles, which bound the blend kernels, start first.
-//   k_tile_fill   each pair claims a slot in its tile's bucket and stores the
-//                 low key (depth bits << 32 | record); after this pass every
-//                 tile's cursor equals its end, so `ranges` is final.
+//   k_tile_fill   each pair claims a slot in its tile's bucket (the cursor's
+//                 atomic) and stores the low key (depth bits << 32 | record).
 //   k_tile_sort   sorts each bucket's low keys: buckets under 256 keys by one
 //                 warp in registers; up to 1024 keys by a CTA bitonic network
 //                 in registers and shared memory; larger ones by a stable LSD
@@ -102,7 +103,7 @@ __device__ __forceinline__ PairSrc pair_source(const RecLoad &L, int i, int n_pe
 template <int R>
 __global__ void __launch_bounds__(kThreads)
     k_tile_count(const float *__restrict__ rec, const int *__restrict__ touched, int M, int n_per_frame, FrameTable ft,
-                 uint32_t *__restrict__ ranges, const int32_t *__restrict__ status) {
+                 TileCtr tc, const int32_t *__restrict__ status) {
     dep_wait();
     if (!status_ok(status)) return;
     const int base = blockIdx.x * kThreads + threadIdx.x, stride = gridDim.x * kThreads;
@@ -112,29 +113,31 @@ __global__ void __launch_bounds__(kThreads)
     for (int j = 0; j < R; ++j) {
         const PairSrc src = pair_source(L[j], base + j * stride, n_per_frame, ft);
         if (!__any_sync(0xffffffffu, src.valid)) continue;
-        warp_for_each_pair(src, [&](bool valid, int, int gt, uint32_t) { warp_claim<false>(valid, gt, ranges); });
+        warp_for_each_pair(src, [&](bool valid, int, int gt, uint32_t) { warp_claim<false>(valid, gt, tc); });
     }
 }
 
-// Zeroes the per-tile counters (ranges) and the scalars of the call before the
-// count: a kernel rather than two memsets, so that the chain of launches stays
-// kernel to kernel.
-__global__ void __launch_bounds__(kThreads) k_bin_clear(uint32_t *__restrict__ ranges, int n_words, int *__restrict__ misc) {
+// Zeroes the per-tile counters and the scalars of the call before the count: a
+// kernel rather than memsets, so that the chain of launches stays kernel to
+// kernel.
+__global__ void __launch_bounds__(kThreads) k_bin_clear(TileCtr tc, int n_tiles, int *__restrict__ misc) {
     dep_wait();
     const int stride = gridDim.x * kThreads;
-    for (int i = blockIdx.x * kThreads + threadIdx.x; i < n_words; i += stride) ranges[i] = 0u;
+    for (int t = blockIdx.x * kThreads + threadIdx.x; t < n_tiles; t += stride) tc.p[(size_t)t * tc.stride] = 0u;
     if (blockIdx.x == 0 && threadIdx.x < 16) misc[threadIdx.x] = 0;
 }
 
-// One CTA: exclusive scan of the per-tile counts (ranges[2t+1]) into
-// ranges[2t] = ranges[2t+1] = start (the fill then advances ranges[2t+1] to end).
+// One CTA: exclusive scan of the per-tile counts into the final ranges
+// [start, end) and the fill's cursors (counter = start; the fill advances it
+// to end). Where the counters are the ranges' end words (tile_counters), the
+// cursor is written after the end, so that the fill starts from start.
 constexpr int kOrderBuckets = kScanThreads;  // list length / 4, clipped
 constexpr int kWarpSortKeys = 256;           // shorter lists are sorted by one warp
 
 __device__ __forceinline__ int order_bucket(uint32_t len) { return (int)min(len >> 2, (uint32_t)kOrderBuckets - 1); }
 
 __global__ void __launch_bounds__(kScanThreads)
-    k_tile_scan(uint32_t *__restrict__ ranges, int n_tiles, int capacity, int32_t *__restrict__ status,
+    k_tile_scan(uint32_t *ranges, TileCtr tc, int n_tiles, int capacity, int32_t *__restrict__ status,
                 int *__restrict__ misc, uint32_t *__restrict__ order) {
     dep_wait();
     __shared__ long long s_w[kScanThreads / 32];
@@ -148,7 +151,7 @@ __global__ void __launch_bounds__(kScanThreads)
     const int lo = min(n_tiles, t * per), hi = min(n_tiles, lo + per);
     long long local = 0;
     for (int k = lo; k < hi; ++k) {
-        const uint32_t c = ranges[2 * (size_t)k + 1];
+        const uint32_t c = tc.p[(size_t)k * tc.stride];
         local += c;
         if (order) atomicAdd(&s_hist[order_bucket(c)], 1u);
     }
@@ -187,11 +190,13 @@ __global__ void __launch_bounds__(kScanThreads)
         __syncthreads();  // read before the scatter below advances the cursors
     }
     for (int k = lo; k < hi; ++k) {
-        const uint32_t c = ranges[2 * (size_t)k + 1];
+        uint32_t *ctr = tc.p + (size_t)k * tc.stride;
+        const uint32_t c = *ctr;
         const uint32_t start = (uint32_t)(run > UINT_MAX ? UINT_MAX : run);
-        ranges[2 * (size_t)k] = start;
-        ranges[2 * (size_t)k + 1] = start;
         run += c;
+        ranges[2 * (size_t)k] = start;
+        ranges[2 * (size_t)k + 1] = (uint32_t)(run > UINT_MAX ? UINT_MAX : run);
+        *ctr = start;  // after the end word, which it may alias
         if (order) order[atomicAdd(&s_hist[order_bucket(c)], 1u)] = (uint32_t)k;
     }
     if (t == 0) {
@@ -204,8 +209,7 @@ __global__ void __launch_bounds__(kScanThreads)
 template <int R>
 __global__ void __launch_bounds__(kThreads)
     k_tile_fill(const float *__restrict__ rec, const int *__restrict__ touched, int M, int n_per_frame, FrameTable ft,
-                uint32_t *__restrict__ ranges, uint64_t *__restrict__ low_keys, int capacity,
-                const int32_t *__restrict__ status) {
+                TileCtr tc, uint64_t *__restrict__ low_keys, int capacity, const int32_t *__restrict__ status) {
     dep_wait();
     if (!status_ok(status)) return;
     const int base = blockIdx.x * kThreads + threadIdx.x, stride = gridDim.x * kThreads;
@@ -217,7 +221,7 @@ __global__ void __launch_bounds__(kThreads)
         const PairSrc src = pair_source(L[j], i, n_per_frame, ft);
         if (!__any_sync(0xffffffffu, src.valid)) continue;
         warp_for_each_pair(src, [&](bool valid, int owner, int gt, uint32_t o_zb) {
-            const uint32_t slot = warp_claim<true>(valid, gt, ranges);
+            const uint32_t slot = warp_claim<true>(valid, gt, tc);
             const uint32_t o_i = (uint32_t)(i - (threadIdx.x & 31) + owner);
             if (valid && slot < (uint32_t)capacity) low_keys[slot] = ((uint64_t)o_zb << 32) | o_i;
         });
@@ -611,11 +615,36 @@ size_t bin_workspace_bytes(int n_records, int capacity) {
     return layout(capacity).total;
 }
 
+// Every (record, tile) pair adds to its tile's counter with an atomic, in the
+// count (or the counting projection) and again in the fill, and the atomics on
+// one line are executed one after another by the L2 slice that holds it.
+// Packed next to each other (the end words of `ranges`), the ~1,200 counters
+// of a 640x480 frame take 75 lines, and ncu showed one L2 slice's atomic unit
+// busy for half of the fill while the average slice was at 2%. So the
+// counters of a call with at most kCtrSpreadTiles tiles get a 128-byte line
+// each (kCtrStride words apart) in the sort's ping-pong buffer, which is
+// unused until the sort, when it has room for them: tracking at 640x480 /
+// 300k measured 6,213 -> 6,267 iterations/s (same box, two runs each; 256
+// words apart the same, 6,267). Batches of more tiles keep them in `ranges`:
+// their counters already span hundreds of lines, and the 8-frame mapping
+// window measured 2,418 -> 2,406 keyframe-iterations/s spread out.
+constexpr int kCtrStride = 32;
+constexpr int kCtrSpreadTiles = 4096;
+
+TileCtr tile_counters(uint32_t *ranges, const FrameTable &ft, int capacity, void *ws) {
+    const WsLayout L = layout(capacity);
+    if (ft.total_tiles <= kCtrSpreadTiles &&
+        (size_t)ft.total_tiles * kCtrStride * sizeof(uint32_t) <= sizeof(uint64_t) * (size_t)capacity)
+        return TileCtr{reinterpret_cast<uint32_t *>(static_cast<char *>(ws) + L.tmp), kCtrStride};
+    return TileCtr{ranges + 1, 2};
+}
+
 cudaError_t launch_bin_clear(uint32_t *ranges, const FrameTable &ft, int capacity, void *ws, cudaStream_t s) {
     int *misc = reinterpret_cast<int *>(static_cast<char *>(ws) + layout(capacity).misc);
-    const int n_words = 2 * ft.total_tiles;
-    const int clear_grid = n_words > 0 ? min((n_words + kThreads - 1) / kThreads, 4 * device_sm_count()) : 1;
-    return launch_chained(k_bin_clear, dim3(clear_grid), dim3(kThreads), 0, s, ranges, n_words, misc);
+    const int n = ft.total_tiles;
+    const int clear_grid = n > 0 ? min((n + kThreads - 1) / kThreads, 4 * device_sm_count()) : 1;
+    return launch_chained(k_bin_clear, dim3(clear_grid), dim3(kThreads), 0, s, tile_counters(ranges, ft, capacity, ws),
+                          n, misc);
 }
 
 cudaError_t launch_bin_tiles(const float *rec, const int *touched, int n_records, int n_per_frame,
@@ -627,6 +656,7 @@ cudaError_t launch_bin_tiles(const float *rec, const int *touched, int n_records
     uint64_t *low = reinterpret_cast<uint64_t *>(w + L.low);
     uint64_t *tmp = reinterpret_cast<uint64_t *>(w + L.tmp);
     int *misc = reinterpret_cast<int *>(w + L.misc);
+    const TileCtr tc = tile_counters(ranges, ft, capacity, ws);
     // low key = depth bits << 32 | record index; only the index bits that can be set are sorted
     const int rec_bits = bit_width((unsigned)(n_records > 0 ? n_records - 1 : 0));
     cudaError_t err;
@@ -638,13 +668,13 @@ cudaError_t launch_bin_tiles(const float *rec, const int *touched, int n_records
     auto count = large ? k_tile_count<kRecLarge> : k_tile_count<1>;
     auto fill = large ? k_tile_fill<kRecLarge> : k_tile_fill<1>;
     if (!counted && (err = launch_chained(count, dim3(grid), dim3(kThreads), 0, s, rec, touched, n_records, n_per_frame,
-                                          ft, ranges, status)) != cudaSuccess)
+                                          ft, tc, status)) != cudaSuccess)
         return err;
-    if ((err = launch_chained(k_tile_scan, dim3(1), dim3(kScanThreads), 0, s, ranges, ft.total_tiles, capacity, status,
-                              misc, order)) != cudaSuccess)
+    if ((err = launch_chained(k_tile_scan, dim3(1), dim3(kScanThreads), 0, s, ranges, tc, ft.total_tiles, capacity,
+                              status, misc, order)) != cudaSuccess)
         return err;
-    if ((err = launch_chained(fill, dim3(grid), dim3(kThreads), 0, s, rec, touched, n_records, n_per_frame, ft, ranges,
-                              low, capacity, status)) != cudaSuccess)
+    if ((err = launch_chained(fill, dim3(grid), dim3(kThreads), 0, s, rec, touched, n_records, n_per_frame, ft, tc, low,
+                              capacity, status)) != cudaSuccess)
         return err;
     if ((err = launch_chained(k_tile_sort, dim3(ft.total_tiles), dim3(kThreads), 0, s, low, tmp, ranges, order, misc,
                               ft.total_tiles, values, keys_out, rec_bits, status)) != cudaSuccess)

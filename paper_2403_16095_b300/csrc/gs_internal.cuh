@@ -97,16 +97,25 @@ void set_error_message(const char *msg);
 // read once per device and cached; api.cu); grid caps are multiples of it
 int device_sm_count();
 
+// The per-tile pair counters of a binning: tile t's counter is p[t stride].
+// Each (record, tile) pair of the count and fill passes adds to its tile's
+// counter with an atomic; see tile_counters (binning.cu) for where they live.
+struct TileCtr {
+    uint32_t *p;
+    int stride;
+};
+
 // ----------------------------------------------------------------- launchers
 // project.cu
-// tile_counts: NULL, or the tile counters (ranges) of a following binning,
-// zeroed by launch_bin_clear: the projection then also counts the pairs
+// tile_counts: p NULL, or the tile counters of a following binning
+// (tile_counters), zeroed by launch_bin_clear: the projection then also counts
+// the pairs
 cudaError_t launch_project(const GaussPtrs &g, int n, const FrameTable &ft, const float *T_cw, float jclamp,
-                           float nu_cull, int mode, float *rec, int *touched, float *jac, uint32_t *tile_counts,
+                           float nu_cull, int mode, float *rec, int *touched, float *jac, TileCtr tile_counts,
                            const int32_t *status, cudaStream_t s);
 cudaError_t launch_project_bf16(const float *anchors, const uint16_t *packed, int n, const FrameTable &ft,
                                 const float *T_cw, float jclamp, float nu_cull, int mode, float *rec, int *touched,
-                                float *jac, uint32_t *tile_counts, const int32_t *status, cudaStream_t s);
+                                float *jac, TileCtr tile_counts, const int32_t *status, cudaStream_t s);
 cudaError_t launch_project_bwd(const GaussPtrs &g, int n, const FrameTable &ft, const float *T_cw, float jclamp,
                                const float *rec, const float *grad2d, gs_grads grads, float *pose_partials,
                                int per_frame, double *pose_grad, unsigned *counters, const int32_t *status,
@@ -119,6 +128,8 @@ cudaError_t launch_bin_tiles(const float *rec, const int *touched, int n_records
                              bool counted = false);  // counted: clear + count already done (counting projection)
 // zeroes the tile counters and the binning's scalars (ws) ahead of a counting projection
 cudaError_t launch_bin_clear(uint32_t *ranges, const FrameTable &ft, int capacity, void *ws, cudaStream_t s);
+// where the binning of this call keeps its tile counters (ranges, or ws)
+TileCtr tile_counters(uint32_t *ranges, const FrameTable &ft, int capacity, void *ws);
 // render_fwd.cu
 // batch: list entries staged per batch at 16x16 and 32x32 tiles (256 or 512;
 // other values take 512); queue: NULL for one CTA per tile, else the two

@@ -76,20 +76,21 @@ __device__ __forceinline__ void warp_for_each_pair(const PairSrc &s, F &&f) {
     }
 }
 
-// Warp-aggregated claim of one slot per valid lane in the counter of its tile:
-// lanes with the same tile share one atomic (issued by the lowest of them).
-// Returns the lane's slot when want_slot (the atomic's old value + its rank
-// among its peers), else 0 and the atomic needs no return value. Records of a
-// warp are often neighbours in space (Morton-ordered storage), so most of a
-// warp's pairs tend to fall on a few tiles.
+// Warp-aggregated claim of one slot per valid lane in the counter of its tile
+// (tile t's counter at tc.p[t tc.stride]): lanes with the same tile share one
+// atomic (issued by the lowest of them). Returns the lane's slot when want_slot
+// (the atomic's old value + its rank among its peers), else 0 and the atomic
+// needs no return value. Records of a warp are often neighbours in space
+// (Morton-ordered storage), so most of a warp's pairs tend to fall on a few
+// tiles.
 template <bool WANT_SLOT>
-__device__ __forceinline__ uint32_t warp_claim(bool valid, int gt, uint32_t *ranges) {
+__device__ __forceinline__ uint32_t warp_claim(bool valid, int gt, TileCtr tc) {
     const int lane = threadIdx.x & 31;
     const uint32_t peers = __match_any_sync(0xffffffffu, valid ? gt : -1);
     const int leader = __ffs(peers) - 1;
     uint32_t base = 0;
     if (valid && lane == leader) {
-        uint32_t *ctr = &ranges[2 * (size_t)gt + 1];
+        uint32_t *ctr = tc.p + (size_t)gt * (size_t)tc.stride;
         if (WANT_SLOT)
             base = atomicAdd(ctr, (uint32_t)__popc(peers));
         else

@@ -200,7 +200,7 @@ __device__ __forceinline__ void write_culled(float *rec, int *touched, size_t r)
 }
 
 // COUNT: the projection also counts the (record, tile) pairs of the visible
-// records into the tile counters ranges[2 t + 1] (zeroed before the launch),
+// records into the binning's tile counters (zeroed before the launch),
 // with the same warp-balanced walk and warp-aggregated atomics as
 // k_tile_count, so that the binning can skip its count pass. Every lane then
 // stays to the end of the walk (no early return).
@@ -212,7 +212,7 @@ template <bool JAC, bool COUNT, class Src>
 __global__ void __launch_bounds__(kProjThreads, 4)
     k_project(Src src, int n, FrameTable ft, const float *__restrict__ T_cw, float jclamp, float nu_cull,
               float *__restrict__ rec, int *__restrict__ touched, float *__restrict__ jac,
-              uint32_t *__restrict__ ranges, const int32_t *__restrict__ status) {
+              TileCtr tc, const int32_t *__restrict__ status) {
     dep_wait();
     if (status[0] != 0) return;
     const int i = blockIdx.x * kProjThreads + threadIdx.x;
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(kProjThreads, 4)
             ps.tiles_x = fd.tiles_x;
         }
         if (__any_sync(0xffffffffu, ps.valid))
-            warp_for_each_pair(ps, [&](bool valid, int, int gt, uint32_t) { warp_claim<false>(valid, gt, ranges); });
+            warp_for_each_pair(ps, [&](bool valid, int, int gt, uint32_t) { warp_claim<false>(valid, gt, tc); });
     }
     if (!vis) return;
     const int ts = ft.tile;
@@ -518,32 +518,32 @@ __global__ void __launch_bounds__(kProjThreads)
 
 template <class Src>
 cudaError_t launch_src(const Src &src, int n, const FrameTable &ft, const float *T_cw, float jclamp, float nu_cull,
-                       int mode, float *rec, int *touched, float *jac, uint32_t *ranges, const int32_t *status,
+                       int mode, float *rec, int *touched, float *jac, TileCtr tc, const int32_t *status,
                        cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     dim3 grid((n + kProjThreads - 1) / kProjThreads, ft.n);
     const dim3 block(kProjThreads);
     const bool jacob = mode == GS_MODE_POSE;
-    if (ranges)
+    if (tc.p)
         return jacob ? launch_chained(k_project<true, true, Src>, grid, block, 0, s, src, n, ft, T_cw, jclamp, nu_cull,
-                                      rec, touched, jac, ranges, status)
+                                      rec, touched, jac, tc, status)
                      : launch_chained(k_project<false, true, Src>, grid, block, 0, s, src, n, ft, T_cw, jclamp, nu_cull,
-                                      rec, touched, jac, ranges, status);
+                                      rec, touched, jac, tc, status);
     return jacob ? launch_chained(k_project<true, false, Src>, grid, block, 0, s, src, n, ft, T_cw, jclamp, nu_cull,
-                                  rec, touched, jac, ranges, status)
+                                  rec, touched, jac, tc, status)
                  : launch_chained(k_project<false, false, Src>, grid, block, 0, s, src, n, ft, T_cw, jclamp, nu_cull,
-                                  rec, touched, jac, ranges, status);
+                                  rec, touched, jac, tc, status);
 }
 
 cudaError_t launch_project(const GaussPtrs &g, int n, const FrameTable &ft, const float *T_cw, float jclamp,
-                           float nu_cull, int mode, float *rec, int *touched, float *jac, uint32_t *tile_counts,
+                           float nu_cull, int mode, float *rec, int *touched, float *jac, TileCtr tile_counts,
                            const int32_t *status, cudaStream_t s) {
     return launch_src(F32Src{g}, n, ft, T_cw, jclamp, nu_cull, mode, rec, touched, jac, tile_counts, status, s);
 }
 
 cudaError_t launch_project_bf16(const float *anchors, const uint16_t *packed, int n, const FrameTable &ft,
                                 const float *T_cw, float jclamp, float nu_cull, int mode, float *rec, int *touched,
-                                float *jac, uint32_t *tile_counts, const int32_t *status, cudaStream_t s) {
+                                float *jac, TileCtr tile_counts, const int32_t *status, cudaStream_t s) {
     const BF16Src src{reinterpret_cast<const float4 *>(anchors), reinterpret_cast<const uint4 *>(packed)};
     return launch_src(src, n, ft, T_cw, jclamp, nu_cull, mode, rec, touched, jac, tile_counts, status, s);
 }

@@ -130,6 +130,7 @@ def _synthetic_records(n, cams, tile, seed, ties=True):
 @pytest.mark.parametrize("cams,tile,ties,n", [
     ([synth.Camera(128, 96, 1, 1, 0, 0)], 16, True, 3000),                  # 48 tiles
     ([synth.Camera(640, 480, 1, 1, 0, 0)], 16, False, 3000),                # 1200 tiles
+    ([synth.Camera(640, 480, 1, 1, 0, 0)], 16, "short", 20000),             # 1200 tiles, counters a line apart
     ([synth.Camera(1200, 680, 1, 1, 0, 0)], 8, True, 3000),                 # 12750 tiles
     ([synth.Camera(100, 70, 1, 1, 0, 0), synth.Camera(37, 53, 1, 1, 0, 0),
       synth.Camera(64, 64, 1, 1, 0, 0)], 16, True, 3000),                   # uneven frames, ragged
