@@ -291,11 +291,12 @@ def test_project_bin_equals_project_then_bin(storage, pose_mode):
                           np.minimum(lens[rb.order.cpu().numpy()] >> 2, 1023))
 
 
-@pytest.mark.parametrize("n", [1, 2, 31, 32, 33, 64, 65, 128, 129, 255, 256, 257])
+@pytest.mark.parametrize("n", [1, 2, 31, 32, 33, 64, 65, 128, 129, 255, 256, 257, 511, 512, 513])
 def test_bin_tiles_list_length_boundaries(n):
     """One tile holding exactly n pairs, across the boundaries of the sort paths
     (one warp in registers with 1, 2, 4 or 8 keys per lane below 256; a CTA
-    bitonic network from 256), with ties: keys equal the oracle's."""
+    bitonic network from 256, with 2 keys per thread up to 512 and 4 above),
+    with ties: keys equal the oracle's."""
     cams = [synth.Camera(16, 16, 1, 1, 0, 0)]
     rng = np.random.default_rng(9000 + n)
     rec = np.zeros((n, 16), np.float32)
