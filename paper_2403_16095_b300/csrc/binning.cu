@@ -21,7 +21,7 @@
 //   k_tile_fill   each pair claims a slot in its tile's bucket (the cursor's
 //                 atomic) and stores the low key (depth bits << 32 | record).
 //   k_tile_sort   sorts each bucket's low keys: buckets under 256 keys by one
-//                 warp in registers; up to 1024 keys by a CTA bitonic network
+//                 warp in registers; up to 512 keys by a CTA bitonic network
 //                 in registers and shared memory; larger ones by a stable LSD
 //                 radix sort over the four 8-bit depth digits (digits constant
 //                 over the bucket are skipped) in shared memory up to 2048 keys,
@@ -45,7 +45,7 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kScanThreads = 1024;
 constexpr int kPassUnroll = 4;  // 32-key groups per step of a radix pass (loads issued together)
-constexpr int kRadixMinKeys = 1024;  // CTA lists above this (up to kSmemKeys) take the shared-memory radix sort
+constexpr int kRadixMinKeys = 512;   // CTA lists above this (up to kSmemKeys) take the shared-memory radix sort
 constexpr int kSmemKeys = 2048;  // bucket size sorted entirely in shared memory
 
 __device__ __forceinline__ bool status_ok(const int32_t *status) { return status[0] == 0; }
@@ -511,7 +511,10 @@ __global__ void __launch_bounds__(kThreads, 4)
     if (n > kRadixMinKeys && n <= kSmemKeys) {
         // LSD radix over the depth digits in shared memory (4 passes of ~25
         // instructions per key against ~6 per key for each of the 45-66 stages
-        // of a bitonic network), then the equal-depth fix-up
+        // of a bitonic network), then the equal-depth fix-up. From 513 keys:
+        // above 1,024 only, tracking at 640x480 / 300k measured 0.6 us per
+        // iteration slower (6,269 / 6,271 against 6,277 / 6,285 iterations/s,
+        // same box); from 257 keys, slower again (6,240 / 6,258)
         for (int i = tid; i < n; i += kThreads) s_a[i] = low_keys[s + i];
         __syncthreads();
         uint64_t *a = s_a, *b = s_b;
@@ -542,12 +545,11 @@ __global__ void __launch_bounds__(kThreads, 4)
     if (n <= kSmemKeys) {
         int np = kThreads;
         while (np < n) np <<= 1;
-        static_assert(kRadixMinKeys <= 4 * kThreads, "bitonic lists fit 4 keys per thread");
-        switch (np / kThreads) {  // n <= kRadixMinKeys here
-            case 1: cta_sort_regs<1>(low_keys + s, n, s_a); break;
-            case 2: cta_sort_regs<2>(low_keys + s, n, s_a); break;
-            default: cta_sort_regs<4>(low_keys + s, n, s_a); break;
-        }
+        static_assert(kRadixMinKeys <= 2 * kThreads, "bitonic lists fit 2 keys per thread");
+        if (np == kThreads)  // n <= kRadixMinKeys here
+            cta_sort_regs<1>(low_keys + s, n, s_a);
+        else
+            cta_sort_regs<2>(low_keys + s, n, s_a);
         // cta_sort_regs leaves the sorted keys in s_a[0, n)
         for (int i = tid; i < n; i += kThreads) {
             const uint64_t k = s_a[i];

@@ -295,7 +295,7 @@ def test_project_bin_equals_project_then_bin(storage, pose_mode):
 def test_bin_tiles_list_length_boundaries(n):
     """One tile holding exactly n pairs, across the boundaries of the sort paths
     (one warp in registers with 1, 2, 4 or 8 keys per lane below 256; a CTA
-    bitonic network from 256, with 2 keys per thread up to 512 and 4 above),
+    bitonic network from 256 to 512 keys; the shared-memory radix sort above),
     with ties: keys equal the oracle's."""
     cams = [synth.Camera(16, 16, 1, 1, 0, 0)]
     rng = np.random.default_rng(9000 + n)
