@@ -83,6 +83,14 @@ DRAM_BYTES_PER_ITERATION = 0.552448e6 + 3.041024e6
 PREC16_FUSED_DRAM_BYTES_PER_LAUNCH = 104.30976e6 + 2.601984e6
 PREC32_FUSED_DRAM_BYTES_PER_LAUNCH = 104.235264e6 + 3.001088e6
 PREC32_GIVEN_ORDER_FUSED_DRAM_BYTES_PER_LAUNCH = None  # not captured for the current kernel
+# DRAM bytes of one step's FULL backward (k_render_bwd<16, FULL> + the
+# projection adjoint k_project_bwd) on the mapping window and on the uneven
+# batch, per-tile schedule at tile 16, staging batch 512 (the blend backward's
+# bytes at 256 measured the same within 0.1%), maps in Morton order; ncu, one
+# pass per launch (profiles/dram_bwd_full_mapping-uneven.md); None for other
+# configurations and once either kernel changes.
+MAP_BWD_DRAM_BYTES_PER_STEP = (280.562944e6 + 36.974080e6) + (140.781056e6 + 27.464192e6)
+UNEVEN_BWD_DRAM_BYTES_PER_STEP = (621.399808e6 + 87.581440e6) + (474.705152e6 + 103.974656e6)
 FP32_LANES_PER_SM = 128
 
 
@@ -667,6 +675,13 @@ def run_batch(a):
                "sample": f"the FP64 oracle's forward + analytic FULL gradient of frame {f0} (640x480) of the batch, "
                          f"{g.n // 1000}k Gaussians, one frame"}
     sched_name = "persistent" if sched == A.GS_SCHED_PERSISTENT else "per-tile"
+    # the captured configurations only (the autotuner's picks on the default workloads)
+    cap_bytes = {"mapping": MAP_BWD_DRAM_BYTES_PER_STEP, "uneven": UNEVEN_BWD_DRAM_BYTES_PER_STEP}[a.workload]
+    bwd_traffic = (cap_bytes if (sched_name == "per-tile" and tile == 16 and a.order == "morton" and ws == 1)
+                   else None)
+    bwd_traffic_src = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_render_bwd + k_project_bwd, "
+                       "one step, caches flushed before each launch" if bwd_traffic else
+                       "not captured for this configuration")
     line = {"metric": metric, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": total_ms / a.steps, "higher_is_better": True,
             "scaling": "strong" if a.workload == "mapping" else "weak", "vs_baseline": None,
@@ -682,8 +697,8 @@ def run_batch(a):
                        "pairs": int(r.read_status()[1]), "contributions": E},
             "roofline": {"kernel": f"k_render_bwd<{tile},FULL> + k_project_bwd", "bound": "alu",
                          "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                         "traffic": None, "flop_per_contribution": BWD_FULL_FLOP_PER_CONTRIB,
-                         "avg_launch_ms": bwd_ms},
+                         "traffic": bwd_traffic, "traffic_source": bwd_traffic_src,
+                         "flop_per_contribution": BWD_FULL_FLOP_PER_CONTRIB, "avg_launch_ms": bwd_ms},
             # projection, 5 binning kernels, forward, FULL backward, projection adjoint
             "cpu_baseline": cpu, "gpu_launches": 9 * a.steps, "clocks": clk}
     print(json.dumps(line), flush=True)

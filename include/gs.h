@@ -350,7 +350,8 @@ gs_status gs_render_fwd(const gs_projected *proj, const gs_tiles *tiles, int n_f
  * zero-filled before its first use (one cudaMemset after allocating it): its
  * last 256 bytes hold the arrival counters of that reduction, which every call
  * leaves at zero again, so no call clears them. A ws whose counters are not
- * zero gives a wrong pose_grad.                                              */
+ * zero gives a wrong pose_grad. The FULL backward takes a record's
+ * visibility from proj->tiles_touched (> 0), as gs_project wrote it.         */
 int gs_pose_partials_per_frame(int mode, int n_gaussians, int n_frames, const gs_camera *cams, int tile);
 size_t gs_render_bwd_workspace_size(int n_records, int mode);
 gs_status gs_render_bwd(const gs_projected *proj, const gs_tiles *tiles, int n_frames,

@@ -399,9 +399,14 @@ def gs_render_bwd(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tensor, pose
                   obs_depth: Optional[torch.Tensor], fwd: dict, dL: Optional[dict], loss: Optional[dict],
                   grads: Optional[dict], pose_partials: torch.Tensor, pose_grad: Optional[torch.Tensor],
                   status: torch.Tensor, ws: torch.Tensor, stream=None, order: Optional[torch.Tensor] = None,
-                  queue: Optional[torch.Tensor] = None) -> None:
+                  queue: Optional[torch.Tensor] = None, touched: Optional[torch.Tensor] = None) -> None:
+    """touched: the projection's tiles_touched, required in FULL mode (each
+    record's visibility); POSE mode does not read it."""
     F = len(cams)
-    proj = gs_projected(n_gaussians, F, _ptr(rec, torch.float32, "rec"), 1,
+    if touched is None and opts.mode == GS_MODE_FULL:
+        raise ValueError("gs_render_bwd: FULL mode needs the projection's tiles_touched (touched=)")
+    tt = _ptr(touched, torch.int32, "touched", n_gaussians * F) if touched is not None else 1  # 1: not read
+    proj = gs_projected(n_gaussians, F, _ptr(rec, torch.float32, "rec"), tt,
                         _ptr(pose_jac, torch.float32, "pose_jac"))
     tiles = gs_tiles(values.numel(), ranges.numel() // 2, _ptr(values, torch.int32), None,
                      _ptr(ranges, torch.int32), _ptr(order, torch.int32, "order", ranges.numel() // 2),

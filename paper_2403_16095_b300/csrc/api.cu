@@ -418,7 +418,7 @@ gs_status gs_render_bwd(const gs_projected *proj, const gs_tiles *tiles, int n_f
                                    ip, lp, grad2d, pose_partials, per_frame, nullptr, nullptr, status, opts->batch,
                                    queue, stream)) != cudaSuccess)
         return cuda_status(e, "gs_render_bwd");
-    return cuda_status(gs::launch_project_bwd(gauss_ptrs(g), N, ft, T_cw, opts->jclamp, proj->rec, grad2d, *grads,
+    return cuda_status(gs::launch_project_bwd(gauss_ptrs(g), N, ft, T_cw, opts->jclamp, proj->tiles_touched, grad2d, *grads,
                                               pose_partials, per_frame, pose_grad, counters, status, stream),
                        "gs_render_bwd (projection adjoint)");
 }

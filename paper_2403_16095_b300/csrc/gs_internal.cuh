@@ -116,8 +116,10 @@ cudaError_t launch_project(const GaussPtrs &g, int n, const FrameTable &ft, cons
 cudaError_t launch_project_bf16(const float *anchors, const uint16_t *packed, int n, const FrameTable &ft,
                                 const float *T_cw, float jclamp, float nu_cull, int mode, float *rec, int *touched,
                                 float *jac, TileCtr tile_counts, const int32_t *status, cudaStream_t s);
+// touched: the projection's tiles_touched (a record is visible iff > 0);
+// grad2d: the blend backward's per-record accumulators
 cudaError_t launch_project_bwd(const GaussPtrs &g, int n, const FrameTable &ft, const float *T_cw, float jclamp,
-                               const float *rec, const float *grad2d, gs_grads grads, float *pose_partials,
+                               const int *touched, const float *grad2d, gs_grads grads, float *pose_partials,
                                int per_frame, double *pose_grad, unsigned *counters, const int32_t *status,
                                cudaStream_t s);
 // binning.cu

@@ -136,7 +136,7 @@ class Rasterizer:
         A.gs_render_bwd(self.N, self.cams, self.opts, self.rec, self.jac, self.values, self.ranges, T_cw, g,
                         obs_depth, self.img, dL, loss, grads, self.pose_partials,
                         self.pose_grad if fused_pose else None, self.status, self.bwd_ws, stream, order=self.order,
-                        queue=self.queue)
+                        queue=self.queue, touched=self.touched)
 
     def fwd_bwd_pose(self, loss: dict, images: bool = False, fused_pose: bool = True, stream=None,
                      adam_state=None, adam=None, T_cw=None) -> None:

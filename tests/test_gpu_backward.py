@@ -98,6 +98,35 @@ def test_full_mode_gradients_match_oracle(w):
     _rel_check("pose", r.pose_grad[0].cpu().numpy(), og["pose"], elem=1e-5, norm=1e-5)
 
 
+def test_full_mode_repeated_calls_on_one_workspace():
+    """Three FULL backward calls on one Rasterizer (one workspace), two of
+    them with a forward between, give the same gradients, up to the arrival
+    order of the per-record accumulators' atomics, and match the oracle: no
+    call sees another's accumulators, and the projection adjoint's
+    visibility (tiles_touched) is the projection's."""
+    from paper_2403_16095_b300 import _abi as A
+    sc, cam, T, tc, td = _case()
+    g = to_gpu_gaussians(sc)
+    Tt = poses_gpu(T)
+    r = _setup(A.GS_MODE_FULL, sc, cam, T, 16)
+    obs = torch.from_numpy(np.ascontiguousarray(td)).cuda().reshape(-1)
+    runs = []
+    for k in range(3):
+        if k != 1:  # the second call reuses the first call's forward
+            r.render(g, Tt, obs)
+        grads = {p: torch.empty_like(getattr(g, p)) for p in PARAMS}
+        r.backward(obs_depth=obs, loss=_loss_dict(tc, td, W_ALL), g=g, T_cw=Tt, grads=grads)
+        torch.cuda.synchronize()
+        assert r.read_status()[0] == 0
+        runs.append({p: v.cpu().numpy().astype(np.float64) for p, v in grads.items()})
+    og = oracle.grad(f32_scene(sc), cam, T, _spec(W_ALL, tc, td))
+    for p in PARAMS:
+        scale = np.abs(runs[0][p]).max()
+        for k in (1, 2):
+            assert np.abs(runs[k][p] - runs[0][p]).max() <= 1e-5 * scale, (p, k)
+        _rel_check(p, runs[2][p], og[p])
+
+
 def test_pose_mode_matches_full_mode_and_oracle():
     """P10c: the per-pixel Jacobian contraction (POSE) and the per-Gaussian
     reverse chain (FULL) give the same pose gradient."""
