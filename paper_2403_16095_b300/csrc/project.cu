@@ -215,8 +215,14 @@ __global__ void __launch_bounds__(kProjThreads, 4)
               TileCtr tc, const int32_t *__restrict__ status) {
     dep_wait();
     if (status[0] != 0) return;
-    const int i = blockIdx.x * kProjThreads + threadIdx.x;
-    const int f = blockIdx.y;
+    // frame fastest: the CTAs of one block of Gaussians for every frame are
+    // launched together, so a batch's frames read the block's parameters from
+    // DRAM once and from L2 after that (uneven 16-frame batch 2,006 -> 2,035
+    // frames/s, mapping window 2,440 -> 2,454 keyframe-iterations/s, same box,
+    // two runs each)
+    const unsigned nf = (unsigned)ft.n;
+    const int f = nf == 1u ? 0 : (int)(blockIdx.x % nf);
+    const int i = (int)(nf == 1u ? blockIdx.x : blockIdx.x / nf) * kProjThreads + threadIdx.x;
     if (!COUNT && i >= n) return;
     const FrameDesc &fd = ft.f[f];
     const size_t r = (size_t)f * n + i;
@@ -526,7 +532,7 @@ cudaError_t launch_src(const Src &src, int n, const FrameTable &ft, const float 
                        int mode, float *rec, int *touched, float *jac, TileCtr tc, const int32_t *status,
                        cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    dim3 grid((n + kProjThreads - 1) / kProjThreads, ft.n);
+    dim3 grid((unsigned)((n + kProjThreads - 1) / kProjThreads) * (unsigned)ft.n);
     const dim3 block(kProjThreads);
     const bool jacob = mode == GS_MODE_POSE;
     if (tc.p)
