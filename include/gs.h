@@ -128,7 +128,11 @@ typedef struct {
     int n_gaussians;      /* N                                                 */
     int n_frames;         /* F; records = F * N                                */
     float *rec;           /* [F*N][16]                                         */
-    int *tiles_touched;   /* [F*N] tiles overlapped (0 if culled)              */
+    int *tiles_touched;   /* [F*N] tiles overlapped (0 if culled); read by the
+                             binning and the FULL-mode gs_render_bwd. The blend
+                             calls that read only rec (gs_render_fwd, the POSE
+                             backward, gs_render_fwd_bwd_pose, gs_nu_accumulate)
+                             accept NULL here                                   */
     float *pose_jac;      /* [F*N][6][6] d(mean2d.x, mean2d.y, A, B, C, z)/d(rho, phi),
                              written in POSE mode only; may be NULL otherwise
                              (and when F*N = 0)                                 */

@@ -377,7 +377,7 @@ def gs_render_fwd(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tensor, valu
                   ranges: torch.Tensor, obs_depth: Optional[torch.Tensor], out: dict, status: torch.Tensor,
                   stream=None, order: Optional[torch.Tensor] = None, queue: Optional[torch.Tensor] = None) -> None:
     F = len(cams)
-    proj = gs_projected(n_gaussians, F, _ptr(rec, torch.float32, "rec"), 1, None)  # touched unused
+    proj = gs_projected(n_gaussians, F, _ptr(rec, torch.float32, "rec"), None, None)  # touched not read
     tiles = gs_tiles(values.numel(), ranges.numel() // 2, _ptr(values, torch.int32), None,
                      _ptr(ranges, torch.int32), _ptr(order, torch.int32, "order", ranges.numel() // 2),
                      _ptr(queue, torch.int32, "queue", 2))
@@ -405,7 +405,7 @@ def gs_render_bwd(n_gaussians: int, cams, opts: gs_opts, rec: torch.Tensor, pose
     F = len(cams)
     if touched is None and opts.mode == GS_MODE_FULL:
         raise ValueError("gs_render_bwd: FULL mode needs the projection's tiles_touched (touched=)")
-    tt = _ptr(touched, torch.int32, "touched", n_gaussians * F) if touched is not None else 1  # 1: not read
+    tt = _ptr(touched, torch.int32, "touched", n_gaussians * F)  # POSE mode: may be None (not read)
     proj = gs_projected(n_gaussians, F, _ptr(rec, torch.float32, "rec"), tt,
                         _ptr(pose_jac, torch.float32, "pose_jac"))
     tiles = gs_tiles(values.numel(), ranges.numel() // 2, _ptr(values, torch.int32), None,
@@ -441,7 +441,7 @@ def gs_nu_accumulate(n_gaussians: int, cams, rec: torch.Tensor, values: torch.Te
                      fwd: dict, nu_num: torch.Tensor, nu_cnt: torch.Tensor, dominant: Optional[torch.Tensor],
                      status: torch.Tensor, stream=None) -> None:
     F = len(cams)
-    proj = gs_projected(n_gaussians, F, _ptr(rec, torch.float32, "rec"), 1, None)
+    proj = gs_projected(n_gaussians, F, _ptr(rec, torch.float32, "rec"), None, None)  # touched not read
     tiles = gs_tiles(values.numel(), 0, _ptr(values, torch.int32, "values"), None, None)
     _check(lib.gs_nu_accumulate(C.byref(proj), C.byref(tiles), F, cameras(cams),
                                 _ptr(obs_depth, torch.float32, "obs_depth"), C.byref(_image(fwd)),
@@ -479,7 +479,7 @@ def gs_render_fwd_bwd_pose(n_gaussians: int, cams, opts: gs_opts, rec: torch.Ten
     """Tracking pass: forward + POSE backward of the colour/depth loss in one launch,
     optionally followed (in the same launch) by the Adam step on the pose."""
     F = len(cams)
-    proj = gs_projected(n_gaussians, F, _ptr(rec, torch.float32, "rec"), 1,
+    proj = gs_projected(n_gaussians, F, _ptr(rec, torch.float32, "rec"), None,
                         _ptr(pose_jac, torch.float32, "pose_jac"))
     tiles = gs_tiles(values.numel(), ranges.numel() // 2, _ptr(values, torch.int32), None,
                      _ptr(ranges, torch.int32), _ptr(order, torch.int32, "order", ranges.numel() // 2))

@@ -79,12 +79,15 @@ gs_status sched_queue(const gs_opts *o, const gs_tiles *t, unsigned **queue) {
     return GS_OK;
 }
 
-gs_status check_proj(const gs_projected *p, int n_frames) {
+// need_touched: the call reads (or writes) tiles_touched; the blend calls read
+// only rec, and for them tiles_touched may be NULL
+gs_status check_proj(const gs_projected *p, int n_frames, bool need_touched = true) {
     if (!p) return fail(GS_ERR_INVALID_ARG, "projected is NULL");
     if (p->n_gaussians < 0) return fail(GS_ERR_INVALID_ARG, "n_gaussians < 0");
     if (p->n_frames != n_frames) return fail(GS_ERR_INVALID_ARG, "projected.n_frames=%d != n_frames=%d", p->n_frames, n_frames);
     if ((long long)p->n_gaussians * n_frames > (long long)INT_MAX) return fail(GS_ERR_INVALID_ARG, "records exceed 2^31-1");
-    if (p->n_gaussians > 0 && (!p->rec || !p->tiles_touched)) return fail(GS_ERR_INVALID_ARG, "rec/tiles_touched NULL");
+    if (p->n_gaussians > 0 && !p->rec) return fail(GS_ERR_INVALID_ARG, "rec NULL");
+    if (p->n_gaussians > 0 && need_touched && !p->tiles_touched) return fail(GS_ERR_INVALID_ARG, "tiles_touched NULL");
     if (!aligned(p->rec, 16)) return fail(GS_ERR_INVALID_ARG, "rec must be 16-byte aligned");
     return GS_OK;
 }
@@ -318,7 +321,7 @@ gs_status gs_render_fwd(const gs_projected *proj, const gs_tiles *tiles, int n_f
     GS_TRY(check_opts(opts));
     gs::FrameTable ft;
     GS_TRY(make_frames(n_frames, cams, opts->tile, ft));
-    GS_TRY(check_proj(proj, n_frames));
+    GS_TRY(check_proj(proj, n_frames, false));
     GS_TRY(check_tiles(tiles, ft));
     if (!out || !out->color || !out->T_final || !out->n_last) return fail(GS_ERR_INVALID_ARG, "image color/T_final/n_last required");
     if (!status) return fail(GS_ERR_INVALID_ARG, "status NULL");
@@ -356,7 +359,7 @@ gs_status gs_render_bwd(const gs_projected *proj, const gs_tiles *tiles, int n_f
     if (mode != GS_MODE_POSE && mode != GS_MODE_FULL) return fail(GS_ERR_INVALID_ARG, "backward needs POSE or FULL mode");
     gs::FrameTable ft;
     GS_TRY(make_frames(n_frames, cams, opts->tile, ft));
-    GS_TRY(check_proj(proj, n_frames));
+    GS_TRY(check_proj(proj, n_frames, opts->mode == GS_MODE_FULL));
     GS_TRY(check_tiles(tiles, ft));
     if (!status || !pose_partials) return fail(GS_ERR_INVALID_ARG, "status/pose_partials NULL");
     if (!fwd || !fwd->T_final || !fwd->n_last) return fail(GS_ERR_INVALID_ARG, "forward T_final/n_last required");
@@ -431,7 +434,7 @@ gs_status gs_render_fwd_bwd_pose(const gs_projected *proj, const gs_tiles *tiles
     if (opts->mode != GS_MODE_POSE) return fail(GS_ERR_INVALID_ARG, "the tracking pass needs POSE mode");
     gs::FrameTable ft;
     GS_TRY(make_frames(n_frames, cams, opts->tile, ft));
-    GS_TRY(check_proj(proj, n_frames));
+    GS_TRY(check_proj(proj, n_frames, false));
     GS_TRY(check_tiles(tiles, ft));
     if (!status || !pose_partials) return fail(GS_ERR_INVALID_ARG, "status/pose_partials NULL");
     if (!proj->pose_jac && proj->n_gaussians > 0) return fail(GS_ERR_INVALID_ARG, "POSE mode needs projected.pose_jac");
@@ -482,7 +485,7 @@ gs_status gs_nu_accumulate(const gs_projected *proj, const gs_tiles *tiles, int 
                            int32_t *dominant, const int32_t *status, gs_stream stream) {
     gs::FrameTable ft;
     GS_TRY(make_frames(n_frames, cams, 16, ft));
-    GS_TRY(check_proj(proj, n_frames));
+    GS_TRY(check_proj(proj, n_frames, false));
     if (!tiles || !tiles->values) return fail(GS_ERR_INVALID_ARG, "tiles.values NULL");
     if (!fwd || !fwd->dom_pos || !fwd->dom_weight)
         return fail(GS_ERR_INVALID_ARG, "fwd.dom_pos and fwd.dom_weight (from gs_render_fwd) required");
