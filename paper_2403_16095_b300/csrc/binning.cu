@@ -22,13 +22,14 @@
 //                 atomic) and stores the low key (depth bits << 32 | record).
 //   k_tile_sort   sorts each bucket's low keys: buckets under 256 keys by one
 //                 warp in registers; up to 512 keys by a CTA bitonic network
-//                 in registers and shared memory; larger ones by a stable LSD
-//                 radix sort over the four 8-bit depth digits (digits constant
-//                 over the bucket are skipped) in shared memory up to 2048 keys,
-//                 ping-ponging in global memory beyond, after which each run of
-//                 equal depth is put in record order (runs longer than 32 keys:
-//                 a full LSD pass over the record-index digits first, then the
-//                 depth digits). Low keys are
+//                 in registers and shared memory; larger ones by two stable LSD
+//                 passes over the depth quantised to 16 bits over the bucket's
+//                 depth range (in shared memory up to 2048 keys, ping-ponging
+//                 in global memory beyond), after which each run of equal
+//                 quantised depth is put in full-key order (runs longer than 32
+//                 keys: a full LSD sort over the record-index digits, then the
+//                 depth digits; digits constant over the bucket are skipped).
+//                 Low keys are
 //                 unique within a bucket, so the order of the atomic fill does
 //                 not matter: the output is bit-exact, the same as a stable sort
 //                 of the 64-bit keys emitted in record order, and independent of
@@ -246,14 +247,35 @@ __device__ __forceinline__ uint32_t cta_excl_scan(uint32_t v, uint32_t *s_warp) 
     return pre + x - v;
 }
 
-// One stable LSD pass of the CTA over n keys: src -> dst by the 8-bit digit at
-// `shift`. Warp w owns the contiguous segment [w seg, (w + 1) seg) of src: it
+// 8-bit digits of a key for the LSD passes: the key's own bits at `shift`, or
+// a byte of its depth quantised to 16 bits over the bucket's depth range,
+// q = ((z - lo) mul) >> 32 with z the depth bits (high word), which is
+// monotone in z (positive FP32 depths order as their bits).
+struct BitDigit {
+    int shift;
+    __device__ __forceinline__ uint32_t operator()(uint64_t k) const { return (uint32_t)(k >> shift) & (kRadix - 1); }
+};
+struct DepthQ {
+    uint32_t lo, mul;
+    __device__ __forceinline__ uint32_t q(uint64_t k) const {
+        return (uint32_t)(((uint64_t)((uint32_t)(k >> 32) - lo) * mul) >> 32);
+    }
+};
+struct QDigit {
+    DepthQ dq;
+    int shift;
+    __device__ __forceinline__ uint32_t operator()(uint64_t k) const { return (dq.q(k) >> shift) & (kRadix - 1); }
+};
+
+// One stable LSD pass of the CTA over n keys: src -> dst by the 8-bit digit
+// dig(key). Warp w owns the contiguous segment [w seg, (w + 1) seg) of src: it
 // counts its segment's digits into its own histogram row, one CTA scan turns
 // the rows (digit-major, warp-minor) into output cursors, and each warp then
 // scatters its segment in order with warp barriers only. Returns false (dst
 // untouched, src still current) when all n keys share the digit.
-__device__ __forceinline__ bool cta_radix_pass(const uint64_t *src, uint64_t *dst, int n, int shift, uint32_t (*s_wh)[kRadix],
-                               uint32_t *s_warp) {
+template <class Dig>
+__device__ __forceinline__ bool cta_radix_pass(const uint64_t *src, uint64_t *dst, int n, Dig dig,
+                                               uint32_t (*s_wh)[kRadix], uint32_t *s_warp) {
     static_assert(kThreads == kRadix, "one digit per thread in the scan");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 #pragma unroll
@@ -270,7 +292,7 @@ __device__ __forceinline__ bool cta_radix_pass(const uint64_t *src, uint64_t *ds
 #pragma unroll
         for (int u = 0; u < kPassUnroll; ++u) {
             const int i = base + 32 * u + lane;
-            dg[u] = i < hi ? ((uint32_t)(src[i] >> shift) & (kRadix - 1)) : (uint32_t)kRadix;
+            dg[u] = i < hi ? dig(src[i]) : (uint32_t)kRadix;
         }
 #pragma unroll
         for (int u = 0; u < kPassUnroll; ++u) {
@@ -304,7 +326,7 @@ __device__ __forceinline__ bool cta_radix_pass(const uint64_t *src, uint64_t *ds
         for (int u = 0; u < kPassUnroll; ++u) {
             const bool active = base + 32 * u + lane < hi;
             const uint64_t key = kg[u];
-            const uint32_t d = active ? ((uint32_t)(key >> shift) & (kRadix - 1)) : (uint32_t)kRadix;
+            const uint32_t d = active ? dig(key) : (uint32_t)kRadix;
             const uint32_t peers = __match_any_sync(0xffffffffu, d);
             const uint32_t rank = __popc(peers & lt_mask);
             const uint32_t off = active ? s_wh[warp][d] : 0u;
@@ -318,20 +340,22 @@ __device__ __forceinline__ bool cta_radix_pass(const uint64_t *src, uint64_t *ds
     return true;
 }
 
-// Keys sorted by their high 32 bits (depth) only: put every run of equal depth
-// in record order (low bits), the run's first position doing an insertion sort
-// of the run in place. Runs are disjoint and other threads read only the depth
-// bits of a run, which the sort does not change. Returns true for the whole CTA
-// when some run is longer than kMaxTieRun (left for a full sort instead).
+// Keys sorted by a run key rk(key) that is monotone in the full key (the
+// quantised depth): put every run of equal rk in full-key order (depth bits,
+// then record), the run's first position doing an insertion sort of the run in
+// place. Runs are disjoint and other threads read only the run keys of a run,
+// which the sort does not change. Returns true for the whole CTA when some run
+// is longer than kMaxTieRun (left for a full sort instead).
 constexpr int kMaxTieRun = 32;
-__device__ __forceinline__ bool cta_fix_depth_ties(uint64_t *a, int n) {
+template <class RunKey>
+__device__ __forceinline__ bool cta_fix_runs(uint64_t *a, int n, RunKey rk) {
     int bad = 0;
     for (int i = threadIdx.x; i < n; i += kThreads) {
-        const uint32_t z = (uint32_t)(a[i] >> 32);
-        if (i + 1 >= n || (uint32_t)(a[i + 1] >> 32) != z) continue;
-        if (i > 0 && (uint32_t)(a[i - 1] >> 32) == z) continue;  // not the first of its run
+        const uint32_t z = rk(a[i]);
+        if (i + 1 >= n || rk(a[i + 1]) != z) continue;
+        if (i > 0 && rk(a[i - 1]) == z) continue;  // not the first of its run
         int j = i + 2;
-        while (j < n && j - i <= kMaxTieRun && (uint32_t)(a[j] >> 32) == z) ++j;
+        while (j < n && j - i <= kMaxTieRun && rk(a[j]) == z) ++j;
         if (j - i > kMaxTieRun) {
             bad = 1;
             continue;
@@ -347,6 +371,75 @@ __device__ __forceinline__ bool cta_fix_depth_ties(uint64_t *a, int n) {
         }
     }
     return __syncthreads_or(bad) != 0;
+}
+
+// Minimum and maximum of the depth bits (high words) of a[0, n), CTA-wide.
+__device__ __forceinline__ void cta_depth_range(const uint64_t *a, int n, uint32_t (*s_mm)[kWarps], uint32_t &lo,
+                                                uint32_t &hi) {
+    uint32_t mn = 0xffffffffu, mx = 0u;
+    for (int i = threadIdx.x; i < n; i += kThreads) {
+        const uint32_t z = (uint32_t)(a[i] >> 32);
+        mn = min(mn, z);
+        mx = max(mx, z);
+    }
+    mn = __reduce_min_sync(0xffffffffu, mn);
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        s_mm[0][warp] = mn;
+        s_mm[1][warp] = mx;
+    }
+    __syncthreads();
+    lo = s_mm[0][0];
+    hi = s_mm[1][0];
+#pragma unroll
+    for (int w = 1; w < kWarps; ++w) {
+        lo = min(lo, s_mm[0][w]);
+        hi = max(hi, s_mm[1][w]);
+    }
+    __syncthreads();
+}
+
+struct QRun {
+    DepthQ dq;
+    __device__ __forceinline__ uint32_t operator()(uint64_t k) const { return dq.q(k); }
+};
+
+// Sorts a bucket of n > kRadixMinKeys low keys by the full key (depth bits,
+// then record), a[0, n) with b[0, n) as the other buffer, and returns the one
+// that holds the result. Two stable LSD passes over the depth quantised to 16
+// bits over the bucket's range (DepthQ, mul = 65535 2^32 / (hi - lo)) order the
+// keys by quantised depth; each run of equal quantised depth is then put in
+// full-key order in place. Quantised depth is monotone in the key, so this is
+// the full-key order, in 2 passes where the 32 depth bits take 4. A run longer
+// than kMaxTieRun (a tile whose depths crowd into a few quanta, or many equal
+// depths) sends the bucket to a full LSD sort over the record-index and depth
+// digits.
+__device__ uint64_t *cta_sort_bucket(uint64_t *a, uint64_t *b, int n, int rec_bits, uint32_t (*s_wh)[kRadix],
+                                     uint32_t *s_warp, uint32_t (*s_mm)[kWarps]) {
+    uint32_t lo, hi;
+    cta_depth_range(a, n, s_mm, lo, hi);
+    const uint32_t mul =
+        hi > lo ? (uint32_t)min((unsigned long long)0xffffffffu, (65535ull << 32) / (unsigned long long)(hi - lo)) : 0u;
+    const DepthQ dq{lo, mul};
+    for (int shift = 0; shift < 16; shift += kRadixBits) {
+        if (cta_radix_pass(a, b, n, QDigit{dq, shift}, s_wh, s_warp)) {
+            uint64_t *t = a;
+            a = b;
+            b = t;
+        }
+    }
+    if (cta_fix_runs(a, n, QRun{dq})) {
+        for (int shift = 0; shift < 64; shift += kRadixBits) {
+            if (shift >= rec_bits && shift < 32) continue;
+            if (cta_radix_pass(a, b, n, BitDigit{shift}, s_wh, s_warp)) {
+                uint64_t *t = a;
+                a = b;
+                b = t;
+            }
+        }
+    }
+    return a;
 }
 
 // ---------------------------------------------------------------------------
@@ -487,6 +580,7 @@ __global__ void __launch_bounds__(kThreads, 4)
     __shared__ uint64_t s_a[kSmemKeys], s_b[kSmemKeys];
     __shared__ uint32_t s_wh[kWarps][kRadix];
     __shared__ uint32_t s_warp[kWarps];
+    __shared__ uint32_t s_mm[2][kWarps];
     if (!status_ok(status)) return;
     const int tid = threadIdx.x;
     const int n_large = order ? misc[1] : n_tiles;
@@ -509,32 +603,16 @@ __global__ void __launch_bounds__(kThreads, 4)
     const int n = (int)(e - s);
     if (n <= 0) return;
     if (n > kRadixMinKeys && n <= kSmemKeys) {
-        // LSD radix over the depth digits in shared memory (4 passes of ~25
+        // LSD radix over the quantised depth in shared memory (2 passes of ~25
         // instructions per key against ~6 per key for each of the 45-66 stages
-        // of a bitonic network), then the equal-depth fix-up. From 513 keys:
+        // of a bitonic network), then the run fix-up. From 513 keys (with the
+        // 4 passes over the depth bits of the build before):
         // above 1,024 only, tracking at 640x480 / 300k measured 0.6 us per
         // iteration slower (6,269 / 6,271 against 6,277 / 6,285 iterations/s,
         // same box); from 257 keys, slower again (6,240 / 6,258)
         for (int i = tid; i < n; i += kThreads) s_a[i] = low_keys[s + i];
         __syncthreads();
-        uint64_t *a = s_a, *b = s_b;
-        for (int shift = 32; shift < 64; shift += kRadixBits) {
-            if (cta_radix_pass(a, b, n, shift, s_wh, s_warp)) {
-                uint64_t *t = a;
-                a = b;
-                b = t;
-            }
-        }
-        if (cta_fix_depth_ties(a, n)) {
-            for (int shift = 0; shift < 64; shift += kRadixBits) {
-                if (shift >= rec_bits && shift < 32) continue;
-                if (cta_radix_pass(a, b, n, shift, s_wh, s_warp)) {
-                    uint64_t *t = a;
-                    a = b;
-                    b = t;
-                }
-            }
-        }
+        const uint64_t *a = cta_sort_bucket(s_a, s_b, n, rec_bits, s_wh, s_warp, s_mm);
         for (int i = tid; i < n; i += kThreads) {
             const uint64_t k = a[i];
             values[s + i] = (uint32_t)k;
@@ -559,28 +637,7 @@ __global__ void __launch_bounds__(kThreads, 4)
         return;
     }
     // large buckets ping-pong between their own slots and the same slots of tmp
-    uint64_t *a = low_keys + s, *b = tmp + s;
-    // the four depth digits (bits [32, 64)), least significant first; equal
-    // depths are then put in record order
-    for (int shift = 32; shift < 64; shift += kRadixBits) {
-        if (cta_radix_pass(a, b, n, shift, s_wh, s_warp)) {
-            uint64_t *t = a;
-            a = b;
-            b = t;
-        }
-    }
-    if (cta_fix_depth_ties(a, n)) {
-        // a long run of one depth: full LSD over the record-index digits (bits
-        // [0, rec_bits)), then the depth digits
-        for (int shift = 0; shift < 64; shift += kRadixBits) {
-            if (shift >= rec_bits && shift < 32) continue;
-            if (cta_radix_pass(a, b, n, shift, s_wh, s_warp)) {
-                uint64_t *t = a;
-                a = b;
-                b = t;
-            }
-        }
-    }
+    const uint64_t *a = cta_sort_bucket(low_keys + s, tmp + s, n, rec_bits, s_wh, s_warp, s_mm);
     for (int i = tid; i < n; i += kThreads) {
         const uint64_t k = a[i];
         values[s + i] = (uint32_t)k;
