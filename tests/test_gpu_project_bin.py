@@ -139,6 +139,9 @@ def _synthetic_records(n, cams, tile, seed, ties=True):
     ([synth.Camera(16, 16, 1, 1, 0, 0)], 16, "short", 9000),                # runs of a few equal depths
     ([synth.Camera(40, 24, 1, 1, 0, 0)], 16, False, 20000),                 # 6 tiles, ~10k keys each
     ([synth.Camera(48, 40, 1, 1, 0, 0), synth.Camera(16, 16, 1, 1, 0, 0)], 8, "short", 5000),
+    # lists of 2,049-4,096 keys (radix passes in global memory)
+    ([synth.Camera(16, 16, 1, 1, 0, 0)], 16, False, 3500),
+    ([synth.Camera(16, 16, 1, 1, 0, 0)], 16, "short", 4000),
     # lists of 1,025-2,048 keys (radix sort in shared memory), with short runs of
     # equal depth and with long ones (full-sort fallback)
     ([synth.Camera(16, 16, 1, 1, 0, 0)], 16, "short", 1800),
