@@ -75,7 +75,7 @@ FUSED_DRAM_BYTES_PER_LAUNCH = 16.32128e6 + 0
 # from one ncu capture with the caches carried over between kernels
 # (profiles/dram_iteration_track-640x480-300k.md); None once a kernel of the
 # iteration changes.
-DRAM_BYTES_PER_ITERATION = 0.552448e6 + 3.041024e6
+DRAM_BYTES_PER_ITERATION = 0.905728e6 + 5.036544e6
 # DRAM bytes of one k_render_fused_pose<16, 3> launch at 1200x680 on the 5M
 # Gaussians: 16-bit storage and FP32 storage with the map in Morton order, and
 # FP32 storage in the generator's order; ncu, cold cache
