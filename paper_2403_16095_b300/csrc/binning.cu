@@ -267,13 +267,33 @@ struct QDigit {
     __device__ __forceinline__ uint32_t operator()(uint64_t k) const { return (dq.q(k) >> shift) & (kRadix - 1); }
 };
 
+// The lanes of the warp whose 8-bit digit d equals this lane's, among the lanes
+// with `active`, from eight ballots over the digit's bits. The radix passes of
+// lists in global memory use it in place of __match_any_sync: ncu showed the
+// sort kernel with its ADU pipe, which runs the match instruction, 70% busy on
+// the mapping window; with the ballots there, the mapping window went from
+// 2,506 to 2,532 keyframe-iterations/s, the uneven batch from 2,103 to 2,126
+// frames/s and 5M tracking from 575 to 577 iterations/s (same box, two runs
+// each). Lists in shared memory keep the match instruction: with the ballots
+// there too (mapping 2,548, uneven 2,135, 5M 584), the tracking iteration's
+// binning, whose long lists all sit in shared memory, was 1.6 us slower.
+__device__ __forceinline__ uint32_t peers8(uint32_t d, bool active) {
+    uint32_t m = __ballot_sync(0xffffffffu, active);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const uint32_t v = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+        m &= ((d >> b) & 1u) ? v : ~v;
+    }
+    return m;
+}
+
 // One stable LSD pass of the CTA over n keys: src -> dst by the 8-bit digit
 // dig(key). Warp w owns the contiguous segment [w seg, (w + 1) seg) of src: it
 // counts its segment's digits into its own histogram row, one CTA scan turns
 // the rows (digit-major, warp-minor) into output cursors, and each warp then
 // scatters its segment in order with warp barriers only. Returns false (dst
 // untouched, src still current) when all n keys share the digit.
-template <class Dig>
+template <bool kBallotPeers, class Dig>
 __device__ __forceinline__ bool cta_radix_pass(const uint64_t *src, uint64_t *dst, int n, Dig dig,
                                                uint32_t (*s_wh)[kRadix], uint32_t *s_warp) {
     static_assert(kThreads == kRadix, "one digit per thread in the scan");
@@ -297,7 +317,7 @@ __device__ __forceinline__ bool cta_radix_pass(const uint64_t *src, uint64_t *ds
 #pragma unroll
         for (int u = 0; u < kPassUnroll; ++u) {
             const uint32_t d = dg[u];
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t peers = kBallotPeers ? peers8(d, d < (uint32_t)kRadix) : __match_any_sync(0xffffffffu, d);
             if (d < (uint32_t)kRadix && (peers & lt_mask) == 0) s_wh[warp][d] += __popc(peers);
             __syncwarp();
         }
@@ -327,7 +347,7 @@ __device__ __forceinline__ bool cta_radix_pass(const uint64_t *src, uint64_t *ds
             const bool active = base + 32 * u + lane < hi;
             const uint64_t key = kg[u];
             const uint32_t d = active ? dig(key) : (uint32_t)kRadix;
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t peers = kBallotPeers ? peers8(d, active) : __match_any_sync(0xffffffffu, d);
             const uint32_t rank = __popc(peers & lt_mask);
             const uint32_t off = active ? s_wh[warp][d] : 0u;
             if (active) dst[off + rank] = key;
@@ -415,6 +435,7 @@ struct QRun {
 // than kMaxTieRun (a tile whose depths crowd into a few quanta, or many equal
 // depths) sends the bucket to a full LSD sort over the record-index and depth
 // digits.
+template <bool kBallotPeers>
 __device__ uint64_t *cta_sort_bucket(uint64_t *a, uint64_t *b, int n, int rec_bits, uint32_t (*s_wh)[kRadix],
                                      uint32_t *s_warp, uint32_t (*s_mm)[kWarps]) {
     uint32_t lo, hi;
@@ -423,7 +444,7 @@ __device__ uint64_t *cta_sort_bucket(uint64_t *a, uint64_t *b, int n, int rec_bi
         hi > lo ? (uint32_t)min((unsigned long long)0xffffffffu, (65535ull << 32) / (unsigned long long)(hi - lo)) : 0u;
     const DepthQ dq{lo, mul};
     for (int shift = 0; shift < 16; shift += kRadixBits) {
-        if (cta_radix_pass(a, b, n, QDigit{dq, shift}, s_wh, s_warp)) {
+        if (cta_radix_pass<kBallotPeers>(a, b, n, QDigit{dq, shift}, s_wh, s_warp)) {
             uint64_t *t = a;
             a = b;
             b = t;
@@ -432,7 +453,7 @@ __device__ uint64_t *cta_sort_bucket(uint64_t *a, uint64_t *b, int n, int rec_bi
     if (cta_fix_runs(a, n, QRun{dq})) {
         for (int shift = 0; shift < 64; shift += kRadixBits) {
             if (shift >= rec_bits && shift < 32) continue;
-            if (cta_radix_pass(a, b, n, BitDigit{shift}, s_wh, s_warp)) {
+            if (cta_radix_pass<kBallotPeers>(a, b, n, BitDigit{shift}, s_wh, s_warp)) {
                 uint64_t *t = a;
                 a = b;
                 b = t;
@@ -612,7 +633,7 @@ __global__ void __launch_bounds__(kThreads, 4)
         // same box); from 257 keys, slower again (6,240 / 6,258)
         for (int i = tid; i < n; i += kThreads) s_a[i] = low_keys[s + i];
         __syncthreads();
-        const uint64_t *a = cta_sort_bucket(s_a, s_b, n, rec_bits, s_wh, s_warp, s_mm);
+        const uint64_t *a = cta_sort_bucket<false>(s_a, s_b, n, rec_bits, s_wh, s_warp, s_mm);
         for (int i = tid; i < n; i += kThreads) {
             const uint64_t k = a[i];
             values[s + i] = (uint32_t)k;
@@ -637,7 +658,7 @@ __global__ void __launch_bounds__(kThreads, 4)
         return;
     }
     // large buckets ping-pong between their own slots and the same slots of tmp
-    const uint64_t *a = cta_sort_bucket(low_keys + s, tmp + s, n, rec_bits, s_wh, s_warp, s_mm);
+    const uint64_t *a = cta_sort_bucket<true>(low_keys + s, tmp + s, n, rec_bits, s_wh, s_warp, s_mm);
     for (int i = tid; i < n; i += kThreads) {
         const uint64_t k = a[i];
         values[s + i] = (uint32_t)k;
