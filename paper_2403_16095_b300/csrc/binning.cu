@@ -270,8 +270,8 @@ struct QDigit {
 // The lanes of the warp whose 8-bit digit d equals this lane's, among the lanes
 // with `active`, from eight ballots over the digit's bits. The radix passes of
 // lists in global memory use it in place of __match_any_sync: ncu showed the
-// sort kernel with its ADU pipe, which runs the match instruction, 70% busy on
-// the mapping window; with the ballots there, the mapping window went from
+// sort kernel's ADU pipe 70% busy on the mapping window, with the match
+// instruction as the suspect; with the ballots there, the mapping window went from
 // 2,506 to 2,532 keyframe-iterations/s, the uneven batch from 2,103 to 2,126
 // frames/s and 5M tracking from 575 to 577 iterations/s (same box, two runs
 // each). Lists in shared memory keep the match instruction: with the ballots
