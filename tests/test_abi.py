@@ -114,3 +114,40 @@ def test_schedule_and_batch_options_are_checked(A):
     tiles = A.gs_tiles(10, 12, p, None, p)  # no queue
     st = lib.gs_render_fwd(C.byref(p0), C.byref(tiles), 1, cam, None, C.byref(persist), C.byref(img), st32, None)
     assert st == A.GS_ERR_INVALID_ARG and "queue" in A.last_error()
+
+
+def test_tiles_touched_required_only_where_read(A):
+    """The binning and the FULL backward read each record's tiles_touched; the
+    blend calls read only rec and accept NULL there. Checked on the argument
+    validation, which runs before any launch."""
+    lib = A.lib
+    cam = (A.gs_camera * 1)(A.gs_camera(64, 48, 50.0, 50.0, 32.0, 24.0, 0.2))
+    p = C.c_void_p(256)
+    no_touched = A.gs_projected(10, 1, p, None, p)
+    tiles = A.gs_tiles(64, 12, p, None, p)
+    status = C.c_void_p(256)
+    # binning: rejected for the missing counts
+    opts = A.gs_opts(16, A.GS_MODE_POSE, 1.3, 0.0)
+    st = lib.gs_bin_tiles(C.byref(no_touched), 1, cam, C.byref(opts), C.byref(tiles), status, p, 1 << 20, None)
+    assert st == A.GS_ERR_INVALID_ARG and "tiles_touched" in A.last_error()
+    # FULL backward: rejected for the missing counts (before its other checks
+    # of the forward images)
+    full = A.gs_opts(16, A.GS_MODE_FULL, 1.3, 0.0)
+    img = A.gs_image()
+    st = lib.gs_render_bwd(C.byref(no_touched), C.byref(tiles), 1, cam, None, None, None, C.byref(img), None, None,
+                           C.byref(full), None, None, None, status, p, 1 << 20, None)
+    assert st == A.GS_ERR_INVALID_ARG and "tiles_touched" in A.last_error()
+    # POSE backward: the counts are not read; it fails on the missing forward
+    # images instead
+    st = lib.gs_render_bwd(C.byref(no_touched), C.byref(tiles), 1, cam, None, None, None, C.byref(img), None, None,
+                           C.byref(opts), None, None, None, status, p, 1 << 20, None)
+    assert st == A.GS_ERR_INVALID_ARG and "tiles_touched" not in A.last_error()
+
+
+def test_full_backward_binding_needs_touched(A):
+    """The Python binding refuses a FULL-mode backward without tiles_touched
+    before it marshals any tensor."""
+    full = A.gs_opts(16, A.GS_MODE_FULL, 1.3, 0.0)
+    with pytest.raises(ValueError, match="tiles_touched"):
+        A.gs_render_bwd(10, [None], full, None, None, None, None, None, None, None, {}, None, None, None, None, None,
+                        None, None)
