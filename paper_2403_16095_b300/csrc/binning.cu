@@ -48,6 +48,7 @@ constexpr int kScanThreads = 1024;
 constexpr int kPassUnroll = 4;  // 32-key groups per step of a radix pass (loads issued together)
 constexpr int kRadixMinKeys = 512;   // CTA lists above this (up to kSmemKeys) take the shared-memory radix sort
 constexpr int kSmemKeys = 2048;  // bucket size sorted entirely in shared memory
+constexpr int kBallotSmemTiles = 2048;  // larger batches: ballot peers in the shared-memory passes too
 
 __device__ __forceinline__ bool status_ok(const int32_t *status) { return status[0] == 0; }
 
@@ -274,8 +275,9 @@ struct QDigit {
 // instruction as the suspect; with the ballots there, the mapping window went from
 // 2,506 to 2,532 keyframe-iterations/s, the uneven batch from 2,103 to 2,126
 // frames/s and 5M tracking from 575 to 577 iterations/s (same box, two runs
-// each). Lists in shared memory keep the match instruction: with the ballots
-// there too (mapping 2,548, uneven 2,135, 5M 584), the tracking iteration's
+// each). Lists in shared memory use it in batches of more than
+// kBallotSmemTiles tiles (launch_bin_tiles): there too it measured faster
+// (mapping 2,548, uneven 2,135, 5M 584), but a 640x480 tracking frame's
 // binning, whose long lists all sit in shared memory, was 1.6 us slower.
 __device__ __forceinline__ uint32_t peers8(uint32_t d, bool active) {
     uint32_t m = __ballot_sync(0xffffffffu, active);
@@ -592,6 +594,7 @@ __device__ void warp_sort_regs(const uint64_t *__restrict__ keys, int n, uint32_
 // registers (cta_sort_regs); buckets of more than kSmemKeys keys take the LSD
 // radix sort over the depth digits and the equal-depth fix-up, ping-ponging in
 // global memory.
+template <bool kBallotSmem>
 __global__ void __launch_bounds__(kThreads, 4)
     k_tile_sort(uint64_t *low_keys, uint64_t *tmp, const uint32_t *__restrict__ ranges,
                 const uint32_t *__restrict__ order, const int *__restrict__ misc, int n_tiles,
@@ -633,7 +636,7 @@ __global__ void __launch_bounds__(kThreads, 4)
         // same box); from 257 keys, slower again (6,240 / 6,258)
         for (int i = tid; i < n; i += kThreads) s_a[i] = low_keys[s + i];
         __syncthreads();
-        const uint64_t *a = cta_sort_bucket<false>(s_a, s_b, n, rec_bits, s_wh, s_warp, s_mm);
+        const uint64_t *a = cta_sort_bucket<kBallotSmem>(s_a, s_b, n, rec_bits, s_wh, s_warp, s_mm);
         for (int i = tid; i < n; i += kThreads) {
             const uint64_t k = a[i];
             values[s + i] = (uint32_t)k;
@@ -756,7 +759,13 @@ cudaError_t launch_bin_tiles(const float *rec, const int *touched, int n_records
     if ((err = launch_chained(fill, dim3(grid), dim3(kThreads), 0, s, rec, touched, n_records, n_per_frame, ft, tc, low,
                               capacity, status)) != cudaSuccess)
         return err;
-    if ((err = launch_chained(k_tile_sort, dim3(ft.total_tiles), dim3(kThreads), 0, s, low, tmp, ranges, order, misc,
+    // Batches of more than kBallotSmemTiles tiles (multi-frame windows, the
+    // 1200x680 frames) take ballot peers in the shared-memory passes too: with
+    // them, mapping measured 2,532 -> 2,548 keyframe-iterations/s, uneven
+    // 2,126 -> 2,135 frames/s and 5M tracking 577 -> 584 iterations/s, while the
+    // 1,200-tile tracking frame lost 1.6 us of binning per iteration (peers8).
+    auto sort = ft.total_tiles > kBallotSmemTiles ? k_tile_sort<true> : k_tile_sort<false>;
+    if ((err = launch_chained(sort, dim3(ft.total_tiles), dim3(kThreads), 0, s, low, tmp, ranges, order, misc,
                               ft.total_tiles, values, keys_out, rec_bits, status)) != cudaSuccess)
         return err;
     return cudaGetLastError();
