@@ -131,6 +131,9 @@ def _synthetic_records(n, cams, tile, seed, ties=True):
     ([synth.Camera(128, 96, 1, 1, 0, 0)], 16, True, 3000),                  # 48 tiles
     ([synth.Camera(640, 480, 1, 1, 0, 0)], 16, False, 3000),                # 1200 tiles
     ([synth.Camera(640, 480, 1, 1, 0, 0)], 16, "short", 20000),             # 1200 tiles, counters a line apart
+    # 6,450 tiles (a batch of more than 2,048: ballot peers in the shared-memory
+    # passes) with lists of ~600 keys
+    ([synth.Camera(1200, 680, 1, 1, 0, 0)] * 2, 16, "short", 300000),
     ([synth.Camera(1200, 680, 1, 1, 0, 0)], 8, True, 3000),                 # 12750 tiles
     ([synth.Camera(100, 70, 1, 1, 0, 0), synth.Camera(37, 53, 1, 1, 0, 0),
       synth.Camera(64, 64, 1, 1, 0, 0)], 16, True, 3000),                   # uneven frames, ragged
